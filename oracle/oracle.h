@@ -1,0 +1,67 @@
+/*
+ * Plain FP64 CPU oracle for the unsplit piecewise-linear CTU step of the compressible solver
+ * (paper §3.2 "Compressible hydrodynamics", Eqs. 8-13, with the CTU construction of §3.1, Eqs. 3-6).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load this library.  It shares no code, header, table or constant with the CUDA library; the two are
+ * compared element by element on identical seeded inputs.
+ *
+ * Layout of a state array: U[k][j][i], k in {rho, rho*u, rho*v, rho*E}, j the row (y), i the column (x,
+ * fastest), with NX = nx + 2 ng columns and NY = ny + 2 ng rows, contiguous.  Interior cells are
+ * i in [ng, ng+nx), j in [ng, ng+ny).
+ *
+ * Every function is a straight transcription of the method's steps in the paper's order, one plain
+ * loop per stage, with no blocking or fusion.  Status codes: 0 ok, 1 invalid arguments, 2 out of memory.
+ */
+#ifndef ORACLE_HYDRO_H
+#define ORACLE_HYDRO_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int nx, ny, ng;
+  double xmin, xmax, ymin, ymax;
+  double gamma, cfl;
+  int bc_xlo, bc_xhi, bc_ylo, bc_yhi; /* 0 outflow (zero gradient), 1 periodic */
+  int limiter;                         /* 0 piecewise constant, 1 MC, 2 fourth-order MC */
+  int use_flattening;                  /* 0/1 */
+  double cvisc;                        /* artificial-viscosity coefficient (0 disables) */
+  int riemann_maxiter;
+  double riemann_tol;
+  double small_dens, small_pres;       /* floors applied to working copies only */
+} oracle_params;
+
+typedef struct {
+  long long riemann_solves;     /* number of two-shock solves performed */
+  long long riemann_iters;      /* total Newton iterations over all solves */
+  long long riemann_nonconv;    /* solves that hit riemann_maxiter without meeting the tolerance */
+  int riemann_maxiters_seen;
+} oracle_stats;
+
+/* ---- whole-grid driver calls (the solver's initialize/timestep/evolve sequence, paper §2) ---- */
+int oracle_fill_ghost(const oracle_params* p, double* U);
+int oracle_cfl_dt(const oracle_params* p, const double* U, double* dt_out);
+int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st);
+int oracle_conserved_totals(const oracle_params* p, const double* U, double out[4]);
+
+/* ---- per-cell / per-face stages, exported so tests can pin each one on its own ---- */
+void oracle_cons_to_prim(const oracle_params* p, const double U[4], double q[4]);
+void oracle_prim_to_cons(const oracle_params* p, const double q[4], double U[4]);
+double oracle_slope(int limiter, double qm2, double qm1, double q0, double qp1, double qp2);
+double oracle_flatten_chi(double pm2, double pm1, double pp1, double pp2, double um1, double up1, double small_pres);
+void oracle_trace(const oracle_params* p, double sigma, const double q[4], const double dq[4], double qL[4],
+                  double qR[4]);
+/* two-shock Riemann problem in the face frame: q = (rho, u_normal, u_transverse, p).
+ * guess <= 0 selects the acoustic (linearised) initial guess.  Outputs the face state and the flux
+ * (mass, normal momentum, transverse momentum, energy), the converged p* and u*, and the iteration count. */
+int oracle_riemann(const oracle_params* p, const double qL[4], const double qR[4], double guess, double face[4],
+                   double flux[4], double* pstar, double* ustar, int* iters);
+void oracle_euler_flux(const oracle_params* p, const double q[4], double F[4]);
+
+int oracle_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
