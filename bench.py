@@ -1,0 +1,387 @@
+"""Throughput of the unsplit CTU step on a GB300 (zone-updates per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload kh1024|sedov4096|sedov8192] [--precision fp32|fp64]
+
+A step is one pass of the solver's driver loop (paper §2): ghost fill, CFL time step reduced on the
+device, one fused CTU step.  Default workload: the 1024 x 1024 periodic Kelvin-Helmholtz shear layer
+(gamma 1.4, CFL 0.8, seeded noise in v), FP32 bulk with double energy recovery; the plain FP64 path is
+measured on the same workload in the same run.  Inputs are resident in HBM when the timed region
+starts; the state (17 MB in FP32) fits in L2, so L2 is flushed (256 MB write) before every timed step
+and each step is timed on its own with CUDA events on the solver's stream.
+
+--impl reference times the FP64 CPU oracle (the plain C implementation the CUDA path is checked
+against) on the host cores, on the same workload and metric.
+
+Multi-GPU (torchrun, N > 1): the problem is replicated, one independent copy per rank (no data-path
+exchange); the value is the sum over ranks, timed by the slowest rank.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic flops per zone-update: counted with an instrumented copy of the FP64 oracle on the
+# Kelvin-Helmholtz workload (+ - * / sqrt = 1 flop each): 973 per zone plus 40 per Newton iteration of
+# the two-shock solver, at 4.008 solves per zone (roofline section)
+FLOPS_BASE = 973.0
+FLOPS_PER_ITER = 40.0
+SOLVES_PER_ZONE = 4.008
+# measured ALU peaks on this machine's GB300 (FMA = 2 flops; 152 SMs): FP32 70.6 TFLOP/s, FP64 1.16 TFLOP/s
+ALU_PEAK_TFLOPS = {"fp32": 70.6, "fp64": 1.16}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "note": "fallback"}
+
+
+def workload(name):
+    import hydro_problems as hp
+    if name == "kh1024":
+        return hp.kh(1024, 1024, seed=0), "kh_1024x1024_periodic"
+    if name == "sedov4096":
+        return hp.sedov(4096, 4096), "sedov_4096x4096_outflow"
+    if name == "sedov8192":
+        return hp.sedov(8192, 8192, density_noise=0.01), "sedov_8192x8192_outflow_1pct_noise"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 250.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in load for k in range(4) if r[3][k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------------- our arm
+def time_device_path(pr, precision, steps, warmup, flush):
+    """Value: steps of fill + device dt + fused step with the state resident in HBM."""
+    import torch
+
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+
+    prec = H.HYDRO_FP32 if precision == "fp32" else H.HYDRO_FP64
+    s = Solver(params_for(pr, prec), pr.U)
+    stream = s.stream
+    for _ in range(warmup):
+        s.fill_ghost()
+        s.cfl_dt_async()
+        s.step_device_dt()
+    st0, stats0 = s.status()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        s.fill_ghost()
+        s.cfl_dt_async()
+        ev[k][1].record(stream)
+        s.step_device_dt()
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    kern_ms = [b.elapsed_time(c) for a, b, c in ev]
+    st, stats1 = s.status()
+    t_sim, n_sim = s.time()
+    tot = s.totals()
+    s.close()
+    solves = stats1[0] - stats0[0]
+    iters = stats1[1] - stats0[1]
+    return {"step_ms": step_ms, "kernel_ms": kern_ms, "iters_per_solve": iters / max(solves, 1),
+            "t_sim": t_sim, "totals": tot, "launches_per_step": 3}
+
+
+def time_e2e(pr, precision, steps, warmup):
+    """Same metric through the public C-ABI calls with host buffers: every step uploads the state from
+    pinned host memory, fills ghosts, reduces dt (read back), steps, and downloads the new state."""
+    import torch
+
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+
+    prec = H.HYDRO_FP32 if precision == "fp32" else H.HYDRO_FP64
+    dt_ = torch.float32 if precision == "fp32" else torch.float64
+    s = Solver(params_for(pr, prec), pr.U)
+    host_in = torch.from_numpy(np.ascontiguousarray(pr.U)).to(dt_).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+
+    def one():
+        s.upload(host_in)
+        s.fill_ghost()
+        dt = s.cfl_dt()
+        s.step(dt)
+        s.download(host_out)
+        host_in.copy_(host_out)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    s.status()
+    s.close()
+    nbytes = host_in.numel() * host_in.element_size()
+    return {"seconds": el, "h2d": nbytes, "d2h": nbytes + 8}
+
+
+def cpu_baseline(pr, budget_s=12.0, max_steps=50):
+    """The oracle as it stands (OpenMP over rows on all host cores), on whole steps of the same workload,
+    for about budget_s seconds."""
+    import oracle
+
+    p = oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl)
+    U = pr.U.copy()
+    oracle.fill_ghost(p, U)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps:
+        oracle.fill_ghost(p, U)
+        oracle.step(p, U, oracle.cfl_dt(p, U))
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": pr.nx * pr.ny * n / el, "unit": "zone-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{n} whole steps of the {pr.nx}x{pr.ny} workload from its initial state, "
+                                        f"{el:.1f} s, FP64"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1306_6883_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    pr, wname = workload(args.workload)
+    zones = pr.nx * pr.ny
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        main = time_device_path(pr, args.precision, args.steps, args.warmup, flush)
+    barrier(world)
+    other = "fp64" if args.precision == "fp32" else "fp32"
+    var = time_device_path(pr, other, max(args.steps // 4, 10), args.warmup, flush)
+    e2e = time_e2e(pr, args.precision, max(args.steps // 4, 10), args.warmup)
+
+    t_step = sum(main["step_ms"]) / 1e3
+    t_step = max_over_ranks(t_step, world)
+    ms_per_step = 1e3 * t_step / args.steps
+    value = world * zones * args.steps / t_step
+    kern_ms = sum(main["kernel_ms"]) / len(main["kernel_ms"])
+    flops_zone = FLOPS_BASE + FLOPS_PER_ITER * SOLVES_PER_ZONE * main["iters_per_solve"]
+    achieved = flops_zone * zones / (kern_ms * 1e-3) / 1e12
+    peak = ALU_PEAK_TFLOPS[args.precision]
+    bytes_zone = 2 * 4 * (4 if args.precision == "fp32" else 8)
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    e2e_steps = max(args.steps // 4, 10)
+    e2e_value = world * zones * e2e_steps / max_over_ranks(e2e["seconds"], world)
+    var_value = zones * len(var["step_ms"]) / (sum(var["step_ms"]) / 1e3)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "zone-updates/s (cells x steps / s) of the unsplit CTU step",
+        "value": value,
+        "unit": "zone-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded initial conditions)",
+        "config": {"workload": wname, "nx": pr.nx, "ny": pr.ny, "gamma": pr.gamma, "cfl": pr.cfl,
+                   "precision": args.precision + ("+fp64 energy recovery" if args.precision == "fp32" else ""),
+                   "step": "ghost fill + device CFL dt + fused CTU step",
+                   "l2": "flushed (256 MB write) before every timed step; per-step CUDA events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "ctu_step_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"measured {args.precision} FMA throughput (152 SMs), see DESIGN.md",
+                     "flops_per_zone": flops_zone, "kernel_ms": kern_ms,
+                     "hbm_gbs": bytes_zone * zones / (kern_ms * 1e-3) / 1e9, "hbm_frac_of_measured": None,
+                     "traffic": None},
+        "cpu_baseline": None,
+        "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"]},
+        "gpu_launches": main["launches_per_step"] * args.steps,
+        "clocks": clk.summary(),
+        "variants": {other: {"value": var_value, "ms_per_step": 1e3 / var_value * zones,
+                             "speedup_of_" + args.precision: value / world / var_value if args.precision == "fp32"
+                             else var_value / (value / world)}},
+        "riemann_iters_per_solve": main["iters_per_solve"],
+    }
+    line["roofline"]["hbm_frac_of_measured"] = line["roofline"]["hbm_gbs"] / hbm
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline(pr)
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank, local):
+    """The FP64 CPU oracle on the host cores: each timed step is one whole oracle step of the workload
+    (if that is too slow for the run to end within a few minutes, a centred window of it)."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import build as obuild
+    obuild.build()
+    pr, wname = workload(args.workload)
+    p = oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl)
+    U = pr.U.copy()
+    oracle.fill_ghost(p, U)
+    # probe one step to size the sample
+    t0 = time.perf_counter()
+    V = U.copy()
+    oracle.step(p, V, oracle.cfl_dt(p, V))
+    one = time.perf_counter() - t0
+    budget = 150.0
+    sample = f"whole {pr.nx}x{pr.ny} steps"
+    if one * (args.steps + args.warmup) > budget:
+        # centred window whose step fits the budget; its outer ng cells act as its ghost cells
+        frac = budget / (one * (args.steps + args.warmup))
+        w = max(64, int(pr.nx * np.sqrt(frac)) // 8 * 8)
+        j0 = (pr.ny - w) // 2 + pr.ng
+        i0 = (pr.nx - w) // 2 + pr.ng
+        U = np.ascontiguousarray(U[:, j0 - pr.ng:j0 + w + pr.ng, i0 - pr.ng:i0 + w + pr.ng])
+        dx = 1.0 / pr.nx
+        p = oracle.params(w, w, xmax=w * dx, ymax=w * dx, gamma=pr.gamma, cfl=pr.cfl)
+        sample = f"{w}x{w} centred window steps (window halo as ghost cells)"
+    zones = p.nx * p.ny
+    for _ in range(args.warmup):
+        oracle.step(p, U, oracle.cfl_dt(p, U))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(p, U, oracle.cfl_dt(p, U))
+    el = time.perf_counter() - t0
+    value = zones * args.steps / el
+    line = {
+        "impl": "reference",
+        "metric": "zone-updates/s (cells x steps / s) of the unsplit CTU step",
+        "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded initial conditions)",
+        "config": {"workload": wname, "nx": pr.nx, "ny": pr.ny, "gamma": pr.gamma, "cfl": pr.cfl,
+                   "precision": "fp64", "step": "oracle dt + oracle CTU step (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="kh1024")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) library for the unsplit piecewise-linear Godunov / CTU step
+ * of a gamma-law gas in 2-D (paper §3.2 "Compressible hydrodynamics", Eqs. 8-13, built on the CTU
+ * construction of §3.1, Eqs. 3-6).
+ *
+ * The calls follow the paper's single driver loop (§2): fill boundary conditions, get the time step,
+ * evolve one step, t += dt.  All compute runs in the library's CUDA kernels on the caller's stream.
+ *
+ * Conventions shared by every call
+ *  - Plain C types only.  "Device pointer" means memory from cudaMalloc (or any allocator handing out
+ *    device memory, e.g. PyTorch) on the device that is current when hydro_init is called.
+ *  - Every call returns a hydro_status and never aborts or throws.  On failure the context keeps a
+ *    message retrievable with hydro_last_error().
+ *  - Invalid parameters are rejected with HYDRO_EINVAL before anything is allocated or launched.
+ *  - Calls on one context are not thread safe; different contexts are independent.
+ *
+ * State layout (device): structure of arrays U[k][j][i] with k in {rho, rho u, rho v, rho E},
+ * j in [0, ny + 2 ng) the row (y), i in [0, nx + 2 ng) the column (x).  Element (k, j, i) lives at
+ * offset (k * (ny + 2 ng) + j) * pitch + i, with pitch = hydro_state_pitch(params) elements (the row
+ * length rounded up so every row starts on a 128-byte boundary).  Interior cells are
+ * i in [ng, ng + nx), j in [ng, ng + ny); the ng >= 4 cells around them are ghost cells.  Element type
+ * is double for HYDRO_FP64 and float for HYDRO_FP32.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYDRO_OK = 0,
+  HYDRO_EINVAL = 1,      /* bad argument or parameter */
+  HYDRO_ENOMEM = 2,      /* device or host allocation failed */
+  HYDRO_ECUDA = 3,       /* a CUDA runtime call failed (message in hydro_last_error) */
+  HYDRO_ENONFINITE = 4,  /* a NaN or Inf was found in the state */
+  HYDRO_ENEGATIVE = 5,   /* density or pressure <= 0 was found in the state */
+  HYDRO_ENONCONV = 6,    /* at least one Riemann solve hit riemann_maxiter without converging */
+  HYDRO_ETIMEOUT = 7     /* a bounded device-side wait ran out */
+} hydro_status;
+
+typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1 } hydro_bc;
+
+typedef enum {
+  HYDRO_FP64 = 0, /* state and arithmetic in double */
+  HYDRO_FP32 = 1  /* state and stencil arithmetic in float; the pressure of a cell whose kinetic energy
+                     is within 0.1% of its total energy is recomputed in double; dt and conserved totals
+                     are reduced in double */
+} hydro_precision;
+
+/* Parameters of one problem (the paper's RuntimeParameters for the compressible solver, §2). */
+typedef struct {
+  int nx, ny;                       /* interior cells, >= 1 */
+  int ng;                           /* ghost cells per side, must be >= 4 (stencil reach of the step) */
+  double xmin, xmax, ymin, ymax;    /* domain; dx = (xmax - xmin)/nx, dy = (ymax - ymin)/ny */
+  double gamma;                     /* gamma-law EOS p = rho e (gamma - 1) (Eq. 12), > 1 */
+  double cfl;                       /* CFL number C of Eq. 6, > 0 */
+  int bc_xlo, bc_xhi, bc_ylo, bc_yhi; /* hydro_bc; periodic sides must be paired and have n >= ng */
+  int limiter;                      /* 0 piecewise constant, 1 MC, 2 fourth-order MC (default) */
+  int use_flattening;               /* shock flattening, 0/1 (default 1) */
+  double cvisc;                     /* artificial-viscosity coefficient (default 0.1), >= 0 */
+  int riemann_maxiter;              /* Newton iteration cap of the two-shock solver (default 32) */
+  double riemann_tol;               /* relative |dp|/p stopping tolerance (default 1e-14 FP64, 1e-6 FP32) */
+  double small_dens, small_pres;    /* floors on working copies only, never on the stored state */
+  int precision;                    /* hydro_precision */
+  int use_learned_guess;            /* reserved, must be 0 */
+} hydro_params;
+
+typedef struct hydro_ctx hydro_ctx;
+
+/* Fill *p with the defaults above for an nx x ny grid on [0,1]^2, outflow on all sides, FP64.
+ * Returns HYDRO_EINVAL if p is NULL. */
+hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision);
+
+/* Row pitch (elements) and total byte size of one state array for these parameters; 0 if invalid. */
+size_t hydro_state_pitch(const hydro_params* p);
+size_t hydro_state_bytes(const hydro_params* p);
+
+/* Paper §2 Simulation.initialize(): validate parameters and create a context.
+ *   d_state, d_state_alt: two caller-owned device buffers of hydro_state_bytes(p) bytes each, in the
+ *     layout above.  The library borrows them (they must outlive the context): a step reads the current
+ *     one and writes the other, then they swap roles.  d_state holds the initial state.
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every kernel is launched.
+ * The context allocates its own small device scratch (reduction partials, status word, time).
+ * Errors: HYDRO_EINVAL (bad params or NULL/unaligned pointers: both buffers must be 256-byte aligned),
+ * HYDRO_ENOMEM, HYDRO_ECUDA. */
+hydro_status hydro_init(const hydro_params* p, void* d_state, void* d_state_alt, void* cuda_stream, hydro_ctx** out);
+
+/* Release the context's own resources (not the borrowed state buffers).  NULL is a no-op. */
+void hydro_destroy(hydro_ctx* ctx);
+
+/* Device pointer of the buffer that currently holds the state (d_state or d_state_alt). */
+void* hydro_state(const hydro_ctx* ctx);
+
+/* Fill the ghost cells of the current state (paper §2, CellCenterData2d ghost filling; Fig. 1):
+ * outflow copies the nearest interior cell (zero gradient), periodic wraps; a ghost cell (i, j)
+ * takes the value of interior cell (map_x(i), map_y(j)), which also defines the corners.  Async. */
+hydro_status hydro_fill_ghost(hydro_ctx* ctx);
+
+/* CFL time step (Eq. 6 with signal speeds |u| + c and |v| + c):
+ * *dt_out = cfl * min over interior cells of min(dx/(|u|+c), dy/(|v|+c)), c = sqrt(gamma p / rho).
+ * Synchronises the stream.  Also checks the state: returns HYDRO_ENONFINITE / HYDRO_ENEGATIVE (and
+ * leaves *dt_out unchanged) if any interior cell is non-finite or has rho <= 0 or p <= 0. */
+hydro_status hydro_cfl_dt(hydro_ctx* ctx, double* dt_out);
+
+/* One unsplit CTU step of length dt > 0 on the (ghost-filled) current state (paper §3.2 algorithm,
+ * update Eq. 5): slopes + flattening, characteristic tracing (Eq. 13), two-shock Riemann solves on the
+ * traced states, transverse flux-difference correction, final Riemann solves + artificial viscosity,
+ * conservative update.  Writes the other buffer and swaps.  Asynchronous: problems found on the device
+ * (non-finite or non-positive results, unconverged Riemann solves) are recorded in the context's status
+ * word and reported by hydro_sync_status(). */
+hydro_status hydro_step(hydro_ctx* ctx, double dt);
+
+/* CFL time step kept on the device: reduce the dt of hydro_cfl_dt into the context's device memory,
+ * clamp it so the simulated time does not pass tmax (tmax <= 0: no clamp), and advance the device-side
+ * time and step counter by it.  Asynchronous (no host synchronisation); the state checks of
+ * hydro_cfl_dt are recorded in the status word instead of returned. */
+hydro_status hydro_cfl_dt_async(hydro_ctx* ctx, double tmax);
+
+/* hydro_step with the time step produced by the last hydro_cfl_dt_async on this context (read on the
+ * device).  Asynchronous. */
+hydro_status hydro_step_device_dt(hydro_ctx* ctx);
+
+/* The driver loop of §2 kept on the device: for each of nsteps steps, fill ghosts, reduce the CFL dt
+ * into device memory, clamp it so the simulated time does not pass tmax (tmax <= 0: no clamp), and step
+ * with it.  No host synchronisation; time and step count stay on the device (hydro_get_time). */
+hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
+/* Equivalent to nsteps x {hydro_fill_ghost, hydro_cfl_dt_async(tmax), hydro_step_device_dt}. */
+
+/* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */
+hydro_status hydro_get_time(hydro_ctx* ctx, double* t, long long* nsteps);
+
+/* Conserved totals out[k] = sum over interior cells of U_k dx dy, accumulated in double in a fixed
+ * order (deterministic).  Synchronises. */
+hydro_status hydro_conserved_totals(hydro_ctx* ctx, double out[4]);
+
+/* Read and clear the device status word: HYDRO_OK, or the first of HYDRO_ENONFINITE, HYDRO_ENEGATIVE,
+ * HYDRO_ENONCONV recorded since the last call.  Synchronises.  If stats is not NULL it receives
+ * {riemann solves, riemann iterations, unconverged solves} accumulated since hydro_init. */
+hydro_status hydro_sync_status(hydro_ctx* ctx, unsigned long long stats[3]);
+
+/* Copy a host array into / out of the current state.  host has the dense layout
+ * [4][ny + 2 ng][nx + 2 ng] (no pitch) of the context's element type.  Pinned host memory makes the
+ * copies asynchronous; the call returns after enqueueing (upload) or after the copy (download). */
+hydro_status hydro_upload(hydro_ctx* ctx, const void* host);
+hydro_status hydro_download(hydro_ctx* ctx, void* host);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next call. */
+const char* hydro_last_error(const hydro_ctx* ctx);
+
+/* Library build string (compute capability and options), never NULL. */
+const char* hydro_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

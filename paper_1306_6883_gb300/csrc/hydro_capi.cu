@@ -1,0 +1,317 @@
+// C-ABI layer (include/hydro.h): parameter validation, context, scratch, and kernel launches on the
+// caller's stream.  The calls follow the single driver loop of the paper (§2): fill boundary conditions,
+// get the time step, evolve one step.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/hydro.h"
+#include "hydro_kernels.h"
+
+using hydro::DevScratch;
+using hydro::KParams;
+
+struct hydro_ctx {
+  hydro_params p;
+  KParams kp;
+  void* state[2];
+  int cur;
+  cudaStream_t stream;
+  int device;
+  DevScratch* scr;  // device
+  double* partials; // device, totals per-block partials
+  DevScratch* host_scr;  // pinned host mirror for reads
+  char err[512];
+};
+
+static size_t elem_size(int precision) { return precision == HYDRO_FP32 ? sizeof(float) : sizeof(double); }
+
+static int params_valid(const hydro_params* p, char* why, size_t n) {
+#define BAD(msg)                       \
+  do {                                 \
+    if (why) snprintf(why, n, "%s", msg); \
+    return 0;                          \
+  } while (0)
+  if (!p) BAD("params is NULL");
+  if (p->nx < 1 || p->ny < 1) BAD("nx and ny must be >= 1");
+  if (p->ng < 4) BAD("ng must be >= 4 (stencil reach of the CTU step)");
+  if ((long long)(p->nx + 2 * p->ng) * (p->ny + 2 * p->ng) > (1ll << 31)) BAD("grid too large (padded cells > 2^31)");
+  if (!(p->xmax > p->xmin) || !(p->ymax > p->ymin)) BAD("empty domain");
+  if (!(p->gamma > 1.0)) BAD("gamma must be > 1");
+  if (!(p->cfl > 0.0)) BAD("cfl must be > 0");
+  const int bcs[4] = {p->bc_xlo, p->bc_xhi, p->bc_ylo, p->bc_yhi};
+  for (int k = 0; k < 4; ++k)
+    if (bcs[k] != HYDRO_BC_OUTFLOW && bcs[k] != HYDRO_BC_PERIODIC) BAD("unknown boundary condition");
+  if ((p->bc_xlo == HYDRO_BC_PERIODIC) != (p->bc_xhi == HYDRO_BC_PERIODIC) ||
+      (p->bc_ylo == HYDRO_BC_PERIODIC) != (p->bc_yhi == HYDRO_BC_PERIODIC))
+    BAD("periodic boundaries must be paired");
+  if (p->bc_xlo == HYDRO_BC_PERIODIC && p->nx < p->ng) BAD("periodic x needs nx >= ng");
+  if (p->bc_ylo == HYDRO_BC_PERIODIC && p->ny < p->ng) BAD("periodic y needs ny >= ng");
+  if (p->limiter < 0 || p->limiter > 2) BAD("limiter must be 0, 1 or 2");
+  if (p->use_flattening != 0 && p->use_flattening != 1) BAD("use_flattening must be 0 or 1");
+  if (!(p->cvisc >= 0.0)) BAD("cvisc must be >= 0");
+  if (p->riemann_maxiter < 1 || p->riemann_maxiter > 1000) BAD("riemann_maxiter must be in [1, 1000]");
+  if (!(p->riemann_tol > 0.0)) BAD("riemann_tol must be > 0");
+  if (!(p->small_dens > 0.0) || !(p->small_pres > 0.0)) BAD("small_dens and small_pres must be > 0");
+  if (p->precision != HYDRO_FP64 && p->precision != HYDRO_FP32) BAD("precision must be HYDRO_FP64 or HYDRO_FP32");
+  if (p->precision == HYDRO_FP32 && (p->small_pres < 1e-30 || p->small_dens < 1e-30))
+    BAD("FP32 floors must be normal float numbers (>= 1e-30)");
+  if (p->use_learned_guess != 0) BAD("use_learned_guess is reserved and must be 0");
+  return 1;
+#undef BAD
+}
+
+static void set_err(hydro_ctx* c, const char* fmt, ...) {
+  if (!c) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->err, sizeof c->err, fmt, ap);
+  va_end(ap);
+}
+
+static hydro_status cuda_fail(hydro_ctx* c, cudaError_t e, const char* where) {
+  set_err(c, "%s: %s", where, cudaGetErrorString(e));
+  return HYDRO_ECUDA;
+}
+
+extern "C" {
+
+hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision) {
+  if (!p) return HYDRO_EINVAL;
+  memset(p, 0, sizeof *p);
+  p->nx = nx;
+  p->ny = ny;
+  p->ng = 4;
+  p->xmin = 0.0;
+  p->xmax = 1.0;
+  p->ymin = 0.0;
+  p->ymax = 1.0;
+  p->gamma = 1.4;
+  p->cfl = 0.8;
+  p->bc_xlo = p->bc_xhi = p->bc_ylo = p->bc_yhi = HYDRO_BC_OUTFLOW;
+  p->limiter = 2;
+  p->use_flattening = 1;
+  p->cvisc = 0.1;
+  p->riemann_maxiter = precision == HYDRO_FP32 ? 16 : 32;
+  p->riemann_tol = precision == HYDRO_FP32 ? 1e-6 : 1e-14;
+  p->small_dens = 1e-10;
+  p->small_pres = 1e-20;
+  p->precision = precision;
+  p->use_learned_guess = 0;
+  return HYDRO_OK;
+}
+
+size_t hydro_state_pitch(const hydro_params* p) {
+  if (!params_valid(p, nullptr, 0)) return 0;
+  const size_t row = (size_t)p->nx + 2 * (size_t)p->ng;
+  const size_t per = 128 / elem_size(p->precision);  // elements per 128 bytes
+  return (row + per - 1) / per * per;
+}
+
+size_t hydro_state_bytes(const hydro_params* p) {
+  const size_t pitch = hydro_state_pitch(p);
+  if (!pitch) return 0;
+  return 4 * pitch * ((size_t)p->ny + 2 * (size_t)p->ng) * elem_size(p->precision);
+}
+
+hydro_status hydro_init(const hydro_params* p, void* d_state, void* d_state_alt, void* cuda_stream, hydro_ctx** out) {
+  if (!out) return HYDRO_EINVAL;
+  *out = nullptr;
+  char why[256];
+  if (!params_valid(p, why, sizeof why)) return HYDRO_EINVAL;
+  if (!d_state || !d_state_alt || d_state == d_state_alt) return HYDRO_EINVAL;
+  if (((uintptr_t)d_state & 255) || ((uintptr_t)d_state_alt & 255)) return HYDRO_EINVAL;
+  hydro_ctx* c = new (std::nothrow) hydro_ctx();
+  if (!c) return HYDRO_ENOMEM;
+  c->p = *p;
+  c->state[0] = d_state;
+  c->state[1] = d_state_alt;
+  c->cur = 0;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->err[0] = 0;
+  KParams& k = c->kp;
+  k.nx = p->nx;
+  k.ny = p->ny;
+  k.ng = p->ng;
+  k.pitch = (int)hydro_state_pitch(p);
+  k.NX = p->nx + 2 * p->ng;
+  k.NY = p->ny + 2 * p->ng;
+  k.bc[0] = p->bc_xlo;
+  k.bc[1] = p->bc_xhi;
+  k.bc[2] = p->bc_ylo;
+  k.bc[3] = p->bc_yhi;
+  k.dx = (p->xmax - p->xmin) / p->nx;
+  k.dy = (p->ymax - p->ymin) / p->ny;
+  k.gamma = p->gamma;
+  k.gm1 = p->gamma - 1.0;
+  k.g1 = (p->gamma + 1.0) / (2.0 * p->gamma);
+  k.cfl = p->cfl;
+  k.limiter = p->limiter;
+  k.use_flattening = p->use_flattening;
+  k.cvisc = p->cvisc;
+  k.riemann_maxiter = p->riemann_maxiter;
+  k.riemann_tol = p->riemann_tol;
+  k.small_dens = p->small_dens;
+  k.small_pres = p->small_pres;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return HYDRO_ECUDA;
+  }
+  e = cudaMalloc((void**)&c->scr, sizeof(DevScratch));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partials, sizeof(double) * 4 * hydro::totals_max_blocks());
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_scr, sizeof(DevScratch));
+  if (e == cudaSuccess) e = hydro::init_scratch(c->scr, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    hydro_destroy(c);
+    return e == cudaErrorMemoryAllocation ? HYDRO_ENOMEM : HYDRO_ECUDA;
+  }
+  *out = c;
+  return HYDRO_OK;
+}
+
+void hydro_destroy(hydro_ctx* c) {
+  if (!c) return;
+  if (c->scr) cudaFree(c->scr);
+  if (c->partials) cudaFree(c->partials);
+  if (c->host_scr) cudaFreeHost(c->host_scr);
+  delete c;
+}
+
+void* hydro_state(const hydro_ctx* c) { return c ? c->state[c->cur] : nullptr; }
+
+hydro_status hydro_fill_ghost(hydro_ctx* c) {
+  if (!c) return HYDRO_EINVAL;
+  cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
+  return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "fill_ghost");
+}
+
+static hydro_status read_scratch(hydro_ctx* c) {
+  cudaError_t e = cudaMemcpyAsync(c->host_scr, c->scr, sizeof(DevScratch), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "read scratch");
+}
+
+static hydro_status status_from_flags(unsigned int f) {
+  if (f & hydro::STATUS_NONFINITE) return HYDRO_ENONFINITE;
+  if (f & hydro::STATUS_NEGATIVE) return HYDRO_ENEGATIVE;
+  if (f & hydro::STATUS_NONCONV) return HYDRO_ENONCONV;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_cfl_dt(hydro_ctx* c, double* dt_out) {
+  if (!c || !dt_out) return HYDRO_EINVAL;
+  cudaError_t e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, 0.0, 0, nullptr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cfl_dt");
+  hydro_status s = read_scratch(c);
+  if (s != HYDRO_OK) return s;
+  const unsigned int f = c->host_scr->status & (hydro::STATUS_NONFINITE | hydro::STATUS_NEGATIVE);
+  if (f) {
+    set_err(c, "cfl_dt: the state holds %s cells", (f & hydro::STATUS_NONFINITE) ? "non-finite" : "non-positive");
+    return status_from_flags(f);
+  }
+  *dt_out = c->host_scr->dt;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_step(hydro_ctx* c, double dt) {
+  if (!c || !(dt > 0.0) || !(dt < 1e300)) return HYDRO_EINVAL;
+  cudaError_t e =
+      hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], dt, nullptr, c->scr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ctu_step");
+  c->cur = 1 - c->cur;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_cfl_dt_async(hydro_ctx* c, double tmax) {
+  if (!c) return HYDRO_EINVAL;
+  cudaError_t e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
+  return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "cfl_dt_async");
+}
+
+hydro_status hydro_step_device_dt(hydro_ctx* c) {
+  if (!c) return HYDRO_EINVAL;
+  cudaError_t e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], 0.0, &c->scr->dt,
+                                  c->scr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step_device_dt");
+  c->cur = 1 - c->cur;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_advance(hydro_ctx* c, int nsteps, double tmax) {
+  if (!c || nsteps < 0) return HYDRO_EINVAL;
+  for (int n = 0; n < nsteps; ++n) {
+    cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
+    if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
+    if (e == cudaSuccess)
+      e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], 0.0, &c->scr->dt, c->scr,
+                          c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance");
+    c->cur = 1 - c->cur;
+  }
+  return HYDRO_OK;
+}
+
+hydro_status hydro_get_time(hydro_ctx* c, double* t, long long* nsteps) {
+  if (!c) return HYDRO_EINVAL;
+  hydro_status s = read_scratch(c);
+  if (s != HYDRO_OK) return s;
+  if (t) *t = c->host_scr->t;
+  if (nsteps) *nsteps = c->host_scr->nsteps;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_conserved_totals(hydro_ctx* c, double out[4]) {
+  if (!c || !out) return HYDRO_EINVAL;
+  cudaError_t e = hydro::conserved_totals(c->p.precision, c->kp, c->state[c->cur], c->partials, c->scr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "conserved_totals");
+  hydro_status s = read_scratch(c);
+  if (s != HYDRO_OK) return s;
+  for (int k = 0; k < 4; ++k) out[k] = c->host_scr->totals[k];
+  return HYDRO_OK;
+}
+
+hydro_status hydro_sync_status(hydro_ctx* c, unsigned long long stats[3]) {
+  if (!c) return HYDRO_EINVAL;
+  hydro_status s = read_scratch(c);
+  if (s != HYDRO_OK) return s;
+  const unsigned int f = c->host_scr->status;
+  if (stats)
+    for (int k = 0; k < 3; ++k) stats[k] = c->host_scr->stats[k];
+  if (f) {
+    cudaError_t e = cudaMemsetAsync(&c->scr->status, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear status");
+    set_err(c, "device status flags 0x%x", f);
+  }
+  return status_from_flags(f);
+}
+
+hydro_status hydro_upload(hydro_ctx* c, const void* host) {
+  if (!c || !host) return HYDRO_EINVAL;
+  const size_t es = elem_size(c->p.precision);
+  const size_t w = (size_t)c->kp.NX * es, pitchb = (size_t)c->kp.pitch * es;
+  cudaError_t e = cudaMemcpy2DAsync(c->state[c->cur], pitchb, host, w, w, (size_t)4 * c->kp.NY,
+                                    cudaMemcpyHostToDevice, c->stream);
+  return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "upload");
+}
+
+hydro_status hydro_download(hydro_ctx* c, void* host) {
+  if (!c || !host) return HYDRO_EINVAL;
+  const size_t es = elem_size(c->p.precision);
+  const size_t w = (size_t)c->kp.NX * es, pitchb = (size_t)c->kp.pitch * es;
+  cudaError_t e = cudaMemcpy2DAsync(host, w, c->state[c->cur], pitchb, w, (size_t)4 * c->kp.NY,
+                                    cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "download");
+}
+
+const char* hydro_last_error(const hydro_ctx* c) { return c ? c->err : "no context"; }
+
+const char* hydro_build_info(void) { return "hydro sm_103a; kernels: fill_ghost, cfl_dt, ctu_step (fp64 16x16, fp32 32x16), totals"; }
+
+}  // extern "C"

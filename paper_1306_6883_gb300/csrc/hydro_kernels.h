@@ -1,0 +1,31 @@
+// Internal launch interface between the C-ABI layer and the CUDA kernels (not installed).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+// precision: 0 = double, 1 = float.  All launches are asynchronous on `stream`.
+cudaError_t fill_ghost(int precision, const KParams& P, void* U, cudaStream_t stream);
+
+// CFL reduction.  Writes scr->dt = cfl * min(...), clamped to tmax - scr->t when tmax > 0 and, if
+// advance_time, adds it to scr->t and increments scr->nsteps.  Sets status bits for non-finite or
+// non-positive cells.  The min accumulator and block counter are reset by the last block.
+cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* scr, double tmax, int advance_time,
+                   double* partial_unused, cudaStream_t stream);
+
+// Conserved totals into scr->totals (deterministic two-level reduction; partials has room for
+// totals_max_blocks() * 4 doubles).
+int totals_max_blocks();
+cudaError_t conserved_totals(int precision, const KParams& P, const void* U, double* partials, DevScratch* scr,
+                             cudaStream_t stream);
+
+// One fused CTU step Uin -> Uout with dt from dt_dev if not NULL, else dt_host.
+cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, double dt_host,
+                     const double* dt_dev, DevScratch* scr, cudaStream_t stream);
+
+// Scratch initialisation (min accumulator = +inf, counters 0).
+cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream);
+
+}  // namespace hydro

@@ -1,0 +1,238 @@
+// Ghost-cell fill, CFL time-step reduction and conserved-total reduction kernels.
+#include <float.h>
+
+#include "hydro_device.cuh"
+#include "hydro_kernels.h"
+
+namespace hydro {
+
+// ---------------------------------------------------------------------------------------------------
+// Ghost cells (paper §2, CellCenterData2d ghost filling; Fig. 1): ghost (i, j) takes interior cell
+// (map_x(i), map_y(j)); outflow clamps to the nearest interior index (zero gradient), periodic wraps.
+// All sources are interior cells, so one pass over the ghost frame fills edges and corners.
+__device__ __forceinline__ int map_index(int i, int ng, int n, int lo_bc, int hi_bc) {
+  if (i < ng) return lo_bc == 1 ? i + n : ng;
+  if (i >= ng + n) return hi_bc == 1 ? i - n : ng + n - 1;
+  return i;
+}
+
+template <typename R>
+__global__ void fill_ghost_kernel(KParams P, R* __restrict__ U) {
+  // ghost frame enumerated as: bottom band ng x NX, top band ng x NX, then left/right bands ny x ng each
+  const int band = P.ng * P.NX;
+  const int side = P.ny * P.ng;
+  const int n = 2 * band + 2 * side;
+  const size_t plane = (size_t)P.NY * P.pitch;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int i, j;
+    if (e < band) {
+      j = e / P.NX; i = e % P.NX;
+    } else if (e < 2 * band) {
+      const int f = e - band;
+      j = P.ng + P.ny + f / P.NX; i = f % P.NX;
+    } else if (e < 2 * band + side) {
+      const int f = e - 2 * band;
+      j = P.ng + f / P.ng; i = f % P.ng;
+    } else {
+      const int f = e - 2 * band - side;
+      j = P.ng + f / P.ng; i = P.ng + P.nx + f % P.ng;
+    }
+    const int si = map_index(i, P.ng, P.nx, P.bc[0], P.bc[1]);
+    const int sj = map_index(j, P.ng, P.ny, P.bc[2], P.bc[3]);
+    const size_t d = (size_t)j * P.pitch + i, s = (size_t)sj * P.pitch + si;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[d + k * plane] = U[s + k * plane];
+  }
+}
+
+cudaError_t fill_ghost(int precision, const KParams& P, void* U, cudaStream_t stream) {
+  const int n = 2 * P.ng * P.NX + 2 * P.ny * P.ng;
+  const int threads = 256;
+  int blocks = (n + threads - 1) / threads;
+  if (blocks > 1024) blocks = 1024;
+  if (precision == 0)
+    fill_ghost_kernel<double><<<blocks, threads, 0, stream>>>(P, (double*)U);
+  else
+    fill_ghost_kernel<float><<<blocks, threads, 0, stream>>>(P, (float*)U);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------------
+// CFL time step (Eq. 6 with signal speeds |u|+c, |v|+c): per-cell min(dx/(|u|+c), dy/(|v|+c)) in the
+// state's precision, promoted to double; warp-shuffle min, block min, one atomicMin per block on the
+// bit pattern (positive doubles order like their bits); the last block to finish scales by cfl, clamps
+// to tmax - t and resets the accumulator for the next call.
+constexpr int DT_THREADS = 256;
+constexpr int DT_MAX_BLOCKS = 4 * 152;
+
+template <typename R>
+__global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* __restrict__ U,
+                                                           DevScratch* __restrict__ scr, double tmax, int advance) {
+  SP<R> s;
+  s.load(P);
+  const R dx = (R)P.dx, dy = (R)P.dy;
+  const size_t plane = (size_t)P.NY * P.pitch;
+  const long long ncell = (long long)P.nx * P.ny;
+  double best = DBL_MAX;
+  unsigned int flags = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ncell;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / P.nx), i = (int)(e % P.nx);
+    const size_t o = (size_t)(j + P.ng) * P.pitch + (i + P.ng);
+    const R U0 = U[o], U1 = U[o + plane], U2 = U[o + 2 * plane], U3 = U[o + 3 * plane];
+    if (!(isfinite((double)U0) && isfinite((double)U1) && isfinite((double)U2) && isfinite((double)U3))) {
+      flags |= STATUS_NONFINITE;
+      continue;
+    }
+    R rho, u, v, p;
+    cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
+    {
+      const R ke = M<R>::dv((R)0.5 * (U1 * U1 + U2 * U2), U0);
+      if (!(U0 > (R)0) || !(U3 - ke > (R)0)) flags |= STATUS_NEGATIVE;
+    }
+    const R cs = M<R>::sq(M<R>::dv(s.gamma * p, rho));
+    const R tx = M<R>::dv(dx, M<R>::ab(u) + cs);
+    const R ty = M<R>::dv(dy, M<R>::ab(v) + cs);
+    const double t = (double)M<R>::mn(tx, ty);
+    best = t < best ? t : best;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o < best ? o : best;
+    flags |= __shfl_xor_sync(0xffffffffu, flags, off);
+  }
+  __shared__ double wmin[DT_THREADS / 32];
+  __shared__ unsigned int wflags[DT_THREADS / 32];
+  __shared__ bool last;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    wmin[w] = best;
+    wflags[w] = flags;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = wmin[0];
+    unsigned int f = wflags[0];
+    for (int k = 1; k < DT_THREADS / 32; ++k) {
+      b = wmin[k] < b ? wmin[k] : b;
+      f |= wflags[k];
+    }
+    atomicMin(&scr->dt_min_bits, (unsigned long long)__double_as_longlong(b));
+    if (f) atomicOr(&scr->status, f);
+    __threadfence();
+    const unsigned int done = atomicAdd(&scr->dt_blocks_done, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long bits = atomicExch(&scr->dt_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
+    double dt = P.cfl * __longlong_as_double((long long)bits);
+    if (tmax > 0.0) {
+      const double left = tmax - scr->t;
+      dt = dt > left ? left : dt;
+      dt = dt < 0.0 ? 0.0 : dt;
+    }
+    scr->dt = dt;
+    if (advance) {
+      scr->t = scr->t + dt;
+      scr->nsteps = scr->nsteps + 1;
+    }
+    scr->dt_blocks_done = 0u;
+  }
+}
+
+cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* scr, double tmax, int advance_time,
+                   double*, cudaStream_t stream) {
+  const long long ncell = (long long)P.nx * P.ny;
+  long long b = (ncell + DT_THREADS - 1) / DT_THREADS;
+  const int blocks = (int)(b < DT_MAX_BLOCKS ? b : DT_MAX_BLOCKS);
+  if (precision == 0)
+    cfl_dt_kernel<double><<<blocks, DT_THREADS, 0, stream>>>(P, (const double*)U, scr, tmax, advance_time);
+  else
+    cfl_dt_kernel<float><<<blocks, DT_THREADS, 0, stream>>>(P, (const float*)U, scr, tmax, advance_time);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Conserved totals: sum_ij U_k dx dy in double.  Each block owns a fixed set of rows (grid-stride over
+// rows), each thread a fixed set of columns; block partials are combined by a fixed-shape tree, and the
+// last block adds the per-block partials in block order.  Deterministic for a given grid size.
+constexpr int TOT_THREADS = 256;
+constexpr int TOT_MAX_BLOCKS = 2 * 152;
+
+int totals_max_blocks() { return TOT_MAX_BLOCKS; }
+
+template <typename R>
+__global__ void __launch_bounds__(TOT_THREADS) totals_kernel(KParams P, const R* __restrict__ U,
+                                                            double* __restrict__ partials, DevScratch* __restrict__ scr) {
+  const size_t plane = (size_t)P.NY * P.pitch;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = blockIdx.x; j < P.ny; j += gridDim.x) {
+    const size_t row = (size_t)(j + P.ng) * P.pitch + P.ng;
+    for (int i = threadIdx.x; i < P.nx; i += TOT_THREADS) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += (double)U[row + i + k * plane];
+    }
+  }
+  __shared__ double red[4][TOT_THREADS];
+  __shared__ bool last;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = TOT_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) partials[blockIdx.x * 4 + k] = red[k][0];
+    __threadfence();
+    const unsigned int done = atomicAdd(&scr->tot_blocks_done, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const double area = P.dx * P.dy;
+    for (int k = 0; k < 4; ++k) {
+      double sum = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile double*)partials)[b * 4 + k];
+      scr->totals[k] = sum * area;
+    }
+    scr->tot_blocks_done = 0u;
+  }
+}
+
+cudaError_t conserved_totals(int precision, const KParams& P, const void* U, double* partials, DevScratch* scr,
+                             cudaStream_t stream) {
+  const int blocks = P.ny < TOT_MAX_BLOCKS ? P.ny : TOT_MAX_BLOCKS;
+  if (precision == 0)
+    totals_kernel<double><<<blocks, TOT_THREADS, 0, stream>>>(P, (const double*)U, partials, scr);
+  else
+    totals_kernel<float><<<blocks, TOT_THREADS, 0, stream>>>(P, (const float*)U, partials, scr);
+  return cudaGetLastError();
+}
+
+__global__ void init_scratch_kernel(DevScratch* scr) {
+  scr->dt_min_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
+  scr->dt_blocks_done = 0u;
+  scr->tot_blocks_done = 0u;
+  scr->dt = 0.0;
+  scr->t = 0.0;
+  scr->nsteps = 0;
+  scr->status = 0u;
+  scr->stats[0] = scr->stats[1] = scr->stats[2] = 0ull;
+  for (int k = 0; k < 4; ++k) scr->totals[k] = 0.0;
+}
+
+cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream) {
+  init_scratch_kernel<<<1, 1, 0, stream>>>(scr);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

@@ -1,0 +1,341 @@
+// Fused CTU tile kernel (paper §3.2 algorithm; CTU construction §3.1, Eqs. 3-5).
+//
+// One CTA computes TX x TY interior cells.  It stages the (TX+8) x (TY+8) primitive tile (4-cell halo) in
+// shared memory and runs every stage of the step on it without sending any intermediate to global memory:
+//   0. load U, convert to primitives                        (Eqs. 11-12)
+//   1. flattening coefficient xi on (TX+2) x (TY+2) cells    (§3.2, Colella 1990)
+//   2. limited slopes and characteristic tracing, x and y     (§3.1 limiter; Eq. 13)
+//   3. Riemann solves on the traced (hat) states at all faces the transverse terms need
+//   4. transverse correction + final Riemann solves + artificial viscosity at the tile's faces
+//   5. conservative update (Eq. 5), written to the other state buffer
+// Global traffic per cell is one read of U (plus the halo and an L1/L2 re-read of U^n at the faces for
+// the viscosity term) and one write of U^{n+1}.
+#include "hydro_device.cuh"
+#include "hydro_kernels.h"
+
+namespace hydro {
+
+template <typename R, int TX, int TY>
+struct TileLayout {
+  static constexpr int QX = TX + 8, QY = TY + 8;  // primitive tile with a 4-cell halo
+  static constexpr int SX = TX + 2, SY = TY + 2;  // cells whose face states are traced
+  static constexpr int nQ = 4 * QX * QY;
+  static constexpr int nXI = SX * SY;
+  static constexpr int nS = 4 * SX * SY;          // one traced-state family
+  static constexpr int nFXH = 4 * SY * (TX + 1);  // hat x fluxes: rows [3, TY+5), faces [4, TX+5)
+  static constexpr int nFYH = 4 * (TY + 1) * SX;  // hat y fluxes: faces [4, TY+5), columns [3, TX+5)
+  static constexpr int nFX = 4 * TY * (TX + 1);   // final x fluxes of the tile
+  static constexpr int nFY = 4 * (TY + 1) * TX;   // final y fluxes of the tile
+  static constexpr size_t bytes = sizeof(R) * (size_t)(nQ + nXI + 4 * nS + nFXH + nFYH + nFX + nFY);
+};
+
+template <typename R, int TX, int TY>
+size_t ctu_smem_bytes() {
+  return TileLayout<R, TX, TY>::bytes;
+}
+
+template <typename R, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
+                                                      double dt_host, const double* __restrict__ dt_dev,
+                                                      DevScratch* __restrict__ scr) {
+  using L = TileLayout<R, TX, TY>;
+  constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sq = reinterpret_cast<R*>(smem_raw);  // [4][QY][QX]
+  R* sxi = sq + L::nQ;                      // [SY][SX]
+  R* sxl = sxi + L::nXI;                    // [4][SY][SX] left state at i+1/2 of each cell
+  R* sxr = sxl + L::nS;                     // right state at i-1/2
+  R* syl = sxr + L::nS;                     // lower state at j+1/2 (frame rho, u, v, p)
+  R* syr = syl + L::nS;                     // upper state at j-1/2
+  R* sfxh = syr + L::nS;                    // [4][SY][TX+1]
+  R* sfyh = sfxh + L::nFXH;                 // [4][TY+1][SX]
+  R* sfx = sfyh + L::nFYH;                  // [4][TY][TX+1]
+  R* sfy = sfx + L::nFX;                    // [4][TY+1][TX]
+
+  SP<R> s;
+  s.load(P);
+  const double dt = dt_dev ? *dt_dev : dt_host;
+  const R sigx = (R)(dt / P.dx), sigy = (R)(dt / P.dy);
+  const R hx = (R)(0.5 * dt / P.dx), hy = (R)(0.5 * dt / P.dy);
+  const R idx = (R)P.dx, idy = (R)P.dy, idy4 = (R)(4.0 * P.dy), idx4 = (R)(4.0 * P.dx);
+
+  const int tid = threadIdx.x;
+  const int x0 = P.ng + blockIdx.x * TX;  // padded column of the first interior cell of the tile
+  const int y0 = P.ng + blockIdx.y * TY;
+  const size_t plane = (size_t)P.NY * P.pitch;
+
+  // ---- 0. load the tile (clamped to the array; clamped cells only feed cells outside the grid)
+  for (int e = tid; e < QX * QY; e += NT) {
+    const int lx = e % QX, ly = e / QX;
+    int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
+    gi = gi < P.NX - 1 ? gi : P.NX - 1;
+    gj = gj < P.NY - 1 ? gj : P.NY - 1;
+    const size_t o = (size_t)gj * P.pitch + gi;
+    R rho, u, v, p;
+    cons_to_prim(s, Uin[o], Uin[o + plane], Uin[o + 2 * plane], Uin[o + 3 * plane], rho, u, v, p);
+    sq[e] = rho;
+    sq[QX * QY + e] = u;
+    sq[2 * QX * QY + e] = v;
+    sq[3 * QX * QY + e] = p;
+  }
+  __syncthreads();
+
+  const R* qu = sq + QX * QY;
+  const R* qv = sq + 2 * QX * QY;
+  const R* qp = sq + 3 * QX * QY;
+  // ---- 1. flattening xi = min(xi_x, xi_y) on cells lx in [3, TX+5), ly in [3, TY+5)
+  for (int e = tid; e < SX * SY; e += NT) {
+    const int cx = e % SX + 3, cy = e / SX + 3;
+    R xi = (R)1;
+    if (s.flatten) {
+      const int b = cy * QX + cx;
+      auto chix = [&](int m) {
+        return flatten_chi<R>(qp[b + m - 2], qp[b + m - 1], qp[b + m + 1], qp[b + m + 2], qu[b + m - 1], qu[b + m + 1],
+                              s.small_pres);
+      };
+      auto chiy = [&](int m) {
+        return flatten_chi<R>(qp[b + (m - 2) * QX], qp[b + (m - 1) * QX], qp[b + (m + 1) * QX], qp[b + (m + 2) * QX],
+                              qv[b + (m - 1) * QX], qv[b + (m + 1) * QX], s.small_pres);
+      };
+      const int sx = (qp[b + 1] - qp[b - 1]) >= (R)0 ? 1 : -1;
+      const int sy = (qp[b + QX] - qp[b - QX]) >= (R)0 ? 1 : -1;
+      const R xix = M<R>::mn(chix(0), chix(-sx));
+      const R xiy = M<R>::mn(chiy(0), chiy(-sy));
+      xi = M<R>::mn(xix, xiy);
+    }
+    sxi[e] = xi;
+  }
+  __syncthreads();
+
+  // ---- 2. slopes + tracing for the same cells; items [0, nC) trace in x, [nC, 2 nC) in y
+  {
+    constexpr int nC = SX * SY;
+    for (int e = tid; e < 2 * nC; e += NT) {
+      const bool ydir = e >= nC;
+      const int c = ydir ? e - nC : e;
+      const int cx = c % SX + 3, cy = c / SX + 3;
+      const int b = cy * QX + cx;
+      const int st = ydir ? QX : 1;
+      const R xi = sxi[c];
+      R q[4], dq[4];
+      // face frame: (rho, un, ut, p); in y un = v, ut = u
+      const int kmap[4] = {0, ydir ? 2 : 1, ydir ? 1 : 2, 3};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const R* a = sq + kmap[m] * QX * QY + b;
+        q[m] = a[0];
+        dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+      }
+      R ql[4], qrr[4];
+      trace<R>(s, ydir ? sigy : sigx, q, dq, ql, qrr);
+      R* dl = ydir ? syl : sxl;
+      R* dr = ydir ? syr : sxr;
+      // store in (rho, u, v, p) order
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        dl[kmap[m] * nC + c] = ql[m];
+        dr[kmap[m] * nC + c] = qrr[m];
+      }
+    }
+  }
+  __syncthreads();
+
+  unsigned long long n_solves = 0, n_iters = 0, n_nonconv = 0;
+
+  // ---- 3. hat Riemann solves.  x faces: lx in [4, TX+5) between cells lx-1 and lx, rows [3, TY+5).
+  //         y faces: ly in [4, TY+5), columns [3, TX+5).
+  {
+    constexpr int nXF = (TX + 1) * SY, nYF = (TY + 1) * SX;
+    constexpr int nC = SX * SY;
+    for (int e = tid; e < nXF + nYF; e += NT) {
+      R a[4], bq[4], F[4];
+      int it;
+      bool ok;
+      if (e < nXF) {
+        const int fx = e % (TX + 1), ry = e / (TX + 1);  // face index 0..TX <-> lx = fx + 4; row ly = ry + 3
+        const int cL = ry * SX + fx;                      // cell lx-1 = fx + 3 -> s index fx
+        const int cR = cL + 1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          a[m] = sxl[m * nC + cL];
+          bq[m] = sxr[m * nC + cR];
+        }
+        riemann<R>(s, a, bq, (R)0, F, it, ok);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
+      } else {
+        const int f = e - nXF;
+        const int cxs = f % SX, fy = f / SX;  // column s index; face 0..TY <-> ly = fy + 4
+        const int cL = fy * SX + cxs;          // cell ly-1 = fy + 3
+        const int cR = cL + SX;
+        a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
+        bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
+        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        const int o = fy * SX + cxs;
+        sfyh[0 * (TY + 1) * SX + o] = F[0];
+        sfyh[1 * (TY + 1) * SX + o] = F[2];
+        sfyh[2 * (TY + 1) * SX + o] = F[1];
+        sfyh[3 * (TY + 1) * SX + o] = F[3];
+      }
+      n_solves++;
+      n_iters += it;
+      n_nonconv += ok ? 0 : 1;
+    }
+  }
+  __syncthreads();
+
+  // ---- 4. transverse correction + final solves + artificial viscosity at the tile's faces
+  {
+    constexpr int nC = SX * SY;
+    constexpr int nXF = (TX + 1) * TY, nYF = (TY + 1) * TX;
+    for (int e = tid; e < nXF + nYF; e += NT) {
+      R a[4], bq[4], F[4], UL[4], UR[4];
+      int it;
+      bool ok;
+      if (e < nXF) {
+        const int fx = e % (TX + 1), ty = e / (TX + 1);  // face lx = fx + 4, row ly = ty + 4
+        const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
+        // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
+        const int fL = ty * SX + fx, fR = fL + 1;
+        prim_to_cons(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
+        prim_to_cons(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R* fy = sfyh + k * (TY + 1) * SX;
+          UL[k] = UL[k] - hy * (fy[fL + SX] - fy[fL]);
+          UR[k] = UR[k] - hy * (fy[fR + SX] - fy[fR]);
+        }
+        cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
+        cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
+        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        // artificial viscosity from the cell-centred velocities of the time-n state
+        const int lx = fx + 4, ly = ty + 4;
+        const int b = ly * QX + lx;
+        const R div = M<R>::dv(qu[b] - qu[b - 1], idx) +
+                      M<R>::dv(qv[b + QX] + qv[b + QX - 1] - qv[b - QX] - qv[b - QX - 1], idy4);
+        const R av = s.cvisc * M<R>::mx(-div * idx, (R)0);
+        if (s.cvisc > (R)0) {
+          int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
+          gi = gi < P.NX - 1 ? gi : P.NX - 1;
+          gj = gj < P.NY - 1 ? gj : P.NY - 1;
+          const size_t o = (size_t)gj * P.pitch + gi;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) F[k] += av * (Uin[o - 1 + k * plane] - Uin[o + k * plane]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sfx[(k * TY + ty) * (TX + 1) + fx] = F[k];
+      } else {
+        const int f = e - nXF;
+        const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
+        const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
+        // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
+        const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
+        prim_to_cons(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
+        prim_to_cons(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R* fxh = sfxh + k * SY * (TX + 1);
+          UL[k] = UL[k] - hx * (fxh[fL + 1] - fxh[fL]);
+          UR[k] = UR[k] - hx * (fxh[fR + 1] - fxh[fR]);
+        }
+        R ql[4], qrr[4];
+        cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], ql[0], ql[1], ql[2], ql[3]);
+        cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], qrr[0], qrr[1], qrr[2], qrr[3]);
+        a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
+        bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
+        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        R G[4] = {F[0], F[2], F[1], F[3]};
+        const int lx = tx + 4, ly = fy + 4;
+        const int b = ly * QX + lx;
+        const R div = M<R>::dv(qv[b] - qv[b - QX], idy) +
+                      M<R>::dv(qu[b + 1] + qu[b - QX + 1] - qu[b - 1] - qu[b - QX - 1], idx4);
+        const R av = s.cvisc * M<R>::mx(-div * idy, (R)0);
+        if (s.cvisc > (R)0) {
+          int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
+          gi = gi < P.NX - 1 ? gi : P.NX - 1;
+          gj = gj < P.NY - 1 ? gj : P.NY - 1;
+          const size_t o = (size_t)gj * P.pitch + gi;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) G[k] += av * (Uin[o - P.pitch + k * plane] - Uin[o + k * plane]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sfy[(k * (TY + 1) + fy) * TX + tx] = G[k];
+      }
+      n_solves++;
+      n_iters += it;
+      n_nonconv += ok ? 0 : 1;
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. conservative update of the tile's valid cells
+  unsigned int flags = 0;
+  {
+    const R sx = (R)(dt / P.dx), sy = (R)(dt / P.dy);
+    for (int e = tid; e < TX * TY; e += NT) {
+      const int tx = e % TX, ty = e / TX;
+      const int gi = x0 + tx, gj = y0 + ty;
+      if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
+      const size_t o = (size_t)gj * P.pitch + gi;
+      R Un[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const R* fx = sfx + k * TY * (TX + 1);
+        const R* fy = sfy + k * (TY + 1) * TX;
+        const R d = sx * (fx[ty * (TX + 1) + tx] - fx[ty * (TX + 1) + tx + 1]) +
+                    sy * (fy[ty * TX + tx] - fy[(ty + 1) * TX + tx]);
+        Un[k] = Uin[o + k * plane] + d;
+        Uout[o + k * plane] = Un[k];
+      }
+      const bool finite = isfinite((double)Un[0]) && isfinite((double)Un[1]) && isfinite((double)Un[2]) &&
+                          isfinite((double)Un[3]);
+      if (!finite) {
+        flags |= STATUS_NONFINITE;
+      } else {
+        const R ke = M<R>::dv((R)0.5 * (Un[1] * Un[1] + Un[2] * Un[2]), Un[0]);
+        if (!(Un[0] > (R)0) || !(Un[3] - ke > (R)0)) flags |= STATUS_NEGATIVE;
+      }
+    }
+  }
+
+  // ---- per-block reduction of the counters, one atomic per block
+  if (n_nonconv) flags |= STATUS_NONCONV;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    n_solves += __shfl_xor_sync(0xffffffffu, n_solves, off);
+    n_iters += __shfl_xor_sync(0xffffffffu, n_iters, off);
+    n_nonconv += __shfl_xor_sync(0xffffffffu, n_nonconv, off);
+    flags |= __shfl_xor_sync(0xffffffffu, flags, off);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(&scr->stats[0], n_solves);
+    atomicAdd(&scr->stats[1], n_iters);
+    if (n_nonconv) atomicAdd(&scr->stats[2], n_nonconv);
+    if (flags) atomicOr(&scr->status, flags);
+  }
+}
+
+template <typename R, int TX, int TY, int NT>
+cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, double dt_host, const double* dt_dev,
+                            DevScratch* scr, cudaStream_t stream) {
+  const size_t smem = ctu_smem_bytes<R, TX, TY>();
+  static bool attr_set = false;  // per instantiation; set before first launch on any device
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  ctu_step_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, dt_host, dt_dev, scr);
+  return cudaGetLastError();
+}
+
+cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, double dt_host, const double* dt_dev,
+                     DevScratch* scr, cudaStream_t stream) {
+  if (precision == 0)
+    return launch_ctu_step<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, dt_host, dt_dev, scr, stream);
+  return launch_ctu_step<float, 32, 16, 256>(P, (const float*)Uin, (float*)Uout, dt_host, dt_dev, scr, stream);
+}
+
+}  // namespace hydro

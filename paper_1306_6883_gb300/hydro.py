@@ -1,0 +1,177 @@
+"""Thin ctypes binding of libhydro.so (include/hydro.h): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels.  PyTorch provides device memory and the
+stream.  There is no CPU fallback: loading fails loudly if the library is missing.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhydro.so")
+
+HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA, HYDRO_ENONFINITE, HYDRO_ENEGATIVE, HYDRO_ENONCONV, HYDRO_ETIMEOUT = range(8)
+STATUS_NAMES = ["HYDRO_OK", "HYDRO_EINVAL", "HYDRO_ENOMEM", "HYDRO_ECUDA", "HYDRO_ENONFINITE", "HYDRO_ENEGATIVE",
+                "HYDRO_ENONCONV", "HYDRO_ETIMEOUT"]
+HYDRO_FP64, HYDRO_FP32 = 0, 1
+BC = {"outflow": 0, "periodic": 1}
+
+
+class HydroParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("ng", ctypes.c_int),
+        ("xmin", ctypes.c_double), ("xmax", ctypes.c_double), ("ymin", ctypes.c_double), ("ymax", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("bc_xlo", ctypes.c_int), ("bc_xhi", ctypes.c_int), ("bc_ylo", ctypes.c_int), ("bc_yhi", ctypes.c_int),
+        ("limiter", ctypes.c_int), ("use_flattening", ctypes.c_int), ("cvisc", ctypes.c_double),
+        ("riemann_maxiter", ctypes.c_int), ("riemann_tol", ctypes.c_double),
+        ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double),
+        ("precision", ctypes.c_int), ("use_learned_guess", ctypes.c_int),
+    ]
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}" if msg else name)
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+_PP = ctypes.POINTER(HydroParams)
+
+# name -> (restype, argtypes); the same names as the C ABI
+SIGNATURES = {
+    "hydro_default_params": (ctypes.c_int, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "hydro_state_pitch": (ctypes.c_size_t, [_PP]),
+    "hydro_state_bytes": (ctypes.c_size_t, [_PP]),
+    "hydro_init": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "hydro_destroy": (None, [_VP]),
+    "hydro_state": (_VP, [_VP]),
+    "hydro_fill_ghost": (ctypes.c_int, [_VP]),
+    "hydro_cfl_dt": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "hydro_step": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "hydro_advance": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double]),
+    "hydro_cfl_dt_async": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "hydro_step_device_dt": (ctypes.c_int, [_VP]),
+    "hydro_get_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "hydro_conserved_totals": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "hydro_sync_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hydro_upload": (ctypes.c_int, [_VP, _VP]),
+    "hydro_download": (ctypes.c_int, [_VP, _VP]),
+    "hydro_last_error": (ctypes.c_char_p, [_VP]),
+    "hydro_build_info": (ctypes.c_char_p, []),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libhydro.so (build it first with paper_1306_6883_gb300.build.build())."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library {path} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def default_params(nx, ny, precision=HYDRO_FP64, **overrides):
+    p = HydroParams()
+    _check(load().hydro_default_params(ctypes.byref(p), nx, ny, precision), None, "hydro_default_params")
+    for k, v in overrides.items():
+        if k == "bc":
+            p.bc_xlo, p.bc_xhi, p.bc_ylo, p.bc_yhi = (BC[b] if isinstance(b, str) else b for b in v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def state_pitch(p):
+    return load().hydro_state_pitch(ctypes.byref(p))
+
+
+def state_bytes(p):
+    return load().hydro_state_bytes(ctypes.byref(p))
+
+
+def _check(status, ctx, what):
+    if status != HYDRO_OK:
+        msg = load().hydro_last_error(ctx).decode() if ctx else ""
+        raise HydroError(status, f"{what}: {msg}")
+
+
+def hydro_init(p, d_state_ptr, d_state_alt_ptr, stream_ptr):
+    ctx = _VP()
+    _check(load().hydro_init(ctypes.byref(p), _VP(d_state_ptr), _VP(d_state_alt_ptr), _VP(stream_ptr),
+                             ctypes.byref(ctx)), None, "hydro_init")
+    return ctx
+
+
+def hydro_destroy(ctx):
+    load().hydro_destroy(ctx)
+
+
+def hydro_state(ctx):
+    return load().hydro_state(ctx)
+
+
+def hydro_fill_ghost(ctx):
+    _check(load().hydro_fill_ghost(ctx), ctx, "hydro_fill_ghost")
+
+
+def hydro_cfl_dt(ctx):
+    dt = ctypes.c_double()
+    _check(load().hydro_cfl_dt(ctx, ctypes.byref(dt)), ctx, "hydro_cfl_dt")
+    return dt.value
+
+
+def hydro_step(ctx, dt):
+    _check(load().hydro_step(ctx, float(dt)), ctx, "hydro_step")
+
+
+def hydro_advance(ctx, nsteps, tmax=0.0):
+    _check(load().hydro_advance(ctx, int(nsteps), float(tmax)), ctx, "hydro_advance")
+
+
+def hydro_cfl_dt_async(ctx, tmax=0.0):
+    _check(load().hydro_cfl_dt_async(ctx, float(tmax)), ctx, "hydro_cfl_dt_async")
+
+
+def hydro_step_device_dt(ctx):
+    _check(load().hydro_step_device_dt(ctx), ctx, "hydro_step_device_dt")
+
+
+def hydro_get_time(ctx):
+    t, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(load().hydro_get_time(ctx, ctypes.byref(t), ctypes.byref(n)), ctx, "hydro_get_time")
+    return t.value, n.value
+
+
+def hydro_conserved_totals(ctx):
+    out = (ctypes.c_double * 4)()
+    _check(load().hydro_conserved_totals(ctx, out), ctx, "hydro_conserved_totals")
+    return list(out)
+
+
+def hydro_sync_status(ctx, raise_on_error=True):
+    stats = (ctypes.c_ulonglong * 3)()
+    st = load().hydro_sync_status(ctx, stats)
+    if raise_on_error:
+        _check(st, ctx, "hydro_sync_status")
+    return st, list(stats)
+
+
+def hydro_upload(ctx, host_ptr):
+    _check(load().hydro_upload(ctx, _VP(host_ptr)), ctx, "hydro_upload")
+
+
+def hydro_download(ctx, host_ptr):
+    _check(load().hydro_download(ctx, _VP(host_ptr)), ctx, "hydro_download")
+
+
+def hydro_build_info():
+    return load().hydro_build_info().decode()

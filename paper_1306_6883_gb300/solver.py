@@ -1,0 +1,106 @@
+"""Convenience wrapper around the C ABI with PyTorch-owned device buffers (memory and stream only).
+
+    s = Solver(params, U0_numpy)      # U0: (4, ny+2ng, nx+2ng) float64 array, dense layout
+    s.fill_ghost(); dt = s.cfl_dt(); s.step(dt)
+    U = s.state_numpy()
+
+Every operation is one C-ABI call; no arithmetic of the method happens here.
+"""
+import numpy as np
+import torch
+
+from . import hydro as H
+
+
+class Solver:
+    def __init__(self, params, U0=None, stream=None, device="cuda"):
+        self.p = params
+        self.dtype = torch.float32 if params.precision == H.HYDRO_FP32 else torch.float64
+        self.np_dtype = np.float32 if params.precision == H.HYDRO_FP32 else np.float64
+        self.pitch = H.state_pitch(params)
+        if self.pitch == 0:
+            raise H.HydroError(H.HYDRO_EINVAL, "invalid parameters")
+        self.NX = params.nx + 2 * params.ng
+        self.NY = params.ny + 2 * params.ng
+        n = 4 * self.NY * self.pitch
+        self.bufs = [torch.zeros(n, dtype=self.dtype, device=device) for _ in range(2)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.ctx = H.hydro_init(params, self.bufs[0].data_ptr(), self.bufs[1].data_ptr(), self.stream.cuda_stream)
+        if U0 is not None:
+            self.set_state(U0)
+
+    def close(self):
+        if self.ctx is not None:
+            H.hydro_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the C-ABI calls
+    def fill_ghost(self):
+        H.hydro_fill_ghost(self.ctx)
+
+    def cfl_dt(self):
+        return H.hydro_cfl_dt(self.ctx)
+
+    def step(self, dt):
+        H.hydro_step(self.ctx, dt)
+
+    def advance(self, nsteps, tmax=0.0):
+        H.hydro_advance(self.ctx, nsteps, tmax)
+
+    def cfl_dt_async(self, tmax=0.0):
+        H.hydro_cfl_dt_async(self.ctx, tmax)
+
+    def step_device_dt(self):
+        H.hydro_step_device_dt(self.ctx)
+
+    def upload(self, host_tensor):
+        """Enqueue a copy of a pinned host tensor (4, NY, NX) into the current state."""
+        H.hydro_upload(self.ctx, host_tensor.data_ptr())
+
+    def download(self, host_tensor):
+        H.hydro_download(self.ctx, host_tensor.data_ptr())
+
+    def time(self):
+        return H.hydro_get_time(self.ctx)
+
+    def totals(self):
+        return H.hydro_conserved_totals(self.ctx)
+
+    def status(self, raise_on_error=True):
+        return H.hydro_sync_status(self.ctx, raise_on_error)
+
+    # ---- state access
+    def current(self):
+        """Torch view (4, NY, pitch) of the buffer that holds the current state."""
+        ptr = H.hydro_state(self.ctx)
+        buf = self.bufs[0] if ptr == self.bufs[0].data_ptr() else self.bufs[1]
+        return buf.view(4, self.NY, self.pitch)
+
+    def set_state(self, U):
+        U = np.ascontiguousarray(U, dtype=self.np_dtype)
+        assert U.shape == (4, self.NY, self.NX), U.shape
+        host = torch.from_numpy(U).pin_memory()
+        H.hydro_upload(self.ctx, host.data_ptr())
+        self.stream.synchronize()
+
+    def state_numpy(self):
+        out = torch.empty((4, self.NY, self.NX), dtype=self.dtype).pin_memory()
+        H.hydro_download(self.ctx, out.data_ptr())
+        return out.numpy().copy()
+
+    def interior(self):
+        g = self.p.ng
+        return self.state_numpy()[:, g:-g, g:-g]
+
+
+def params_for(problem, precision=H.HYDRO_FP64, **kw):
+    """C-ABI parameters for a hydro_problems.Problem."""
+    xmin, xmax, ymin, ymax = problem.domain
+    return H.default_params(problem.nx, problem.ny, precision, bc=problem.bc, gamma=problem.gamma, cfl=problem.cfl,
+                            xmin=xmin, xmax=xmax, ymin=ymin, ymax=ymax, ng=problem.ng, **kw)

@@ -1,0 +1,364 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element on the same
+seeded inputs.
+
+FP64 bar: after one step from identical input, every element agrees with the oracle to 1e-12 of its
+field's magnitude (max |U_k| over the grid); dt to 1e-14 relative; conserved totals to 1e-13.
+FP32 bar (float storage and stencil arithmetic, double energy recovery in cells where the kinetic energy
+is within 0.1% of the total, double reductions): see test_fp32_step_error_is_within_its_bound.
+"""
+import numpy as np
+import pytest
+
+import hydro_problems as hp
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+NG = 4
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_6883_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _mods():
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+    return H, Solver, params_for
+
+
+def _oparams(pr, **kw):
+    xmin, xmax, ymin, ymax = pr.domain
+    return oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl, xmin=xmin, xmax=xmax, ymin=ymin,
+                         ymax=ymax, **kw)
+
+
+def _field_err(got, ref):
+    scale = np.abs(ref).reshape(4, -1).max(axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return (np.abs(got - ref).reshape(4, -1).max(axis=1) / scale)
+
+
+def _gpu_one_step(pr, precision=0, **kw):
+    H, Solver, params_for = _mods()
+    s = Solver(params_for(pr, precision, **kw), pr.U)
+    s.fill_ghost()
+    Uin = s.state_numpy()
+    dt = s.cfl_dt()
+    s.step(dt)
+    st, stats = s.status(raise_on_error=False)
+    out = s.state_numpy()
+    s.close()
+    return Uin, out, dt, st, stats
+
+
+def _oracle_one_step(pr, Uin, dt=None, **kw):
+    po = _oparams(pr, **kw)
+    U = np.array(Uin, dtype=np.float64)
+    oracle.fill_ghost(po, U)
+    dto = oracle.cfl_dt(po, U)
+    oracle.step(po, U, dto if dt is None else dt)
+    return U, dto
+
+
+def _interior(U):
+    return U[:, NG:-NG, NG:-NG]
+
+
+PROBLEMS = {
+    "sod_x_128": lambda: hp.sod(128, 128),
+    "sod_y_128": lambda: hp.sod(128, 128, direction="y"),
+    "kh_100x70": lambda: hp.kh(100, 70, seed=1),
+    "sedov_100": lambda: hp.sedov(100, 100, r_init=0.05),
+    "quad_70x50": lambda: hp.quad(70, 50, seed=3),
+    "pulse_64": lambda: hp.pulse(64, 64),
+    "quad_1x1": lambda: hp.quad(1, 1, seed=4),
+    "quad_5x3": lambda: hp.quad(5, 3, seed=5),
+    "quad_17x33": lambda: hp.quad(17, 33, seed=6),
+    "kh_4x4": lambda: hp.kh(4, 4, seed=2),
+}
+
+
+# ------------------------------------------------------------------------------------------------ ghost / dt / totals
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", [("outflow",) * 4, ("periodic",) * 4, ("outflow", "outflow", "periodic", "periodic"),
+                                ("periodic", "periodic", "outflow", "outflow")])
+@pytest.mark.parametrize("shape", [(13, 9), (64, 64), (37, 100)])
+def test_ghost_fill_is_bit_exact(precision, bc, shape):
+    H, Solver, params_for = _mods()
+    nx, ny = shape
+    rng = np.random.default_rng(nx * 1000 + ny)
+    U = np.zeros((4, ny + 2 * NG, nx + 2 * NG))
+    U[:, NG:-NG, NG:-NG] = rng.uniform(0.5, 2.0, size=(4, ny, nx))
+    p = H.default_params(nx, ny, precision, bc=bc)
+    s = Solver(p, U)
+    s.fill_ghost()
+    got = s.state_numpy()
+    s.close()
+    ref = np.array(U, dtype=np.float32 if precision else np.float64).astype(np.float64)
+    oracle.fill_ghost(oracle.params(nx, ny, bc=bc), ref)
+    np.testing.assert_array_equal(got.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("name", ["sod_x_128", "kh_100x70", "sedov_100", "quad_70x50", "quad_1x1"])
+def test_dt_and_totals_match_the_oracle(name):
+    pr = PROBLEMS[name]()
+    Uin, _, dt, _, _ = _gpu_one_step(pr)
+    po = _oparams(pr)
+    U = Uin.copy()
+    dto = oracle.cfl_dt(po, U)
+    assert abs(dt - dto) <= 1e-14 * dto
+    H, Solver, params_for = _mods()
+    s = Solver(params_for(pr), pr.U)
+    tot = np.array(s.totals())
+    s.close()
+    ref = oracle.conserved_totals(po, pr.U)
+    scale = np.abs(_interior(pr.U)).sum(axis=(1, 2)) * (1.0 / pr.nx) * (1.0 / pr.ny)
+    assert np.all(np.abs(tot - ref) <= 1e-13 * np.maximum(scale, 1e-300)), (tot, ref)
+
+
+# ------------------------------------------------------------------------------------------------ one FP64 step
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_fp64_step_matches_the_oracle(name):
+    pr = PROBLEMS[name]()
+    Uin, out, dt, st, _ = _gpu_one_step(pr)
+    assert st == 0
+    ref, dto = _oracle_one_step(pr, Uin, dt)
+    assert abs(dt - dto) <= 1e-14 * dto
+    err = _field_err(_interior(out), _interior(ref))
+    assert np.all(err <= FP64_TOL), err
+
+
+@pytest.mark.parametrize("opts", [dict(limiter=0), dict(limiter=1), dict(use_flattening=0), dict(cvisc=0.0),
+                                  dict(cvisc=0.5, limiter=1, use_flattening=0)])
+def test_fp64_step_matches_the_oracle_for_every_option(opts):
+    pr = hp.quad(48, 40, seed=9)
+    Uin, out, dt, st, _ = _gpu_one_step(pr, **opts)
+    ref, _ = _oracle_one_step(pr, Uin, dt, **opts)
+    err = _field_err(_interior(out), _interior(ref))
+    assert np.all(err <= FP64_TOL), err
+
+
+def test_sod_trajectory_matches_step_by_step():
+    # every step of the Sod run to t = 0.2, each from identical input
+    H, Solver, params_for = _mods()
+    pr = hp.sod(128, 128)
+    po = _oparams(pr)
+    s = Solver(params_for(pr), pr.U)
+    t, n, worst = 0.0, 0, 0.0
+    while t < 0.2:
+        s.fill_ghost()
+        Uin = s.state_numpy()
+        dt = s.cfl_dt()
+        U = Uin.copy()
+        dto = oracle.cfl_dt(po, U)
+        assert abs(dt - dto) <= 1e-14 * dto
+        dt = min(dt, 0.2 - t)
+        s.step(dt)
+        oracle.step(po, U, dt)
+        err = _field_err(_interior(s.state_numpy()), _interior(U))
+        worst = max(worst, err.max())
+        assert np.all(err <= FP64_TOL), (n, err)
+        t += dt
+        n += 1
+    s.status()
+    s.close()
+    assert n > 50
+
+
+def test_device_driver_loop_equals_the_host_loop():
+    # hydro_advance (dt reduced and consumed on the device) == fill / cfl_dt / step from the host
+    H, Solver, params_for = _mods()
+    pr = hp.kh(64, 48, seed=5)
+    a = Solver(params_for(pr), pr.U)
+    b = Solver(params_for(pr), pr.U)
+    t = 0.0
+    for _ in range(10):
+        a.fill_ghost()
+        dt = a.cfl_dt()
+        a.step(dt)
+        t += dt
+    b.advance(10)
+    tb, nb = b.time()
+    assert nb == 10 and tb == pytest.approx(t, rel=1e-15)
+    np.testing.assert_array_equal(_interior(a.state_numpy()), _interior(b.state_numpy()))
+    a.close()
+    b.close()
+
+
+def test_advance_stops_at_tmax():
+    H, Solver, params_for = _mods()
+    pr = hp.sod(64, 8)
+    s = Solver(params_for(pr), pr.U)
+    s.advance(200, 0.2)
+    t, n = s.time()
+    assert t == pytest.approx(0.2, rel=1e-14) and n == 200
+    s.close()
+
+
+def test_periodic_run_conserves_totals_on_the_gpu():
+    H, Solver, params_for = _mods()
+    pr = hp.kh(128, 128, seed=7)
+    s = Solver(params_for(pr), pr.U)
+    t0 = np.array(s.totals())
+    s.advance(50)
+    t1 = np.array(s.totals())
+    s.status()
+    s.close()
+    scale = np.abs(_interior(pr.U)).sum(axis=(1, 2)) / (128 * 128)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
+
+
+def test_transposed_problem_gives_the_transposed_answer():
+    pr = hp.quad(40, 40, seed=8)
+    prT = hp.Problem("quadT", 40, 40, hp.transpose(pr.U), pr.bc)
+    _, out, dt, _, _ = _gpu_one_step(pr)
+    _, outT, dtT, _, _ = _gpu_one_step(prT)
+    assert dt == dtT
+    err = _field_err(_interior(hp.transpose(out)), _interior(outT))
+    assert np.all(err <= 1e-13), err
+
+
+# ------------------------------------------------------------------------------------------------ full sizes, sampled
+def _windows(n, w, count, seed):
+    rng = np.random.default_rng(seed)
+    pts = [(NG, NG), (NG + n - w, NG + n - w)]  # corners touch the boundary
+    while len(pts) < count:
+        pts.append((int(rng.integers(NG, NG + n - w)), int(rng.integers(NG, NG + n - w))))
+    return pts
+
+
+def _check_windows(pr, Uin, out, dt, tol, w=24, count=6, seed=0):
+    """Oracle step on windows of the full ghost-filled input (the window's outer 4 cells act as its ghost
+    cells) compared with the GPU output of the window's interior."""
+    dx = (pr.domain[1] - pr.domain[0]) / pr.nx
+    dy = (pr.domain[3] - pr.domain[2]) / pr.ny
+    worst = np.zeros(4)
+    scale = np.abs(out[:, NG:-NG, NG:-NG]).reshape(4, -1).max(axis=1).astype(np.float64)
+    scale = np.where(scale > 0, scale, 1.0)
+    for (j0, i0) in _windows(min(pr.nx, pr.ny), w, count, seed):
+        Uw = np.ascontiguousarray(Uin[:, j0 - NG:j0 + w + NG, i0 - NG:i0 + w + NG], dtype=np.float64)
+        po = oracle.params(w, w, xmax=w * dx, ymax=w * dy, gamma=pr.gamma, cfl=pr.cfl)
+        oracle.step(po, Uw, dt)
+        got = out[:, j0:j0 + w, i0:i0 + w].astype(np.float64)
+        ref = _interior(Uw)
+        e = np.abs(got - ref).reshape(4, -1).max(axis=1) / scale
+        worst = np.maximum(worst, e)
+    assert np.all(worst <= tol), worst
+    return worst
+
+
+def test_kh_1024_fp64_full_size_sampled():
+    pr = hp.kh(1024, 1024)
+    Uin, out, dt, st, _ = _gpu_one_step(pr)
+    assert st == 0
+    _check_windows(pr, Uin, out, dt, FP64_TOL, count=8)
+
+
+# ------------------------------------------------------------------------------------------------ FP32 path
+def _fp32_case(pr, **kw):
+    Uin, out, dt, st, stats = _gpu_one_step(pr, precision=1, **kw)
+    ref, dto = _oracle_one_step(pr, Uin.astype(np.float64), dt)
+    return Uin, out, dt, dto, st, ref
+
+
+@pytest.mark.parametrize("name", ["sod_x_128", "kh_100x70", "sedov_100", "quad_70x50", "pulse_64", "quad_17x33"])
+def test_fp32_step_error_is_within_its_bound(name):
+    # FP32 bound: float rounding (2^-24) of ~10^2 dependent operations per output, with approximate
+    # division / square root (<= 2 ulp), gives a per-step error of order 1e-5 of each field's scale
+    pr = PROBLEMS[name]()
+    Uin, out, dt, dto, st, ref = _fp32_case(pr)
+    assert st == 0
+    assert abs(dt - dto) <= 1e-6 * dto
+    err = _field_err(_interior(out).astype(np.float64), _interior(ref))
+    assert np.all(err <= 2e-5), err
+
+
+def test_sedov_4096_fp32_full_size_sampled():
+    pr = hp.sedov(4096, 4096)
+    Uin, out, dt, st, _ = _gpu_one_step(pr, precision=1)
+    assert st == 0
+    _check_windows(pr, Uin, out, dt, 2e-5, w=24, count=4)
+    # the blast centre itself
+    c = NG + 2048 - 12
+    dx = 1.0 / 4096
+    Uw = np.ascontiguousarray(Uin[:, c - NG:c + 24 + NG, c - NG:c + 24 + NG], dtype=np.float64)
+    po = oracle.params(24, 24, xmax=24 * dx, ymax=24 * dx)
+    oracle.step(po, Uw, dt)
+    e = _field_err(out[:, c:c + 24, c:c + 24].astype(np.float64), _interior(Uw))
+    assert np.all(e <= 2e-5), e
+
+
+def test_sedov_8192_fp32_maximum_size_runs_and_matches_samples():
+    pr = hp.sedov(8192, 8192, density_noise=0.01)
+    Uin, out, dt, st, _ = _gpu_one_step(pr, precision=1)
+    assert st == 0
+    _check_windows(pr, Uin, out, dt, 2e-5, w=16, count=3, seed=1)
+
+
+# ------------------------------------------------------------------------------------------------ failure reporting
+def test_nonfinite_state_is_reported():
+    H, Solver, params_for = _mods()
+    pr = hp.kh(32, 32)
+    U = pr.U.copy()
+    U[3, 10, 12] = np.nan
+    s = Solver(params_for(pr), U)
+    s.fill_ghost()
+    with pytest.raises(H.HydroError) as e:
+        s.cfl_dt()
+    assert e.value.status == H.HYDRO_ENONFINITE
+    s.close()
+
+
+def test_negative_density_is_reported():
+    H, Solver, params_for = _mods()
+    pr = hp.kh(32, 32)
+    U = pr.U.copy()
+    U[0, 20, 7] = -1.0
+    s = Solver(params_for(pr), U)
+    s.fill_ghost()
+    with pytest.raises(H.HydroError) as e:
+        s.cfl_dt()
+    assert e.value.status == H.HYDRO_ENEGATIVE
+    s.close()
+
+
+def test_riemann_nonconvergence_is_reported():
+    H, Solver, params_for = _mods()
+    pr = hp.sod(32, 8)
+    s = Solver(params_for(pr, riemann_maxiter=1), pr.U)
+    s.fill_ghost()
+    s.step(s.cfl_dt())
+    st, stats = s.status(raise_on_error=False)
+    assert st == H.HYDRO_ENONCONV and stats[2] > 0 and stats[0] > 0
+    # the status word was cleared by the read
+    st2, _ = s.status(raise_on_error=False)
+    assert st2 == H.HYDRO_OK
+    s.close()
+
+
+def test_upload_download_roundtrip_is_exact():
+    H, Solver, params_for = _mods()
+    pr = hp.quad(33, 21, seed=1)
+    for prec, dt_ in ((0, np.float64), (1, np.float32)):
+        s = Solver(params_for(pr, prec), pr.U)
+        np.testing.assert_array_equal(s.state_numpy(), pr.U.astype(dt_))
+        s.close()
+
+
+def test_bad_time_step_is_rejected():
+    H, Solver, params_for = _mods()
+    pr = hp.sod(16, 8)
+    s = Solver(params_for(pr), pr.U)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(H.HydroError) as e:
+            s.step(bad)
+        assert e.value.status == H.HYDRO_EINVAL
+    s.close()
