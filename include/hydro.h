@@ -39,7 +39,8 @@ typedef enum {
   HYDRO_ENONFINITE = 4,  /* a NaN or Inf was found in the state */
   HYDRO_ENEGATIVE = 5,   /* density or pressure <= 0 was found in the state */
   HYDRO_ENONCONV = 6,    /* at least one Riemann solve hit riemann_maxiter without converging */
-  HYDRO_ETIMEOUT = 7     /* a bounded device-side wait ran out */
+  HYDRO_ETIMEOUT = 7,    /* a bounded device-side wait ran out */
+  HYDRO_ERANGE = 8       /* a size is beyond a fixed maximum of the call (see the call) */
 } hydro_status;
 
 typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1 } hydro_bc;
@@ -136,6 +137,26 @@ hydro_status hydro_get_time(hydro_ctx* ctx, double* t, long long* nsteps);
 /* Conserved totals out[k] = sum over interior cells of U_k dx dy, accumulated in double in a fixed
  * order (deterministic).  Synchronises. */
 hydro_status hydro_conserved_totals(hydro_ctx* ctx, double out[4]);
+
+/* Conserved totals for callers that cannot allocate device memory (no counterpart in the paper; it is
+ * a runtime convenience).  Such callers are code running while another allocator owns the device memory
+ * (a framework's caching allocator or a fixed pool, where a stray cudaMalloc would fragment or overrun
+ * the budget) and diagnostics taken after an out-of-memory error, when cudaMalloc itself fails.
+ *   p:        parameters of the state (validated as in hydro_init).
+ *   d_state:  device pointer to one state in the layout above, ghost cells need not be filled.
+ *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ *   out:      host array receiving sum over interior cells of U_k dx dy, k = 0..3, accumulated in double.
+ * Needs no context and calls no cudaMalloc, cudaFree or other allocating routine.  Its reduction scratch
+ * is one file-scope device array of (4 HYDRO_NOALLOC_MAX_ROWS + 8) doubles (512 KB), which every GPU
+ * that loads the library holds until the process exits.  The first call on a device looks up that
+ * array's device address (with that device current) and caches it, so make the first call on each device
+ * before any stream capture.  Every call shares the one array: calls whose kernels overlap on the GPU
+ * (two streams, two threads) race and return wrong totals; serialise them.  Synchronises the stream.
+ * Errors: HYDRO_EINVAL (bad params or NULL pointers), HYDRO_ERANGE (ny > HYDRO_NOALLOC_MAX_ROWS),
+ * HYDRO_ECUDA. */
+#define HYDRO_NOALLOC_MAX_ROWS 16384
+hydro_status hydro_conserved_totals_noalloc(const hydro_params* p, const void* d_state, void* cuda_stream,
+                                            double out[4]);
 
 /* Read and clear the device status word: HYDRO_OK, or the first of HYDRO_ENONFINITE, HYDRO_ENEGATIVE,
  * HYDRO_ENONCONV recorded since the last call.  Synchronises.  If stats is not NULL it receives

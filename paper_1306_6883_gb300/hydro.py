@@ -9,9 +9,11 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhydro.so")
 
-HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA, HYDRO_ENONFINITE, HYDRO_ENEGATIVE, HYDRO_ENONCONV, HYDRO_ETIMEOUT = range(8)
+(HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA, HYDRO_ENONFINITE, HYDRO_ENEGATIVE, HYDRO_ENONCONV,
+ HYDRO_ETIMEOUT, HYDRO_ERANGE) = range(9)
 STATUS_NAMES = ["HYDRO_OK", "HYDRO_EINVAL", "HYDRO_ENOMEM", "HYDRO_ECUDA", "HYDRO_ENONFINITE", "HYDRO_ENEGATIVE",
-                "HYDRO_ENONCONV", "HYDRO_ETIMEOUT"]
+                "HYDRO_ENONCONV", "HYDRO_ETIMEOUT", "HYDRO_ERANGE"]
+NOALLOC_MAX_ROWS = 16384
 HYDRO_FP64, HYDRO_FP32 = 0, 1
 BC = {"outflow": 0, "periodic": 1}
 
@@ -57,6 +59,7 @@ SIGNATURES = {
     "hydro_get_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "hydro_conserved_totals": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "hydro_sync_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hydro_conserved_totals_noalloc": (ctypes.c_int, [_PP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "hydro_upload": (ctypes.c_int, [_VP, _VP]),
     "hydro_download": (ctypes.c_int, [_VP, _VP]),
     "hydro_last_error": (ctypes.c_char_p, [_VP]),
@@ -154,6 +157,14 @@ def hydro_get_time(ctx):
 def hydro_conserved_totals(ctx):
     out = (ctypes.c_double * 4)()
     _check(load().hydro_conserved_totals(ctx, out), ctx, "hydro_conserved_totals")
+    return list(out)
+
+
+def hydro_conserved_totals_noalloc(p, d_state_ptr, stream_ptr):
+    """Totals of a state without any allocation (file-scope device scratch; see include/hydro.h)."""
+    out = (ctypes.c_double * 4)()
+    _check(load().hydro_conserved_totals_noalloc(ctypes.byref(p), _VP(d_state_ptr), _VP(stream_ptr), out), None,
+           "hydro_conserved_totals_noalloc")
     return list(out)
 
 
