@@ -156,6 +156,18 @@ hydro_status hydro_init(const hydro_params* p, void* d_state, void* d_state_alt,
   k.riemann_tol = p->riemann_tol;
   k.small_dens = p->small_dens;
   k.small_pres = p->small_pres;
+  k.gamma_f = (float)k.gamma;
+  k.gm1_f = (float)k.gm1;
+  k.igm1_f = (float)(1.0 / k.gm1);
+  k.idx_f = (float)(1.0 / k.dx);
+  k.idy_f = (float)(1.0 / k.dy);
+  k.g1_f = (float)k.g1;
+  k.small_dens_f = (float)k.small_dens;
+  k.small_pres_f = (float)k.small_pres;
+  k.tol_f = (float)k.riemann_tol;
+  k.cvisc_f = (float)k.cvisc;
+  k.dx_f = (float)k.dx;
+  k.dy_f = (float)k.dy;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     delete c;
@@ -221,7 +233,8 @@ hydro_status hydro_cfl_dt(hydro_ctx* c, double* dt_out) {
 hydro_status hydro_step(hydro_ctx* c, double dt) {
   if (!c || !(dt > 0.0) || !(dt < 1e300)) return HYDRO_EINVAL;
   cudaError_t e =
-      hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], dt, nullptr, c->scr, c->stream);
+      hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur],
+                      hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy), nullptr, c->scr, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "ctu_step");
   c->cur = 1 - c->cur;
   return HYDRO_OK;
@@ -235,8 +248,8 @@ hydro_status hydro_cfl_dt_async(hydro_ctx* c, double tmax) {
 
 hydro_status hydro_step_device_dt(hydro_ctx* c) {
   if (!c) return HYDRO_EINVAL;
-  cudaError_t e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], 0.0, &c->scr->dt,
-                                  c->scr, c->stream);
+  cudaError_t e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], hydro::StepScalars{},
+                                  &c->scr->sc, c->scr, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step_device_dt");
   c->cur = 1 - c->cur;
   return HYDRO_OK;
@@ -248,8 +261,8 @@ hydro_status hydro_advance(hydro_ctx* c, int nsteps, double tmax) {
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
     if (e == cudaSuccess)
-      e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], 0.0, &c->scr->dt, c->scr,
-                          c->stream);
+      e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], hydro::StepScalars{},
+                          &c->scr->sc, c->scr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "advance");
     c->cur = 1 - c->cur;
   }

@@ -1,11 +1,11 @@
 // Device-side building blocks of the unsplit CTU step (paper §3.2; CTU construction of §3.1), templated
 // on the arithmetic type R (double for the FP64 path, float for the FP32 path).
 //
-// Each function states the passage it implements.  For R = double the operations are written in the same
-// association order as a plain left-to-right evaluation of the formulas, so results differ from a
-// reference evaluation only by FMA contraction.  For R = float, divisions and square roots use the fast
-// hardware approximations (a few ulp), and the internal-energy recovery is done in double where the
-// kinetic energy is within 0.1% of the total energy.
+// Each function states the passage it implements.  For R = double the operations follow the formulas
+// left to right, so results differ from a plain evaluation only by FMA contraction.  For R = float the
+// same quantities are formed from hardware reciprocal and reciprocal-square-root approximations
+// (a few ulp), sharing one reciprocal wherever a formula divides twice by the same value, and the
+// internal energy is recovered in double where the kinetic energy is within 0.1% of the total energy.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,7 +28,30 @@ struct KParams {
   int riemann_maxiter;
   double riemann_tol;
   double small_dens, small_pres;
+  // float copies (filled on the host) so the FP32 kernels never convert from double
+  float gamma_f, gm1_f, igm1_f, g1_f, small_dens_f, small_pres_f, tol_f, cvisc_f, dx_f, dy_f, idx_f, idy_f;
 };
+
+// Time-step dependent factors of one CTU step, computed once in double (host, or the last block of
+// the dt reduction) so the kernels do no double division: sig = dt/dx, h = dt/(2dx), as in Eqs. 3-5.
+struct StepScalars {
+  double dt, sigx, sigy, hx, hy;
+  float sigx_f, sigy_f, hx_f, hy_f;
+};
+
+__host__ __device__ inline StepScalars make_step_scalars(double dt, double dx, double dy) {
+  StepScalars s;
+  s.dt = dt;
+  s.sigx = dt / dx;
+  s.sigy = dt / dy;
+  s.hx = 0.5 * dt / dx;
+  s.hy = 0.5 * dt / dy;
+  s.sigx_f = (float)s.sigx;
+  s.sigy_f = (float)s.sigy;
+  s.hx_f = (float)s.hx;
+  s.hy_f = (float)s.hy;
+  return s;
+}
 
 // Scratch words the kernels share with the host, one block per context (device memory).
 struct DevScratch {
@@ -36,6 +59,7 @@ struct DevScratch {
   unsigned int dt_blocks_done;     // last-block detection of the dt reduction
   unsigned int tot_blocks_done;    // last-block detection of the totals reduction
   double dt;                       // last reduced (and clamped) time step
+  StepScalars sc;                  // factors of that time step
   double t;                        // simulated time (device driver loop)
   long long nsteps;                // steps taken
   unsigned int status;             // bit flags, see STATUS_*
@@ -49,6 +73,11 @@ enum : unsigned int {
   STATUS_NEGATIVE = 2u,
   STATUS_NONCONV = 4u,
 };
+
+template <typename R>
+constexpr bool is_f32() {
+  return std::is_same<R, float>::value;
+}
 
 // ---------------------------------------------------------------------------------------------------
 // arithmetic helpers per precision
@@ -66,7 +95,7 @@ struct M<double> {
 
 template <>
 struct M<float> {
-  // arguments are strictly positive wherever sq is used (floored pressures and densities)
+  // arguments are strictly positive wherever sq / rs are used (floored pressures and densities)
   static __device__ __forceinline__ float sq(float x) { return x * rsqrtf(x); }
   static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float mn(float a, float b) { return fminf(a, b); }
@@ -74,43 +103,60 @@ struct M<float> {
   static __device__ __forceinline__ float ab(float a) { return fabsf(a); }
 };
 
+// approximate reciprocal (MUFU.RCP) for the FP32 path
+__device__ __forceinline__ float rcpa(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Per-precision copies of the scalar parameters used in the stencil.
 template <typename R>
 struct SP {
-  R gamma, gm1, g1, small_dens, small_pres, tol, cvisc;
+  R gamma, gm1, igm1, g1, small_dens, small_pres, tol, cvisc, dx, dy, idx, idy;
   int maxiter, limiter, flatten;
   __device__ __forceinline__ void load(const KParams& P) {
-    gamma = (R)P.gamma;
-    gm1 = (R)P.gm1;
-    g1 = (R)P.g1;
-    small_dens = (R)P.small_dens;
-    small_pres = (R)P.small_pres;
-    tol = (R)P.riemann_tol;
-    cvisc = (R)P.cvisc;
+    if constexpr (is_f32<R>()) {
+      gamma = P.gamma_f; gm1 = P.gm1_f; igm1 = P.igm1_f; g1 = P.g1_f; small_dens = P.small_dens_f;
+      small_pres = P.small_pres_f; tol = P.tol_f; cvisc = P.cvisc_f; dx = P.dx_f; dy = P.dy_f;
+      idx = P.idx_f; idy = P.idy_f;
+    } else {
+      gamma = P.gamma; gm1 = P.gm1; igm1 = 0.0; g1 = P.g1; small_dens = P.small_dens; small_pres = P.small_pres;
+      tol = P.riemann_tol; cvisc = P.cvisc; dx = P.dx; dy = P.dy; idx = 0.0; idy = 0.0;
+    }
     maxiter = P.riemann_maxiter;
     limiter = P.limiter;
     flatten = P.use_flattening;
   }
 };
 
+template <typename R>
+__device__ __forceinline__ bool finite4(R a, R b, R c, R d) {
+  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+
 // ---------------------------------------------------------------------------------------------------
 // EOS (Eqs. 11-12): conserved (rho, mx, my, E) -> primitive (rho, u, v, p), floors on the copy.
 template <typename R>
 __device__ __forceinline__ void cons_to_prim(const SP<R>& s, R U0, R U1, R U2, R U3, R& rho, R& u, R& v, R& p) {
   rho = U0 < s.small_dens ? s.small_dens : U0;
-  u = M<R>::dv(U1, rho);
-  v = M<R>::dv(U2, rho);
-  R ke = (R)0.5 * rho * (u * u + v * v);
-  if constexpr (std::is_same<R, float>::value) {
+  if constexpr (is_f32<R>()) {
+    const float ir = rcpa(rho);
+    u = U1 * ir;
+    v = U2 * ir;
+    const float ke = 0.5f * rho * (u * u + v * v);
     if (ke > 0.999f * U3) {
       // kinetic energy within 0.1% of the total: recover e = E - rho |u|^2 / 2 in double
-      double rd = (double)rho, ud = (double)U1 / rd, vd = (double)U2 / rd;
-      double ked = 0.5 * rd * (ud * ud + vd * vd);
+      const double rd = (double)rho, ud = (double)U1 / rd, vd = (double)U2 / rd;
+      const double ked = 0.5 * rd * (ud * ud + vd * vd);
       p = (float)(((double)s.gm1) * ((double)U3 - ked));
     } else {
       p = s.gm1 * (U3 - ke);
     }
   } else {
+    u = U1 / rho;
+    v = U2 / rho;
+    const double ke = 0.5 * rho * (u * u + v * v);
     p = s.gm1 * (U3 - ke);
   }
   p = p < s.small_pres ? s.small_pres : p;
@@ -122,7 +168,10 @@ __device__ __forceinline__ void prim_to_cons(const SP<R>& s, R rho, R u, R v, R 
   U0 = rho;
   U1 = rho * u;
   U2 = rho * v;
-  U3 = M<R>::dv(p, s.gm1) + (R)0.5 * rho * (u * u + v * v);
+  if constexpr (is_f32<R>())
+    U3 = p * s.igm1 + 0.5f * rho * (u * u + v * v);
+  else
+    U3 = p / s.gm1 + 0.5 * rho * (u * u + v * v);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -153,12 +202,18 @@ template <typename R>
 __device__ __forceinline__ R flatten_chi(R pm2, R pm1, R pp1, R pp2, R um1, R up1, R small_pres) {
   const R z0 = (R)0.75, z1 = (R)0.85, delta = (R)0.33;
   R dp1 = pp1 - pm1;
-  R dp2 = pp2 - pm2;
-  R z = M<R>::dv(M<R>::ab(dp1), M<R>::mx(M<R>::ab(dp2), small_pres));
   bool compress = (um1 - up1) > (R)0;
   bool jump = M<R>::ab(dp1) > delta * M<R>::mn(pp1, pm1);
   if (!(compress && jump)) return (R)1;
-  R chi = (R)1 - M<R>::dv(z - z0, z1 - z0);
+  R dp2 = pp2 - pm2;
+  R chi;
+  if constexpr (is_f32<R>()) {
+    const float z = M<float>::ab(dp1) * rcpa(M<float>::mx(M<float>::ab(dp2), small_pres));
+    chi = 1.0f - (z - z0) * (1.0f / (0.85f - 0.75f));
+  } else {
+    R z = M<R>::ab(dp1) / M<R>::mx(M<R>::ab(dp2), small_pres);
+    chi = (R)1 - (z - z0) / (z1 - z0);
+  }
   chi = chi < (R)0 ? (R)0 : chi;
   chi = chi > (R)1 ? (R)1 : chi;
   return chi;
@@ -175,13 +230,26 @@ __device__ __forceinline__ R flatten_chi(R pm2, R pm1, R pp1, R pp2, R um1, R up
 template <typename R>
 __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], const R dq[4], R qL[4], R qR[4]) {
   const R rho = q[0], un = q[1], pres = q[3];
-  const R c = M<R>::sq(M<R>::dv(s.gamma * pres, rho));
+  R c, c2, roc, ic2h, ic2, cor;
+  if constexpr (is_f32<R>()) {
+    const float ir = rcpa(rho);
+    const float x = s.gamma * pres * ir;  // c^2
+    const float ic = rsqrtf(x);           // 1/c
+    c = x * ic;
+    c2 = c * c;
+    roc = 0.5f * rho * ic;
+    ic2 = ic * ic;
+    ic2h = 0.5f * ic2;
+    cor = c * ir;
+  } else {
+    c = sqrt(s.gamma * pres / rho);
+    c2 = c * c;
+    roc = (0.5 * rho) / c;
+    ic2h = 0.5 / c2;
+    ic2 = 1.0 / c2;
+    cor = c / rho;
+  }
   const R lam1 = un - c, lam2 = un, lam4 = un + c;
-  const R c2 = c * c;
-  const R roc = M<R>::dv((R)0.5 * rho, c);  // rho / 2c
-  const R ic2h = M<R>::dv((R)0.5, c2);      // 1 / 2c^2
-  const R ic2 = M<R>::dv((R)1, c2);         // 1 / c^2
-  const R cor = M<R>::dv(c, rho);           // c / rho
   const R b1 = -roc * dq[1] + ic2h * dq[3];
   const R b2 = dq[0] + (-ic2) * dq[3];
   const R b3 = dq[2];
@@ -226,34 +294,47 @@ __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], con
 }
 
 // ---------------------------------------------------------------------------------------------------
+// Euler flux (Eqs. 8-10, g = 0) of a face state (rho, un, ut, p): (rho un, rho un^2 + p, rho un ut, un (rho E + p)).
+template <typename R>
+__device__ __forceinline__ void face_flux(const SP<R>& s, R fr, R fu, R fv, R fp, R F[4]) {
+  R rhoE;
+  if constexpr (is_f32<R>())
+    rhoE = fp * s.igm1 + 0.5f * fr * (fu * fu + fv * fv);
+  else
+    rhoE = fp / s.gm1 + 0.5 * fr * (fu * fu + fv * fv);
+  F[0] = fr * fu;
+  F[1] = fr * fu * fu + fp;
+  F[2] = fr * fu * fv;
+  F[3] = fu * (rhoE + fp);
+}
+
 // Two-shock Riemann solver (§3.2, "the Riemann solver described in almgren:2010").
 // Face frame: (rho, un, ut, p).  Newton iteration on u*_L(p) = u*_R(p) with the shock mass fluxes
 // W_K = C_K sqrt(1 + (gamma+1)/(2 gamma) (p/p_K - 1)), C_K = sqrt(gamma p_K rho_K), slopes
 // Z_K = 2 W_K^3 / (W_K^2 + C_K^2); acoustic start unless guess > 0.  Sampling at x/t = 0 from the upwind
 // side of the contact, Hugoniot star density, shock or linearly interpolated fan.  Returns the flux
 // (mass, normal momentum, transverse momentum, energy); iters/conv report the iteration.
-template <typename R>
-__device__ __forceinline__ void riemann(const SP<R>& s, const R qL[4], const R qR[4], R guess, R F[4], int& iters,
-                                        bool& conv) {
-  const R g = s.gamma, g1 = s.g1;
-  const R rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
-  const R rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
-  const R cl = M<R>::sq(g * pl * rl);
-  const R cr = M<R>::sq(g * pr * rr);
-  R pst = guess > (R)0 ? guess : M<R>::dv(cr * pl + cl * pr + cl * cr * (ul - ur), cl + cr);
+__device__ __forceinline__ void riemann(const SP<double>& s, const double qL[4], const double qR[4], double guess,
+                                        double F[4], int& iters, bool& conv) {
+  const double g = s.gamma, g1 = s.g1;
+  const double rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
+  const double rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
+  const double cl = sqrt(g * pl * rl);
+  const double cr = sqrt(g * pr * rr);
+  double pst = guess > 0.0 ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) / (cl + cr);
   pst = pst < s.small_pres ? s.small_pres : pst;
   int it = 0;
   bool ok = false;
   while (it < s.maxiter) {
-    R wl = cl * M<R>::sq((R)1 + g1 * (M<R>::dv(pst, pl) - (R)1));
-    R wr = cr * M<R>::sq((R)1 + g1 * (M<R>::dv(pst, pr) - (R)1));
-    R usl = ul - M<R>::dv(pst - pl, wl);
-    R usr = ur + M<R>::dv(pst - pr, wr);
-    R zl = M<R>::dv((R)2 * wl * wl * wl, wl * wl + cl * cl);
-    R zr = M<R>::dv((R)2 * wr * wr * wr, wr * wr + cr * cr);
-    R pnew = pst - M<R>::dv(zl * zr * (usr - usl), zl + zr);
+    double wl = cl * sqrt(1.0 + g1 * (pst / pl - 1.0));
+    double wr = cr * sqrt(1.0 + g1 * (pst / pr - 1.0));
+    double usl = ul - (pst - pl) / wl;
+    double usr = ur + (pst - pr) / wr;
+    double zl = 2.0 * wl * wl * wl / (wl * wl + cl * cl);
+    double zr = 2.0 * wr * wr * wr / (wr * wr + cr * cr);
+    double pnew = pst - zl * zr * (usr - usl) / (zl + zr);
     pnew = pnew < s.small_pres ? s.small_pres : pnew;
-    R dp = M<R>::ab(pnew - pst);
+    double dp = fabs(pnew - pst);
     pst = pnew;
     ++it;
     if (dp <= s.tol * pst) {
@@ -263,52 +344,132 @@ __device__ __forceinline__ void riemann(const SP<R>& s, const R qL[4], const R q
   }
   iters = it;
   conv = ok;
-  const R wl = cl * M<R>::sq((R)1 + g1 * (M<R>::dv(pst, pl) - (R)1));
-  const R wr = cr * M<R>::sq((R)1 + g1 * (M<R>::dv(pst, pr) - (R)1));
-  const R ust = M<R>::dv((wl * ul + wr * ur) + (pl - pr), wl + wr);
+  const double wl = cl * sqrt(1.0 + g1 * (pst / pl - 1.0));
+  const double wr = cr * sqrt(1.0 + g1 * (pst / pr - 1.0));
+  const double ust = ((wl * ul + wr * ur) + (pl - pr)) / (wl + wr);
 
-  R fr, fu, fv, fp;
-  if (ust == (R)0) {
-    fr = (R)0.5 * (rl + rr);
-    fu = (R)0;
-    fv = (R)0.5 * (vl + vr);
+  double fr, fu, fv, fp;
+  if (ust == 0.0) {
+    fr = 0.5 * (rl + rr);
+    fu = 0.0;
+    fv = 0.5 * (vl + vr);
     fp = pst;
   } else {
-    const bool left = ust > (R)0;
-    const R sgn = left ? (R)1 : (R)-1;
-    const R ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
-    const R wo = left ? wl : wr;
-    const R rst = M<R>::dv((R)1, M<R>::dv((R)1, ro) - M<R>::dv(pst - po, wo * wo));
+    const bool left = ust > 0.0;
+    const double sgn = left ? 1.0 : -1.0;
+    const double ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
+    const double wo = left ? wl : wr;
+    const double rst = 1.0 / (1.0 / ro - (pst - po) / (wo * wo));
     fv = vo;
     if (pst > po) {
-      const R S = uo - sgn * M<R>::dv(wo, ro);
-      if (sgn * S >= (R)0) {
+      const double S = uo - sgn * (wo / ro);
+      if (sgn * S >= 0.0) {
         fr = ro; fu = uo; fp = po;
       } else {
         fr = rst; fu = ust; fp = pst;
       }
     } else {
-      const R co = M<R>::sq(M<R>::dv(g * po, ro));
-      const R cst = M<R>::sq(M<R>::dv(g * pst, rst));
-      const R SH = uo - sgn * co;
-      const R ST = ust - sgn * cst;
-      if (sgn * SH >= (R)0) {
+      const double co = sqrt(g * po / ro);
+      const double cst = sqrt(g * pst / rst);
+      const double SH = uo - sgn * co;
+      const double ST = ust - sgn * cst;
+      if (sgn * SH >= 0.0) {
         fr = ro; fu = uo; fp = po;
-      } else if (sgn * ST <= (R)0) {
+      } else if (sgn * ST <= 0.0) {
         fr = rst; fu = ust; fp = pst;
       } else {
-        const R frac = M<R>::dv(SH, SH - ST);
+        const double frac = SH / (SH - ST);
         fr = ro + frac * (rst - ro);
         fu = uo + frac * (ust - uo);
         fp = po + frac * (pst - po);
       }
     }
   }
-  const R rhoE = M<R>::dv(fp, s.gm1) + (R)0.5 * fr * (fu * fu + fv * fv);
-  F[0] = fr * fu;
-  F[1] = fr * fu * fu + fp;
-  F[2] = fr * fu * fv;
-  F[3] = fu * (rhoE + fp);
+  face_flux(s, fr, fu, fv, fp, F);
+}
+
+// FP32 form of the same solver.  With a_K = 1 + (gamma+1)/(2 gamma)(p/p_K - 1) and t_K = 1/sqrt(a_K):
+// 1/W_K = t_K / C_K, W_K = C_K a_K t_K, and the Newton step -(u*_R - u*_L) / (1/Z_L + 1/Z_R) uses
+// 1/Z_K = (a_K + 1) t_K^3 / (2 C_K); one rsqrt per side and one reciprocal per iteration.
+__device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], const float qR[4], float guess,
+                                        float F[4], int& iters, bool& conv) {
+  const float g = s.gamma, g1 = s.g1;
+  const float rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
+  const float rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
+  const float xl = g * pl * rl, xr = g * pr * rr;
+  const float icl = rsqrtf(xl), icr = rsqrtf(xr);  // 1/C_K
+  const float cl = xl * icl, cr = xr * icr;
+  const float ipl = rcpa(pl), ipr = rcpa(pr);
+  float pst = guess > 0.0f ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) * rcpa(cl + cr);
+  pst = pst < s.small_pres ? s.small_pres : pst;
+  int it = 0;
+  bool ok = false;
+  while (it < s.maxiter) {
+    const float al = 1.0f + g1 * (pst * ipl - 1.0f), ar = 1.0f + g1 * (pst * ipr - 1.0f);
+    const float tl = rsqrtf(al), tr = rsqrtf(ar);
+    const float iwl = tl * icl, iwr = tr * icr;
+    const float usl = ul - (pst - pl) * iwl;
+    const float usr = ur + (pst - pr) * iwr;
+    const float izl = 0.5f * (al + 1.0f) * tl * tl * iwl;
+    const float izr = 0.5f * (ar + 1.0f) * tr * tr * iwr;
+    float pnew = pst - (usr - usl) * rcpa(izl + izr);
+    pnew = pnew < s.small_pres ? s.small_pres : pnew;
+    const float dp = fabsf(pnew - pst);
+    pst = pnew;
+    ++it;
+    if (dp <= s.tol * pst) {
+      ok = true;
+      break;
+    }
+  }
+  iters = it;
+  conv = ok;
+  const float al = 1.0f + g1 * (pst * ipl - 1.0f), ar = 1.0f + g1 * (pst * ipr - 1.0f);
+  const float tl = rsqrtf(al), tr = rsqrtf(ar);
+  const float wl = cl * al * tl, wr = cr * ar * tr;
+  const float ust = ((wl * ul + wr * ur) + (pl - pr)) * rcpa(wl + wr);
+
+  float fr, fu, fv, fp;
+  if (ust == 0.0f) {
+    fr = 0.5f * (rl + rr);
+    fu = 0.0f;
+    fv = 0.5f * (vl + vr);
+    fp = pst;
+  } else {
+    const bool left = ust > 0.0f;
+    const float sgn = left ? 1.0f : -1.0f;
+    const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
+    const float wo = left ? wl : wr;
+    const float iwo = left ? tl * icl : tr * icr;
+    const float iro = rcpa(ro);
+    const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
+    const float rst = rcpa(irst);
+    fv = vo;
+    if (pst > po) {
+      const float S = uo - sgn * wo * iro;
+      if (sgn * S >= 0.0f) {
+        fr = ro; fu = uo; fp = po;
+      } else {
+        fr = rst; fu = ust; fp = pst;
+      }
+    } else {
+      const float co = M<float>::sq(g * po * iro);
+      const float cst = M<float>::sq(g * pst * irst);
+      const float SH = uo - sgn * co;
+      const float ST = ust - sgn * cst;
+      if (sgn * SH >= 0.0f) {
+        fr = ro; fu = uo; fp = po;
+      } else if (sgn * ST <= 0.0f) {
+        fr = rst; fu = ust; fp = pst;
+      } else {
+        const float frac = SH * rcpa(SH - ST);
+        fr = ro + frac * (rst - ro);
+        fu = uo + frac * (ust - uo);
+        fp = po + frac * (pst - po);
+      }
+    }
+  }
+  face_flux(s, fr, fu, fv, fp, F);
 }
 
 }  // namespace hydro

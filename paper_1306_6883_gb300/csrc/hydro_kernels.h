@@ -21,9 +21,9 @@ int totals_max_blocks();
 cudaError_t conserved_totals(int precision, const KParams& P, const void* U, double* partials, DevScratch* scr,
                              cudaStream_t stream);
 
-// One fused CTU step Uin -> Uout with dt from dt_dev if not NULL, else dt_host.
-cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, double dt_host,
-                     const double* dt_dev, DevScratch* scr, cudaStream_t stream);
+// One fused CTU step Uin -> Uout with the time-step factors from sc_dev if not NULL, else sc_host.
+cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
+                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
 
 // Scratch initialisation (min accumulator = +inf, counters 0).
 cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream);

@@ -70,17 +70,17 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
                                                            DevScratch* __restrict__ scr, double tmax, int advance) {
   SP<R> s;
   s.load(P);
-  const R dx = (R)P.dx, dy = (R)P.dy;
+  const R dx = s.dx, dy = s.dy;
   const size_t plane = (size_t)P.NY * P.pitch;
   const long long ncell = (long long)P.nx * P.ny;
-  double best = DBL_MAX;
+  R rbest = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
   unsigned int flags = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ncell;
        e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e / P.nx), i = (int)(e % P.nx);
     const size_t o = (size_t)(j + P.ng) * P.pitch + (i + P.ng);
     const R U0 = U[o], U1 = U[o + plane], U2 = U[o + 2 * plane], U3 = U[o + 3 * plane];
-    if (!(isfinite((double)U0) && isfinite((double)U1) && isfinite((double)U2) && isfinite((double)U3))) {
+    if (!finite4(U0, U1, U2, U3)) {
       flags |= STATUS_NONFINITE;
       continue;
     }
@@ -93,15 +93,17 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
     const R cs = M<R>::sq(M<R>::dv(s.gamma * p, rho));
     const R tx = M<R>::dv(dx, M<R>::ab(u) + cs);
     const R ty = M<R>::dv(dy, M<R>::ab(v) + cs);
-    const double t = (double)M<R>::mn(tx, ty);
-    best = t < best ? t : best;
+    const R t = M<R>::mn(tx, ty);
+    rbest = t < rbest ? t : rbest;
   }
+  // the minimum of the per-cell values is exact in their own precision; promote once
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const double o = __shfl_xor_sync(0xffffffffu, best, off);
-    best = o < best ? o : best;
+    const R o = __shfl_xor_sync(0xffffffffu, rbest, off);
+    rbest = o < rbest ? o : rbest;
     flags |= __shfl_xor_sync(0xffffffffu, flags, off);
   }
+  const double best = (double)rbest;
   __shared__ double wmin[DT_THREADS / 32];
   __shared__ unsigned int wflags[DT_THREADS / 32];
   __shared__ bool last;
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
       dt = dt < 0.0 ? 0.0 : dt;
     }
     scr->dt = dt;
+    scr->sc = make_step_scalars(dt, P.dx, P.dy);
     if (advance) {
       scr->t = scr->t + dt;
       scr->nsteps = scr->nsteps + 1;

@@ -10,6 +10,10 @@
 //   5. conservative update (Eq. 5), written to the other state buffer
 // Global traffic per cell is one read of U (plus the halo and an L1/L2 re-read of U^n at the faces for
 // the viscosity term) and one write of U^{n+1}.
+//
+// Shared memory is reused across stages: the hat fluxes of stage 3 overwrite the primitive tile (dead
+// after stage 2; the velocities the viscosity needs are kept separately), and each final flux of stage 4
+// overwrites the left traced state that only its own face reads.
 #include "hydro_device.cuh"
 #include "hydro_kernels.h"
 
@@ -19,45 +23,45 @@ template <typename R, int TX, int TY>
 struct TileLayout {
   static constexpr int QX = TX + 8, QY = TY + 8;  // primitive tile with a 4-cell halo
   static constexpr int SX = TX + 2, SY = TY + 2;  // cells whose face states are traced
+  static constexpr int nC = SX * SY;
   static constexpr int nQ = 4 * QX * QY;
-  static constexpr int nXI = SX * SY;
-  static constexpr int nS = 4 * SX * SY;          // one traced-state family
   static constexpr int nFXH = 4 * SY * (TX + 1);  // hat x fluxes: rows [3, TY+5), faces [4, TX+5)
   static constexpr int nFYH = 4 * (TY + 1) * SX;  // hat y fluxes: faces [4, TY+5), columns [3, TX+5)
-  static constexpr int nFX = 4 * TY * (TX + 1);   // final x fluxes of the tile
-  static constexpr int nFY = 4 * (TY + 1) * TX;   // final y fluxes of the tile
-  static constexpr size_t bytes = sizeof(R) * (size_t)(nQ + nXI + 4 * nS + nFXH + nFYH + nFX + nFY);
+  static constexpr int nA = (nQ + nC) > (nFXH + nFYH) ? (nQ + nC) : (nFXH + nFYH);  // region A
+  static constexpr int nS = 4 * nC;               // one traced-state family
+  static constexpr int elems = nA + 4 * nS + 2 * nC;
+  static constexpr size_t bytes = sizeof(R) * (size_t)elems;
 };
-
-template <typename R, int TX, int TY>
-size_t ctu_smem_bytes() {
-  return TileLayout<R, TX, TY>::bytes;
-}
 
 template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
-                                                      double dt_host, const double* __restrict__ dt_dev,
+                                                      StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
                                                       DevScratch* __restrict__ scr) {
   using L = TileLayout<R, TX, TY>;
-  constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY;
+  constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sq = reinterpret_cast<R*>(smem_raw);  // [4][QY][QX]
-  R* sxi = sq + L::nQ;                      // [SY][SX]
-  R* sxl = sxi + L::nXI;                    // [4][SY][SX] left state at i+1/2 of each cell
+  R* sq = reinterpret_cast<R*>(smem_raw);  // region A, stages 0-2: [4][QY][QX] primitives
+  R* sxi = sq + L::nQ;                      //                         [SY][SX] flattening
+  R* sfxh = sq;                             // region A, stages 3-4: [4][SY][TX+1] hat x fluxes
+  R* sfyh = sq + L::nFXH;                   //                         [4][TY+1][SX] hat y fluxes
+  R* sxl = sq + L::nA;                      // [4][SY][SX] left state at i+1/2 of each cell (then final Fx)
   R* sxr = sxl + L::nS;                     // right state at i-1/2
-  R* syl = sxr + L::nS;                     // lower state at j+1/2 (frame rho, u, v, p)
+  R* syl = sxr + L::nS;                     // lower state at j+1/2 (then final Fy)
   R* syr = syl + L::nS;                     // upper state at j-1/2
-  R* sfxh = syr + L::nS;                    // [4][SY][TX+1]
-  R* sfyh = sfxh + L::nFXH;                 // [4][TY+1][SX]
-  R* sfx = sfyh + L::nFYH;                  // [4][TY][TX+1]
-  R* sfy = sfx + L::nFX;                    // [4][TY+1][TX]
+  R* su = syr + L::nS;                      // [SY][SX] cell velocities for the viscosity
+  R* sv = su + nC;
 
   SP<R> s;
   s.load(P);
-  const double dt = dt_dev ? *dt_dev : dt_host;
-  const R sigx = (R)(dt / P.dx), sigy = (R)(dt / P.dy);
-  const R hx = (R)(0.5 * dt / P.dx), hy = (R)(0.5 * dt / P.dy);
-  const R idx = (R)P.dx, idy = (R)P.dy, idy4 = (R)(4.0 * P.dy), idx4 = (R)(4.0 * P.dx);
+  const StepScalars sc = sc_dev ? *sc_dev : sc_host;
+  R sigx, sigy, hx, hy, ux, uy;
+  if constexpr (is_f32<R>()) {
+    sigx = sc.sigx_f; sigy = sc.sigy_f; hx = sc.hx_f; hy = sc.hy_f;
+  } else {
+    sigx = sc.sigx; sigy = sc.sigy; hx = sc.hx; hy = sc.hy;
+  }
+  ux = sigx;  // update factors dt/dx, dt/dy (Eq. 5)
+  uy = sigy;
 
   const int tid = threadIdx.x;
   const int x0 = P.ng + blockIdx.x * TX;  // padded column of the first interior cell of the tile
@@ -72,7 +76,8 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
     gj = gj < P.NY - 1 ? gj : P.NY - 1;
     const size_t o = (size_t)gj * P.pitch + gi;
     R rho, u, v, p;
-    cons_to_prim(s, Uin[o], Uin[o + plane], Uin[o + 2 * plane], Uin[o + 3 * plane], rho, u, v, p);
+    cons_to_prim(s, __ldg(Uin + o), __ldg(Uin + o + plane), __ldg(Uin + o + 2 * plane), __ldg(Uin + o + 3 * plane),
+                 rho, u, v, p);
     sq[e] = rho;
     sq[QX * QY + e] = u;
     sq[2 * QX * QY + e] = v;
@@ -83,12 +88,12 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
   const R* qu = sq + QX * QY;
   const R* qv = sq + 2 * QX * QY;
   const R* qp = sq + 3 * QX * QY;
-  // ---- 1. flattening xi = min(xi_x, xi_y) on cells lx in [3, TX+5), ly in [3, TY+5)
-  for (int e = tid; e < SX * SY; e += NT) {
+  // ---- 1. flattening xi = min(xi_x, xi_y) on cells lx in [3, TX+5), ly in [3, TY+5); keep u, v there
+  for (int e = tid; e < nC; e += NT) {
     const int cx = e % SX + 3, cy = e / SX + 3;
+    const int b = cy * QX + cx;
     R xi = (R)1;
     if (s.flatten) {
-      const int b = cy * QX + cx;
       auto chix = [&](int m) {
         return flatten_chi<R>(qp[b + m - 2], qp[b + m - 1], qp[b + m + 1], qp[b + m + 2], qu[b + m - 1], qu[b + m + 1],
                               s.small_pres);
@@ -104,49 +109,47 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
       xi = M<R>::mn(xix, xiy);
     }
     sxi[e] = xi;
+    su[e] = qu[b];
+    sv[e] = qv[b];
   }
   __syncthreads();
 
   // ---- 2. slopes + tracing for the same cells; items [0, nC) trace in x, [nC, 2 nC) in y
-  {
-    constexpr int nC = SX * SY;
-    for (int e = tid; e < 2 * nC; e += NT) {
-      const bool ydir = e >= nC;
-      const int c = ydir ? e - nC : e;
-      const int cx = c % SX + 3, cy = c / SX + 3;
-      const int b = cy * QX + cx;
-      const int st = ydir ? QX : 1;
-      const R xi = sxi[c];
-      R q[4], dq[4];
-      // face frame: (rho, un, ut, p); in y un = v, ut = u
-      const int kmap[4] = {0, ydir ? 2 : 1, ydir ? 1 : 2, 3};
+  for (int e = tid; e < 2 * nC; e += NT) {
+    const bool ydir = e >= nC;
+    const int c = ydir ? e - nC : e;
+    const int cx = c % SX + 3, cy = c / SX + 3;
+    const int b = cy * QX + cx;
+    const int st = ydir ? QX : 1;
+    const R xi = sxi[c];
+    R q[4], dq[4];
+    // face frame: (rho, un, ut, p); in y un = v, ut = u
+    const int kmap[4] = {0, ydir ? 2 : 1, ydir ? 1 : 2, 3};
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const R* a = sq + kmap[m] * QX * QY + b;
-        q[m] = a[0];
-        dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
-      }
-      R ql[4], qrr[4];
-      trace<R>(s, ydir ? sigy : sigx, q, dq, ql, qrr);
-      R* dl = ydir ? syl : sxl;
-      R* dr = ydir ? syr : sxr;
-      // store in (rho, u, v, p) order
+    for (int m = 0; m < 4; ++m) {
+      const R* a = sq + kmap[m] * QX * QY + b;
+      q[m] = a[0];
+      dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+    }
+    R ql[4], qrr[4];
+    trace<R>(s, ydir ? sigy : sigx, q, dq, ql, qrr);
+    R* dl = ydir ? syl : sxl;
+    R* dr = ydir ? syr : sxr;
+    // store in (rho, u, v, p) order
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        dl[kmap[m] * nC + c] = ql[m];
-        dr[kmap[m] * nC + c] = qrr[m];
-      }
+    for (int m = 0; m < 4; ++m) {
+      dl[kmap[m] * nC + c] = ql[m];
+      dr[kmap[m] * nC + c] = qrr[m];
     }
   }
   __syncthreads();
 
-  unsigned long long n_solves = 0, n_iters = 0, n_nonconv = 0;
+  unsigned int n_solves = 0, n_iters = 0, n_nonconv = 0;
 
   // ---- 3. hat Riemann solves.  x faces: lx in [4, TX+5) between cells lx-1 and lx, rows [3, TY+5).
-  //         y faces: ly in [4, TY+5), columns [3, TX+5).
+  //         y faces: ly in [4, TY+5), columns [3, TX+5).  Results overwrite region A.
   {
     constexpr int nXF = (TX + 1) * SY, nYF = (TY + 1) * SX;
-    constexpr int nC = SX * SY;
     for (int e = tid; e < nXF + nYF; e += NT) {
       R a[4], bq[4], F[4];
       int it;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
           a[m] = sxl[m * nC + cL];
           bq[m] = sxr[m * nC + cR];
         }
-        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        riemann(s, a, bq, (R)0, F, it, ok);
 #pragma unroll
         for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
       } else {
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
         const int cR = cL + SX;
         a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
         bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
-        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        riemann(s, a, bq, (R)0, F, it, ok);
         const int o = fy * SX + cxs;
         sfyh[0 * (TY + 1) * SX + o] = F[0];
         sfyh[1 * (TY + 1) * SX + o] = F[2];
@@ -186,7 +189,6 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
 
   // ---- 4. transverse correction + final solves + artificial viscosity at the tile's faces
   {
-    constexpr int nC = SX * SY;
     constexpr int nXF = (TX + 1) * TY, nYF = (TY + 1) * TX;
     for (int e = tid; e < nXF + nYF; e += NT) {
       R a[4], bq[4], F[4], UL[4], UR[4];
@@ -207,23 +209,23 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
         }
         cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
         cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
-        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        riemann(s, a, bq, (R)0, F, it, ok);
         // artificial viscosity from the cell-centred velocities of the time-n state
-        const int lx = fx + 4, ly = ty + 4;
-        const int b = ly * QX + lx;
-        const R div = M<R>::dv(qu[b] - qu[b - 1], idx) +
-                      M<R>::dv(qv[b + QX] + qv[b + QX - 1] - qv[b - QX] - qv[b - QX - 1], idy4);
-        const R av = s.cvisc * M<R>::mx(-div * idx, (R)0);
         if (s.cvisc > (R)0) {
-          int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
-          gi = gi < P.NX - 1 ? gi : P.NX - 1;
-          gj = gj < P.NY - 1 ? gj : P.NY - 1;
-          const size_t o = (size_t)gj * P.pitch + gi;
+          R div;
+          const R dvy = sv[cR + SX] + sv[cL + SX] - sv[cR - SX] - sv[cL - SX];
+          if constexpr (is_f32<R>())
+            div = (su[cR] - su[cL]) * s.idx + dvy * (0.25f * s.idy);
+          else
+            div = (su[cR] - su[cL]) / s.dx + dvy / (4.0 * s.dy);
+          const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
+          const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx (may be clamped)
+          const size_t o = (size_t)(gj < P.NY - 1 ? gj : P.NY - 1) * P.pitch + (gi < P.NX - 1 ? gi : P.NX - 1);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) F[k] += av * (Uin[o - 1 + k * plane] - Uin[o + k * plane]);
+          for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + o - 1 + k * plane) - __ldg(Uin + o + k * plane));
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sfx[(k * TY + ty) * (TX + 1) + fx] = F[k];
+        for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = F[k];  // only this face read sxl[cL]
       } else {
         const int f = e - nXF;
         const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
@@ -243,23 +245,24 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
         cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], qrr[0], qrr[1], qrr[2], qrr[3]);
         a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
         bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
-        riemann<R>(s, a, bq, (R)0, F, it, ok);
+        riemann(s, a, bq, (R)0, F, it, ok);
         R G[4] = {F[0], F[2], F[1], F[3]};
-        const int lx = tx + 4, ly = fy + 4;
-        const int b = ly * QX + lx;
-        const R div = M<R>::dv(qv[b] - qv[b - QX], idy) +
-                      M<R>::dv(qu[b + 1] + qu[b - QX + 1] - qu[b - 1] - qu[b - QX - 1], idx4);
-        const R av = s.cvisc * M<R>::mx(-div * idy, (R)0);
         if (s.cvisc > (R)0) {
-          int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
-          gi = gi < P.NX - 1 ? gi : P.NX - 1;
-          gj = gj < P.NY - 1 ? gj : P.NY - 1;
-          const size_t o = (size_t)gj * P.pitch + gi;
+          R div;
+          const R dux = (su[cR + 1] + su[cL + 1] - su[cR - 1] - su[cL - 1]);
+          if constexpr (is_f32<R>())
+            div = (sv[cR] - sv[cL]) * s.idy + dux * (0.25f * s.idx);
+          else
+            div = (sv[cR] - sv[cL]) / s.dy + dux / (4.0 * s.dx);
+          const R av = s.cvisc * M<R>::mx(-div * s.dy, (R)0);
+          const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
+          const size_t o = (size_t)(gj < P.NY - 1 ? gj : P.NY - 1) * P.pitch + (gi < P.NX - 1 ? gi : P.NX - 1);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) G[k] += av * (Uin[o - P.pitch + k * plane] - Uin[o + k * plane]);
+          for (int k = 0; k < 4; ++k)
+            G[k] += av * (__ldg(Uin + o - P.pitch + k * plane) - __ldg(Uin + o + k * plane));
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sfy[(k * (TY + 1) + fy) * TX + tx] = G[k];
+        for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
       }
       n_solves++;
       n_iters += it;
@@ -270,35 +273,31 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
 
   // ---- 5. conservative update of the tile's valid cells
   unsigned int flags = 0;
-  {
-    const R sx = (R)(dt / P.dx), sy = (R)(dt / P.dy);
-    for (int e = tid; e < TX * TY; e += NT) {
-      const int tx = e % TX, ty = e / TX;
-      const int gi = x0 + tx, gj = y0 + ty;
-      if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
-      const size_t o = (size_t)gj * P.pitch + gi;
-      R Un[4];
+  for (int e = tid; e < TX * TY; e += NT) {
+    const int tx = e % TX, ty = e / TX;
+    const int gi = x0 + tx, gj = y0 + ty;
+    if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
+    const size_t o = (size_t)gj * P.pitch + gi;
+    const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
+    const int cy = ty * SX + tx + 1;    // final y flux of face ty (below the cell) lives in syl[cy]
+    R Un[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const R* fx = sfx + k * TY * (TX + 1);
-        const R* fy = sfy + k * (TY + 1) * TX;
-        const R d = sx * (fx[ty * (TX + 1) + tx] - fx[ty * (TX + 1) + tx + 1]) +
-                    sy * (fy[ty * TX + tx] - fy[(ty + 1) * TX + tx]);
-        Un[k] = Uin[o + k * plane] + d;
-        Uout[o + k * plane] = Un[k];
-      }
-      const bool finite = isfinite((double)Un[0]) && isfinite((double)Un[1]) && isfinite((double)Un[2]) &&
-                          isfinite((double)Un[3]);
-      if (!finite) {
-        flags |= STATUS_NONFINITE;
-      } else {
-        const R ke = M<R>::dv((R)0.5 * (Un[1] * Un[1] + Un[2] * Un[2]), Un[0]);
-        if (!(Un[0] > (R)0) || !(Un[3] - ke > (R)0)) flags |= STATUS_NEGATIVE;
-      }
+    for (int k = 0; k < 4; ++k) {
+      const R* fx = sxl + k * nC;
+      const R* fy = syl + k * nC;
+      const R d = ux * (fx[cx] - fx[cx + 1]) + uy * (fy[cy] - fy[cy + SX]);
+      Un[k] = __ldg(Uin + o + k * plane) + d;
+      Uout[o + k * plane] = Un[k];
+    }
+    if (!finite4(Un[0], Un[1], Un[2], Un[3])) {
+      flags |= STATUS_NONFINITE;
+    } else {
+      const R ke = M<R>::dv((R)0.5 * (Un[1] * Un[1] + Un[2] * Un[2]), Un[0]);
+      if (!(Un[0] > (R)0) || !(Un[3] - ke > (R)0)) flags |= STATUS_NEGATIVE;
     }
   }
 
-  // ---- per-block reduction of the counters, one atomic per block
+  // ---- per-block reduction of the counters, one atomic per warp
   if (n_nonconv) flags |= STATUS_NONCONV;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -308,18 +307,18 @@ __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __rest
     flags |= __shfl_xor_sync(0xffffffffu, flags, off);
   }
   if ((tid & 31) == 0) {
-    atomicAdd(&scr->stats[0], n_solves);
-    atomicAdd(&scr->stats[1], n_iters);
-    if (n_nonconv) atomicAdd(&scr->stats[2], n_nonconv);
+    atomicAdd(&scr->stats[0], (unsigned long long)n_solves);
+    atomicAdd(&scr->stats[1], (unsigned long long)n_iters);
+    if (n_nonconv) atomicAdd(&scr->stats[2], (unsigned long long)n_nonconv);
     if (flags) atomicOr(&scr->status, flags);
   }
 }
 
 template <typename R, int TX, int TY, int NT>
-cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, double dt_host, const double* dt_dev,
-                            DevScratch* scr, cudaStream_t stream) {
-  const size_t smem = ctu_smem_bytes<R, TX, TY>();
-  static bool attr_set = false;  // per instantiation; set before first launch on any device
+cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
+                            const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream) {
+  const size_t smem = TileLayout<R, TX, TY>::bytes;
+  static bool attr_set = false;  // per instantiation; the attribute is per function, not per device
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -327,15 +326,15 @@ cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, double dt_h
     attr_set = true;
   }
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, dt_host, dt_dev, scr);
+  ctu_step_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr);
   return cudaGetLastError();
 }
 
-cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, double dt_host, const double* dt_dev,
-                     DevScratch* scr, cudaStream_t stream) {
+cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
+                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream) {
   if (precision == 0)
-    return launch_ctu_step<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, dt_host, dt_dev, scr, stream);
-  return launch_ctu_step<float, 32, 16, 256>(P, (const float*)Uin, (float*)Uout, dt_host, dt_dev, scr, stream);
+    return launch_ctu_step<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev, scr, stream);
+  return launch_ctu_step<float, 32, 16, 256>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev, scr, stream);
 }
 
 }  // namespace hydro
