@@ -169,6 +169,51 @@ hydro_status hydro_sync_status(hydro_ctx* ctx, unsigned long long stats[3]);
 hydro_status hydro_upload(hydro_ctx* ctx, const void* host);
 hydro_status hydro_download(hydro_ctx* ctx, void* host);
 
+/* ---- Ensembles of independent problems (uneven grids, own time steps) ----------------------------
+ * Not in the paper, which runs one problem at a time; this batches many independent copies of the §2
+ * driver loop.  Each member has its own parameters (all members share one precision) and two caller-owned
+ * state buffers, as for hydro_init.  One ensemble step = ghost fill of every member, CFL dt of every
+ * member (its own), and one CTU step of every member with its own dt; the step runs as one persistent
+ * kernel per size class (members with the same nx x ny) whose CTAs take tiles of any member of the class
+ * from a work queue. */
+typedef struct hydro_batch hydro_batch;
+
+/* Create an ensemble of n members.  params, d_states, d_states_alt: arrays of n entries.
+ * Errors: HYDRO_EINVAL (bad member, mixed precisions), HYDRO_ENOMEM, HYDRO_ECUDA. */
+hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* d_states, void* const* d_states_alt,
+                                void* cuda_stream, hydro_batch** out);
+void hydro_batch_destroy(hydro_batch* b);
+
+/* Project autotuner: for every size class time `reps` launches of each candidate tile shape on the
+ * current states (without advancing them) and keep the fastest.  chosen_shapes (optional) receives one
+ * shape id per class.  Synchronises.  Cached graphs are dropped. */
+hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes);
+
+/* Size classes (largest first) and the tile shape each uses. */
+int hydro_batch_num_classes(const hydro_batch* b);
+hydro_status hydro_batch_class_info(const hydro_batch* b, int k, int* nx, int* ny, int* members, int* tile_x,
+                                    int* tile_y, int* threads);
+
+/* Advance every member by nsteps steps, each with its own CFL dt.  use_graph != 0: the nsteps steps are
+ * captured once into a CUDA graph (cached per nsteps and buffer parity) and launched as one graph;
+ * use_graph = 0 launches the kernels directly.  Asynchronous. */
+hydro_status hydro_batch_run(hydro_batch* b, int nsteps, int use_graph);
+
+/* Device pointer of the buffer holding member i's current state. */
+void* hydro_batch_state(const hydro_batch* b, int member);
+
+/* Member time and step count (synchronises). */
+hydro_status hydro_batch_get_time(hydro_batch* b, int member, double* t, long long* nsteps);
+
+/* Read and clear the status words of the ensemble (first of HYDRO_ENONFINITE, HYDRO_ENEGATIVE,
+ * HYDRO_ENONCONV); stats receives {riemann solves, iterations, unconverged} of the step kernels. */
+hydro_status hydro_batch_sync_status(hydro_batch* b, unsigned long long stats[3]);
+
+/* Conserved totals of member i (as hydro_conserved_totals; synchronises). */
+hydro_status hydro_batch_conserved_totals(hydro_batch* b, int member, double out[4]);
+
+const char* hydro_batch_last_error(const hydro_batch* b);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 const char* hydro_last_error(const hydro_ctx* ctx);
 

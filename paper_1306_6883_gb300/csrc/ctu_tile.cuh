@@ -1,0 +1,314 @@
+// One tile of the fused CTU step (paper §3.2 algorithm; CTU construction §3.1, Eqs. 3-5), shared by the
+// single-problem kernel (k_ctu.cu) and the batched persistent kernel (k_batch.cu).
+//
+// A CTA computes TX x TY interior cells.  It stages the (TX+8) x (TY+8) primitive tile (4-cell halo) in
+// shared memory and runs every stage of the step on it without sending any intermediate to global memory:
+//   0. load U, convert to primitives                        (Eqs. 11-12)
+//   1. flattening coefficient xi on (TX+2) x (TY+2) cells    (§3.2, Colella 1990)
+//   2. limited slopes and characteristic tracing, x and y     (§3.1 limiter; Eq. 13)
+//   3. Riemann solves on the traced (hat) states at all faces the transverse terms need
+//   4. transverse correction + final Riemann solves + artificial viscosity at the tile's faces
+//   5. conservative update (Eq. 5), written to the other state buffer
+// Global traffic per cell is one read of U (plus the halo and an L1/L2 re-read of U^n at the faces for
+// the viscosity term) and one write of U^{n+1}.
+//
+// Shared memory is reused across stages: the hat fluxes of stage 3 overwrite the primitive tile (dead
+// after stage 2; the velocities the viscosity needs are kept separately), and each final flux of stage 4
+// overwrites the left traced state that only its own face reads.
+#pragma once
+
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+template <typename R, int TX, int TY>
+struct TileLayout {
+  static constexpr int QX = TX + 8, QY = TY + 8;  // primitive tile with a 4-cell halo
+  static constexpr int SX = TX + 2, SY = TY + 2;  // cells whose face states are traced
+  static constexpr int nC = SX * SY;
+  static constexpr int nQ = 4 * QX * QY;
+  static constexpr int nFXH = 4 * SY * (TX + 1);  // hat x fluxes: rows [3, TY+5), faces [4, TX+5)
+  static constexpr int nFYH = 4 * (TY + 1) * SX;  // hat y fluxes: faces [4, TY+5), columns [3, TX+5)
+  static constexpr int nA = (nQ + nC) > (nFXH + nFYH) ? (nQ + nC) : (nFXH + nFYH);  // region A
+  static constexpr int nS = 4 * nC;               // one traced-state family
+  static constexpr int elems = nA + 4 * nS + 2 * nC;
+  static constexpr size_t bytes = sizeof(R) * (size_t)elems;
+};
+
+// Counters each thread accumulates over the tiles it works on.
+struct TileCounters {
+  unsigned int solves = 0, iters = 0, nonconv = 0, flags = 0;
+};
+
+// Time-step factors in the kernel's precision.
+template <typename R>
+struct StepFactors {
+  R sigx, sigy, hx, hy;
+  __device__ __forceinline__ void load(const StepScalars& sc) {
+    if constexpr (is_f32<R>()) {
+      sigx = sc.sigx_f; sigy = sc.sigy_f; hx = sc.hx_f; hy = sc.hy_f;
+    } else {
+      sigx = sc.sigx; sigy = sc.sigy; hx = sc.hx; hy = sc.hy;
+    }
+  }
+};
+
+// One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
+// smem_raw must hold TileLayout<R, TX, TY>::bytes.  Starts and ends with a block-wide barrier-free
+// state, so consecutive calls by the same block need one __syncthreads() between them.
+template <typename R, int TX, int TY, int NT>
+__device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
+                                         const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
+                                         unsigned char* smem_raw, TileCounters& cnt) {
+  using L = TileLayout<R, TX, TY>;
+  constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
+  R* sq = reinterpret_cast<R*>(smem_raw);  // region A, stages 0-2: [4][QY][QX] primitives
+  R* sxi = sq + L::nQ;                      //                         [SY][SX] flattening
+  R* sfxh = sq;                             // region A, stages 3-4: [4][SY][TX+1] hat x fluxes
+  R* sfyh = sq + L::nFXH;                   //                         [4][TY+1][SX] hat y fluxes
+  R* sxl = sq + L::nA;                      // [4][SY][SX] left state at i+1/2 of each cell (then final Fx)
+  R* sxr = sxl + L::nS;                     // right state at i-1/2
+  R* syl = sxr + L::nS;                     // lower state at j+1/2 (then final Fy)
+  R* syr = syl + L::nS;                     // upper state at j-1/2
+  R* su = syr + L::nS;                      // [SY][SX] cell velocities for the viscosity
+  R* sv = su + nC;
+
+  const R sigx = f.sigx, sigy = f.sigy, hx = f.hx, hy = f.hy;
+  const R ux = sigx, uy = sigy;  // update factors dt/dx, dt/dy (Eq. 5)
+
+  const int tid = threadIdx.x;
+  const int x0 = P.ng + bx * TX;  // padded column of the first interior cell of the tile
+  const int y0 = P.ng + by * TY;
+  const size_t plane = (size_t)P.NY * P.pitch;
+
+  // ---- 0. load the tile (clamped to the array; clamped cells only feed cells outside the grid)
+  for (int e = tid; e < QX * QY; e += NT) {
+    const int lx = e % QX, ly = e / QX;
+    int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
+    gi = gi < P.NX - 1 ? gi : P.NX - 1;
+    gj = gj < P.NY - 1 ? gj : P.NY - 1;
+    const size_t o = (size_t)gj * P.pitch + gi;
+    R rho, u, v, p;
+    cons_to_prim(s, __ldg(Uin + o), __ldg(Uin + o + plane), __ldg(Uin + o + 2 * plane), __ldg(Uin + o + 3 * plane),
+                 rho, u, v, p);
+    sq[e] = rho;
+    sq[QX * QY + e] = u;
+    sq[2 * QX * QY + e] = v;
+    sq[3 * QX * QY + e] = p;
+  }
+  __syncthreads();
+
+  const R* qu = sq + QX * QY;
+  const R* qv = sq + 2 * QX * QY;
+  const R* qp = sq + 3 * QX * QY;
+  // ---- 1. flattening xi = min(xi_x, xi_y) on cells lx in [3, TX+5), ly in [3, TY+5); keep u, v there
+  for (int e = tid; e < nC; e += NT) {
+    const int cx = e % SX + 3, cy = e / SX + 3;
+    const int b = cy * QX + cx;
+    R xi = (R)1;
+    if (s.flatten) {
+      auto chix = [&](int m) {
+        return flatten_chi<R>(qp[b + m - 2], qp[b + m - 1], qp[b + m + 1], qp[b + m + 2], qu[b + m - 1], qu[b + m + 1],
+                              s.small_pres);
+      };
+      auto chiy = [&](int m) {
+        return flatten_chi<R>(qp[b + (m - 2) * QX], qp[b + (m - 1) * QX], qp[b + (m + 1) * QX], qp[b + (m + 2) * QX],
+                              qv[b + (m - 1) * QX], qv[b + (m + 1) * QX], s.small_pres);
+      };
+      const int sx = (qp[b + 1] - qp[b - 1]) >= (R)0 ? 1 : -1;
+      const int sy = (qp[b + QX] - qp[b - QX]) >= (R)0 ? 1 : -1;
+      const R xix = M<R>::mn(chix(0), chix(-sx));
+      const R xiy = M<R>::mn(chiy(0), chiy(-sy));
+      xi = M<R>::mn(xix, xiy);
+    }
+    sxi[e] = xi;
+    su[e] = qu[b];
+    sv[e] = qv[b];
+  }
+  __syncthreads();
+
+  // ---- 2. slopes + tracing for the same cells; items [0, nC) trace in x, [nC, 2 nC) in y
+  for (int e = tid; e < 2 * nC; e += NT) {
+    const bool ydir = e >= nC;
+    const int c = ydir ? e - nC : e;
+    const int cx = c % SX + 3, cy = c / SX + 3;
+    const int b = cy * QX + cx;
+    const int st = ydir ? QX : 1;
+    const R xi = sxi[c];
+    R q[4], dq[4];
+    // face frame: (rho, un, ut, p); in y un = v, ut = u
+    const int kmap[4] = {0, ydir ? 2 : 1, ydir ? 1 : 2, 3};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const R* a = sq + kmap[m] * QX * QY + b;
+      q[m] = a[0];
+      dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+    }
+    R ql[4], qrr[4];
+    trace<R>(s, ydir ? sigy : sigx, q, dq, ql, qrr);
+    R* dl = ydir ? syl : sxl;
+    R* dr = ydir ? syr : sxr;
+    // store in (rho, u, v, p) order
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      dl[kmap[m] * nC + c] = ql[m];
+      dr[kmap[m] * nC + c] = qrr[m];
+    }
+  }
+  __syncthreads();
+
+
+  // ---- 3. hat Riemann solves.  x faces: lx in [4, TX+5) between cells lx-1 and lx, rows [3, TY+5).
+  //         y faces: ly in [4, TY+5), columns [3, TX+5).  Results overwrite region A.
+  {
+    constexpr int nXF = (TX + 1) * SY, nYF = (TY + 1) * SX;
+    for (int e = tid; e < nXF + nYF; e += NT) {
+      R a[4], bq[4], F[4];
+      int it;
+      bool ok;
+      if (e < nXF) {
+        const int fx = e % (TX + 1), ry = e / (TX + 1);  // face index 0..TX <-> lx = fx + 4; row ly = ry + 3
+        const int cL = ry * SX + fx;                      // cell lx-1 = fx + 3 -> s index fx
+        const int cR = cL + 1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          a[m] = sxl[m * nC + cL];
+          bq[m] = sxr[m * nC + cR];
+        }
+        riemann(s, a, bq, (R)0, F, it, ok);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
+      } else {
+        const int f = e - nXF;
+        const int cxs = f % SX, fy = f / SX;  // column s index; face 0..TY <-> ly = fy + 4
+        const int cL = fy * SX + cxs;          // cell ly-1 = fy + 3
+        const int cR = cL + SX;
+        a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
+        bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
+        riemann(s, a, bq, (R)0, F, it, ok);
+        const int o = fy * SX + cxs;
+        sfyh[0 * (TY + 1) * SX + o] = F[0];
+        sfyh[1 * (TY + 1) * SX + o] = F[2];
+        sfyh[2 * (TY + 1) * SX + o] = F[1];
+        sfyh[3 * (TY + 1) * SX + o] = F[3];
+      }
+      cnt.solves++;
+      cnt.iters += it;
+      cnt.nonconv += ok ? 0 : 1;
+    }
+  }
+  __syncthreads();
+
+  // ---- 4. transverse correction + final solves + artificial viscosity at the tile's faces
+  {
+    constexpr int nXF = (TX + 1) * TY, nYF = (TY + 1) * TX;
+    for (int e = tid; e < nXF + nYF; e += NT) {
+      R a[4], bq[4], F[4], UL[4], UR[4];
+      int it;
+      bool ok;
+      if (e < nXF) {
+        const int fx = e % (TX + 1), ty = e / (TX + 1);  // face lx = fx + 4, row ly = ty + 4
+        const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
+        // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
+        const int fL = ty * SX + fx, fR = fL + 1;
+        prim_to_cons(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
+        prim_to_cons(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R* fy = sfyh + k * (TY + 1) * SX;
+          UL[k] = UL[k] - hy * (fy[fL + SX] - fy[fL]);
+          UR[k] = UR[k] - hy * (fy[fR + SX] - fy[fR]);
+        }
+        cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
+        cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
+        riemann(s, a, bq, (R)0, F, it, ok);
+        // artificial viscosity from the cell-centred velocities of the time-n state
+        if (s.cvisc > (R)0) {
+          R div;
+          const R dvy = sv[cR + SX] + sv[cL + SX] - sv[cR - SX] - sv[cL - SX];
+          if constexpr (is_f32<R>())
+            div = (su[cR] - su[cL]) * s.idx + dvy * (0.25f * s.idy);
+          else
+            div = (su[cR] - su[cL]) / s.dx + dvy / (4.0 * s.dy);
+          const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
+          const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx (may be clamped)
+          const size_t o = (size_t)(gj < P.NY - 1 ? gj : P.NY - 1) * P.pitch + (gi < P.NX - 1 ? gi : P.NX - 1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + o - 1 + k * plane) - __ldg(Uin + o + k * plane));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = F[k];  // only this face read sxl[cL]
+      } else {
+        const int f = e - nXF;
+        const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
+        const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
+        // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
+        const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
+        prim_to_cons(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
+        prim_to_cons(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R* fxh = sfxh + k * SY * (TX + 1);
+          UL[k] = UL[k] - hx * (fxh[fL + 1] - fxh[fL]);
+          UR[k] = UR[k] - hx * (fxh[fR + 1] - fxh[fR]);
+        }
+        R ql[4], qrr[4];
+        cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], ql[0], ql[1], ql[2], ql[3]);
+        cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], qrr[0], qrr[1], qrr[2], qrr[3]);
+        a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
+        bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
+        riemann(s, a, bq, (R)0, F, it, ok);
+        R G[4] = {F[0], F[2], F[1], F[3]};
+        if (s.cvisc > (R)0) {
+          R div;
+          const R dux = (su[cR + 1] + su[cL + 1] - su[cR - 1] - su[cL - 1]);
+          if constexpr (is_f32<R>())
+            div = (sv[cR] - sv[cL]) * s.idy + dux * (0.25f * s.idx);
+          else
+            div = (sv[cR] - sv[cL]) / s.dy + dux / (4.0 * s.dx);
+          const R av = s.cvisc * M<R>::mx(-div * s.dy, (R)0);
+          const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
+          const size_t o = (size_t)(gj < P.NY - 1 ? gj : P.NY - 1) * P.pitch + (gi < P.NX - 1 ? gi : P.NX - 1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            G[k] += av * (__ldg(Uin + o - P.pitch + k * plane) - __ldg(Uin + o + k * plane));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
+      }
+      cnt.solves++;
+      cnt.iters += it;
+      cnt.nonconv += ok ? 0 : 1;
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. conservative update of the tile's valid cells
+  unsigned int& flags = cnt.flags;
+  for (int e = tid; e < TX * TY; e += NT) {
+    const int tx = e % TX, ty = e / TX;
+    const int gi = x0 + tx, gj = y0 + ty;
+    if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
+    const size_t o = (size_t)gj * P.pitch + gi;
+    const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
+    const int cy = ty * SX + tx + 1;    // final y flux of face ty (below the cell) lives in syl[cy]
+    R Un[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const R* fx = sxl + k * nC;
+      const R* fy = syl + k * nC;
+      const R d = ux * (fx[cx] - fx[cx + 1]) + uy * (fy[cy] - fy[cy + SX]);
+      Un[k] = __ldg(Uin + o + k * plane) + d;
+      Uout[o + k * plane] = Un[k];
+    }
+    if (!finite4(Un[0], Un[1], Un[2], Un[3])) {
+      flags |= STATUS_NONFINITE;
+    } else {
+      const R ke = M<R>::dv((R)0.5 * (Un[1] * Un[1] + Un[2] * Un[2]), Un[0]);
+      if (!(Un[0] > (R)0) || !(Un[3] - ke > (R)0)) flags |= STATUS_NEGATIVE;
+    }
+  }
+
+}
+
+}  // namespace hydro

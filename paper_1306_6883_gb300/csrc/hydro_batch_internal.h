@@ -1,0 +1,36 @@
+// Internal interface of the batched (ensemble) kernels (not installed).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+// One ensemble member as the batched kernels see it (device memory).
+struct BatchMember {
+  KParams P;
+  void* U[2];        // the member's two state buffers; parity p reads U[p] and writes U[1 - p]
+  DevScratch* scr;   // the member's own dt, step factors, time and status
+};
+
+constexpr int BATCH_DT_CELLS = 2048;  // cells reduced by one block of the batched dt kernel
+
+struct TileShape {
+  int tx, ty, threads;
+};
+extern const TileShape kTileShapes[];
+extern const int kNumTileShapes;
+
+// tab[b] = (member, first ghost cell) for each 256-cell block
+cudaError_t batch_fill(int precision, const BatchMember* mem, const int2* tab, int nblocks, int parity,
+                       cudaStream_t stream);
+// tab[b] = (member, first cell, member's block count, 0); advance = 0 leaves time and step count alone
+cudaError_t batch_dt(int precision, const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
+                     cudaStream_t stream);
+// tiles[k] = (member, tile x, tile y, 0) for tile shape `shape` (FP64 always uses 16 x 16)
+cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
+                       unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out);
+// set the kernel attributes of every shape (call once before any stream capture)
+cudaError_t batch_prepare(int precision);
+
+}  // namespace hydro

@@ -77,6 +77,51 @@ static hydro_status cuda_fail(hydro_ctx* c, cudaError_t e, const char* where) {
   return HYDRO_ECUDA;
 }
 
+namespace hydro {
+
+// Kernel parameters of one problem (shared by single-problem contexts and ensembles).
+void fill_kparams(const hydro_params* p, KParams* kp) {
+  KParams& k = *kp;
+  memset(&k, 0, sizeof k);
+  k.nx = p->nx;
+  k.ny = p->ny;
+  k.ng = p->ng;
+  k.pitch = (int)hydro_state_pitch(p);
+  k.NX = p->nx + 2 * p->ng;
+  k.NY = p->ny + 2 * p->ng;
+  k.bc[0] = p->bc_xlo;
+  k.bc[1] = p->bc_xhi;
+  k.bc[2] = p->bc_ylo;
+  k.bc[3] = p->bc_yhi;
+  k.dx = (p->xmax - p->xmin) / p->nx;
+  k.dy = (p->ymax - p->ymin) / p->ny;
+  k.gamma = p->gamma;
+  k.gm1 = p->gamma - 1.0;
+  k.g1 = (p->gamma + 1.0) / (2.0 * p->gamma);
+  k.cfl = p->cfl;
+  k.limiter = p->limiter;
+  k.use_flattening = p->use_flattening;
+  k.cvisc = p->cvisc;
+  k.riemann_maxiter = p->riemann_maxiter;
+  k.riemann_tol = p->riemann_tol;
+  k.small_dens = p->small_dens;
+  k.small_pres = p->small_pres;
+  k.gamma_f = (float)k.gamma;
+  k.gm1_f = (float)k.gm1;
+  k.igm1_f = (float)(1.0 / k.gm1);
+  k.idx_f = (float)(1.0 / k.dx);
+  k.idy_f = (float)(1.0 / k.dy);
+  k.g1_f = (float)k.g1;
+  k.small_dens_f = (float)k.small_dens;
+  k.small_pres_f = (float)k.small_pres;
+  k.tol_f = (float)k.riemann_tol;
+  k.cvisc_f = (float)k.cvisc;
+  k.dx_f = (float)k.dx;
+  k.dy_f = (float)k.dy;
+}
+
+}  // namespace hydro
+
 extern "C" {
 
 hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision) {
@@ -132,42 +177,7 @@ hydro_status hydro_init(const hydro_params* p, void* d_state, void* d_state_alt,
   c->cur = 0;
   c->stream = (cudaStream_t)cuda_stream;
   c->err[0] = 0;
-  KParams& k = c->kp;
-  k.nx = p->nx;
-  k.ny = p->ny;
-  k.ng = p->ng;
-  k.pitch = (int)hydro_state_pitch(p);
-  k.NX = p->nx + 2 * p->ng;
-  k.NY = p->ny + 2 * p->ng;
-  k.bc[0] = p->bc_xlo;
-  k.bc[1] = p->bc_xhi;
-  k.bc[2] = p->bc_ylo;
-  k.bc[3] = p->bc_yhi;
-  k.dx = (p->xmax - p->xmin) / p->nx;
-  k.dy = (p->ymax - p->ymin) / p->ny;
-  k.gamma = p->gamma;
-  k.gm1 = p->gamma - 1.0;
-  k.g1 = (p->gamma + 1.0) / (2.0 * p->gamma);
-  k.cfl = p->cfl;
-  k.limiter = p->limiter;
-  k.use_flattening = p->use_flattening;
-  k.cvisc = p->cvisc;
-  k.riemann_maxiter = p->riemann_maxiter;
-  k.riemann_tol = p->riemann_tol;
-  k.small_dens = p->small_dens;
-  k.small_pres = p->small_pres;
-  k.gamma_f = (float)k.gamma;
-  k.gm1_f = (float)k.gm1;
-  k.igm1_f = (float)(1.0 / k.gm1);
-  k.idx_f = (float)(1.0 / k.dx);
-  k.idy_f = (float)(1.0 / k.dy);
-  k.g1_f = (float)k.g1;
-  k.small_dens_f = (float)k.small_dens;
-  k.small_pres_f = (float)k.small_pres;
-  k.tol_f = (float)k.riemann_tol;
-  k.cvisc_f = (float)k.cvisc;
-  k.dx_f = (float)k.dx;
-  k.dy_f = (float)k.dy;
+  hydro::fill_kparams(p, &c->kp);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     delete c;

@@ -135,6 +135,14 @@ __device__ __forceinline__ bool finite4(R a, R b, R c, R d) {
   return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
 }
 
+// Ghost-cell source index along one axis (paper §2, CellCenterData2d ghost filling; Fig. 1): outflow clamps
+// to the nearest interior index (zero gradient), periodic wraps.
+__device__ __forceinline__ int map_index(int i, int ng, int n, int lo_bc, int hi_bc) {
+  if (i < ng) return lo_bc == 1 ? i + n : ng;
+  if (i >= ng + n) return hi_bc == 1 ? i - n : ng + n - 1;
+  return i;
+}
+
 // ---------------------------------------------------------------------------------------------------
 // EOS (Eqs. 11-12): conserved (rho, mx, my, E) -> primitive (rho, u, v, p), floors on the copy.
 template <typename R>
@@ -400,6 +408,10 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float icl = rsqrtf(xl), icr = rsqrtf(xr);  // 1/C_K
   const float cl = xl * icl, cr = xr * icr;
   const float ipl = rcpa(pl), ipr = rcpa(pr);
+  // velocity scale of the problem: float rounding leaves u*_R - u*_L uncertain by ~2^-24 of it, which can
+  // exceed tol * p* in pressure when p* << rho u^2, so the FP32 stopping rule also accepts a pressure
+  // change smaller than the one a velocity mismatch of tol times this scale would produce
+  const float vscale = fabsf(ul) + fabsf(ur) + cl * rcpa(rl) + cr * rcpa(rr);
   float pst = guess > 0.0f ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) * rcpa(cl + cr);
   pst = pst < s.small_pres ? s.small_pres : pst;
   int it = 0;
@@ -412,12 +424,13 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     const float usr = ur + (pst - pr) * iwr;
     const float izl = 0.5f * (al + 1.0f) * tl * tl * iwl;
     const float izr = 0.5f * (ar + 1.0f) * tr * tr * iwr;
-    float pnew = pst - (usr - usl) * rcpa(izl + izr);
+    const float iz = izl + izr;  // 1 / (Z_L Z_R / (Z_L + Z_R))
+    float pnew = pst - (usr - usl) * rcpa(iz);
     pnew = pnew < s.small_pres ? s.small_pres : pnew;
     const float dp = fabsf(pnew - pst);
     pst = pnew;
     ++it;
-    if (dp <= s.tol * pst) {
+    if (dp <= s.tol * pst || dp * iz <= s.tol * vscale) {
       ok = true;
       break;
     }
@@ -470,6 +483,29 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     }
   }
   face_flux(s, fr, fu, fv, fp, F);
+}
+
+// CFL constraint of one interior cell at offset o (Eq. 6 with |u|+c): min(dx/(|u|+c), dy/(|v|+c)), folded
+// into rbest; non-finite and non-positive cells set status bits instead.
+template <typename R>
+__device__ __forceinline__ void cfl_cell(const SP<R>& s, const R* __restrict__ U, size_t o, size_t plane, R& rbest,
+                                         unsigned int& flags) {
+  const R U0 = U[o], U1 = U[o + plane], U2 = U[o + 2 * plane], U3 = U[o + 3 * plane];
+  if (!finite4(U0, U1, U2, U3)) {
+    flags |= STATUS_NONFINITE;
+    return;
+  }
+  R rho, u, v, p;
+  cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
+  {
+    const R ke = M<R>::dv((R)0.5 * (U1 * U1 + U2 * U2), U0);
+    if (!(U0 > (R)0) || !(U3 - ke > (R)0)) flags |= STATUS_NEGATIVE;
+  }
+  const R cs = M<R>::sq(M<R>::dv(s.gamma * p, rho));
+  const R tx = M<R>::dv(s.dx, M<R>::ab(u) + cs);
+  const R ty = M<R>::dv(s.dy, M<R>::ab(v) + cs);
+  const R t = M<R>::mn(tx, ty);
+  rbest = t < rbest ? t : rbest;
 }
 
 }  // namespace hydro

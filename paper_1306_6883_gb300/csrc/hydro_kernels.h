@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/hydro.h"
 #include "hydro_device.cuh"
 
 namespace hydro {
@@ -24,6 +25,9 @@ cudaError_t conserved_totals(int precision, const KParams& P, const void* U, dou
 // One fused CTU step Uin -> Uout with the time-step factors from sc_dev if not NULL, else sc_host.
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
                      const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
+
+// Kernel parameters of one problem from the public parameters (validated by the caller).
+void fill_kparams(const hydro_params* p, KParams* k);
 
 // Scratch initialisation (min accumulator = +inf, counters 0).
 cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream);

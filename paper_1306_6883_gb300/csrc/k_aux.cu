@@ -10,12 +10,6 @@ namespace hydro {
 // Ghost cells (paper §2, CellCenterData2d ghost filling; Fig. 1): ghost (i, j) takes interior cell
 // (map_x(i), map_y(j)); outflow clamps to the nearest interior index (zero gradient), periodic wraps.
 // All sources are interior cells, so one pass over the ghost frame fills edges and corners.
-__device__ __forceinline__ int map_index(int i, int ng, int n, int lo_bc, int hi_bc) {
-  if (i < ng) return lo_bc == 1 ? i + n : ng;
-  if (i >= ng + n) return hi_bc == 1 ? i - n : ng + n - 1;
-  return i;
-}
-
 template <typename R>
 __global__ void fill_ghost_kernel(KParams P, R* __restrict__ U) {
   // ghost frame enumerated as: bottom band ng x NX, top band ng x NX, then left/right bands ny x ng each
@@ -70,7 +64,6 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
                                                            DevScratch* __restrict__ scr, double tmax, int advance) {
   SP<R> s;
   s.load(P);
-  const R dx = s.dx, dy = s.dy;
   const size_t plane = (size_t)P.NY * P.pitch;
   const long long ncell = (long long)P.nx * P.ny;
   R rbest = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
@@ -79,22 +72,7 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
        e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e / P.nx), i = (int)(e % P.nx);
     const size_t o = (size_t)(j + P.ng) * P.pitch + (i + P.ng);
-    const R U0 = U[o], U1 = U[o + plane], U2 = U[o + 2 * plane], U3 = U[o + 3 * plane];
-    if (!finite4(U0, U1, U2, U3)) {
-      flags |= STATUS_NONFINITE;
-      continue;
-    }
-    R rho, u, v, p;
-    cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
-    {
-      const R ke = M<R>::dv((R)0.5 * (U1 * U1 + U2 * U2), U0);
-      if (!(U0 > (R)0) || !(U3 - ke > (R)0)) flags |= STATUS_NEGATIVE;
-    }
-    const R cs = M<R>::sq(M<R>::dv(s.gamma * p, rho));
-    const R tx = M<R>::dv(dx, M<R>::ab(u) + cs);
-    const R ty = M<R>::dv(dy, M<R>::ab(v) + cs);
-    const R t = M<R>::mn(tx, ty);
-    rbest = t < rbest ? t : rbest;
+    cfl_cell(s, U, o, plane, rbest, flags);
   }
   // the minimum of the per-cell values is exact in their own precision; promote once
 #pragma unroll

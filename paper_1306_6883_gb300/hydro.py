@@ -62,6 +62,19 @@ SIGNATURES = {
     "hydro_conserved_totals_noalloc": (ctypes.c_int, [_PP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "hydro_upload": (ctypes.c_int, [_VP, _VP]),
     "hydro_download": (ctypes.c_int, [_VP, _VP]),
+    "hydro_batch_create": (ctypes.c_int, [ctypes.c_int, _PP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP,
+                                          ctypes.POINTER(_VP)]),
+    "hydro_batch_destroy": (None, [_VP]),
+    "hydro_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "hydro_batch_num_classes": (ctypes.c_int, [_VP]),
+    "hydro_batch_class_info": (ctypes.c_int, [_VP, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 6),
+    "hydro_batch_run": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "hydro_batch_state": (_VP, [_VP, ctypes.c_int]),
+    "hydro_batch_get_time": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_longlong)]),
+    "hydro_batch_sync_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hydro_batch_conserved_totals": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "hydro_batch_last_error": (ctypes.c_char_p, [_VP]),
     "hydro_last_error": (ctypes.c_char_p, [_VP]),
     "hydro_build_info": (ctypes.c_char_p, []),
 }
@@ -186,3 +199,69 @@ def hydro_download(ctx, host_ptr):
 
 def hydro_build_info():
     return load().hydro_build_info().decode()
+
+
+# ---------------------------------------------------------------------------------------------------- ensembles
+def _bcheck(status, b, what):
+    if status != HYDRO_OK:
+        msg = load().hydro_batch_last_error(b).decode() if b else ""
+        raise HydroError(status, f"{what}: {msg}")
+
+
+def hydro_batch_create(params_list, states, states_alt, stream_ptr):
+    n = len(params_list)
+    arr = (HydroParams * n)(*params_list)
+    s0 = (_VP * n)(*[_VP(p) for p in states])
+    s1 = (_VP * n)(*[_VP(p) for p in states_alt])
+    b = _VP()
+    _bcheck(load().hydro_batch_create(n, arr, s0, s1, _VP(stream_ptr), ctypes.byref(b)), None, "hydro_batch_create")
+    return b
+
+
+def hydro_batch_destroy(b):
+    load().hydro_batch_destroy(b)
+
+
+def hydro_batch_autotune(b, reps=3):
+    n = load().hydro_batch_num_classes(b)
+    out = (ctypes.c_int * max(n, 1))()
+    _bcheck(load().hydro_batch_autotune(b, int(reps), out), b, "hydro_batch_autotune")
+    return list(out)[:n]
+
+
+def hydro_batch_classes(b):
+    out = []
+    for k in range(load().hydro_batch_num_classes(b)):
+        v = [ctypes.c_int() for _ in range(6)]
+        _bcheck(load().hydro_batch_class_info(b, k, *[ctypes.byref(x) for x in v]), b, "hydro_batch_class_info")
+        nx, ny, members, tx, ty, threads = (x.value for x in v)
+        out.append(dict(nx=nx, ny=ny, members=members, tile=(tx, ty), threads=threads))
+    return out
+
+
+def hydro_batch_run(b, nsteps, use_graph=True):
+    _bcheck(load().hydro_batch_run(b, int(nsteps), 1 if use_graph else 0), b, "hydro_batch_run")
+
+
+def hydro_batch_state(b, member):
+    return load().hydro_batch_state(b, int(member))
+
+
+def hydro_batch_get_time(b, member):
+    t, n = ctypes.c_double(), ctypes.c_longlong()
+    _bcheck(load().hydro_batch_get_time(b, int(member), ctypes.byref(t), ctypes.byref(n)), b, "hydro_batch_get_time")
+    return t.value, n.value
+
+
+def hydro_batch_sync_status(b, raise_on_error=True):
+    stats = (ctypes.c_ulonglong * 3)()
+    st = load().hydro_batch_sync_status(b, stats)
+    if raise_on_error:
+        _bcheck(st, b, "hydro_batch_sync_status")
+    return st, list(stats)
+
+
+def hydro_batch_conserved_totals(b, member):
+    out = (ctypes.c_double * 4)()
+    _bcheck(load().hydro_batch_conserved_totals(b, int(member), out), b, "hydro_batch_conserved_totals")
+    return list(out)

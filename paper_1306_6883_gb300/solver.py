@@ -104,3 +104,65 @@ def params_for(problem, precision=H.HYDRO_FP64, **kw):
     xmin, xmax, ymin, ymax = problem.domain
     return H.default_params(problem.nx, problem.ny, precision, bc=problem.bc, gamma=problem.gamma, cfl=problem.cfl,
                             xmin=xmin, xmax=xmax, ymin=ymin, ymax=ymax, ng=problem.ng, **kw)
+
+
+class Ensemble:
+    """Independent problems advanced together through the hydro_batch_* calls (PyTorch owns the buffers).
+
+        e = Ensemble([params_for(p, H.HYDRO_FP32) for p in problems], [p.U for p in problems])
+        e.autotune(); e.run(100)
+    """
+
+    def __init__(self, params_list, states, stream=None, device="cuda"):
+        self.params = list(params_list)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.bufs, self.shapes = [], []
+        for p in self.params:
+            dt = torch.float32 if p.precision == H.HYDRO_FP32 else torch.float64
+            pitch = H.state_pitch(p)
+            NX, NY = p.nx + 2 * p.ng, p.ny + 2 * p.ng
+            self.shapes.append((NY, NX, pitch, dt))
+            self.bufs.append([torch.zeros(4 * NY * pitch, dtype=dt, device=device) for _ in range(2)])
+        for i, U in enumerate(states):
+            NY, NX, pitch, dt = self.shapes[i]
+            view = self.bufs[i][0].view(4, NY, pitch)
+            view[:, :, :NX].copy_(torch.from_numpy(np.ascontiguousarray(U)).to(dt))
+        torch.cuda.synchronize()
+        self.b = H.hydro_batch_create(self.params, [x[0].data_ptr() for x in self.bufs],
+                                      [x[1].data_ptr() for x in self.bufs], self.stream.cuda_stream)
+
+    def close(self):
+        if self.b is not None:
+            H.hydro_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, reps=3):
+        return H.hydro_batch_autotune(self.b, reps)
+
+    def classes(self):
+        return H.hydro_batch_classes(self.b)
+
+    def run(self, nsteps, use_graph=True):
+        H.hydro_batch_run(self.b, nsteps, use_graph)
+
+    def time(self, i):
+        return H.hydro_batch_get_time(self.b, i)
+
+    def status(self, raise_on_error=True):
+        return H.hydro_batch_sync_status(self.b, raise_on_error)
+
+    def totals(self, i):
+        return H.hydro_batch_conserved_totals(self.b, i)
+
+    def state_numpy(self, i):
+        NY, NX, pitch, dt = self.shapes[i]
+        ptr = H.hydro_batch_state(self.b, i)
+        buf = self.bufs[i][0] if ptr == self.bufs[i][0].data_ptr() else self.bufs[i][1]
+        torch.cuda.synchronize()
+        return buf.view(4, NY, pitch)[:, :, :NX].cpu().numpy().copy()

@@ -362,3 +362,15 @@ def test_bad_time_step_is_rejected():
             s.step(bad)
         assert e.value.status == H.HYDRO_EINVAL
     s.close()
+
+
+def test_fp32_riemann_converges_on_strong_quadrant_problems():
+    # strong rarefactions (p* << rho u^2) are where float rounding of u*_R - u*_L matters most
+    H, Solver, params_for = _mods()
+    for seed in range(8):
+        pr = hp.quad(128, 128, seed=100 + seed)
+        s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
+        s.advance(10)
+        st, stats = s.status(raise_on_error=False)
+        s.close()
+        assert st == H.HYDRO_OK and stats[2] == 0, (seed, st, stats)
