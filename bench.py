@@ -18,6 +18,7 @@ exchange); the value is the sum over ranks, timed by the slowest rank.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -248,6 +249,107 @@ def time_ensemble(steps=100, warmup=3, n=256, seed=0):
     return out
 
 
+def harvest_and_train(train_steps=4000, batch=4096, lr=1e-3, seed=0):
+    """Training set for the learned starting pressure: Riemann problems sampled from FP32 runs of the Sod
+    tube (128^2 to t = 0.2), the Kelvin-Helmholtz layer (1024^2, 40 steps) and the Sedov blast (1024^2,
+    300 steps); then `train_steps` Adam steps of the library's training kernels."""
+    import torch
+
+    import hydro_problems as hp
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Harvest, Model, Solver, params_for
+
+    cap = 12_000_000
+    buf = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    plan = [(hp.sod(128, 128), 0.2, 70, 0.25), (hp.kh(1024, 1024), 0.0, 40, 0.02),
+            (hp.sedov(1024, 1024), 0.0, 300, 0.005)]
+    t0 = time.perf_counter()
+    for pr, tmax, steps, rate in plan:
+        s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
+        H.hydro_set_harvest(s.ctx, buf.data_ptr(), cap, rate, count.data_ptr())
+        s.advance(steps, tmax)
+        s.status()
+        s.close()
+    n = min(int(count.item()), cap)
+    data = buf[:n]
+    t1 = time.perf_counter()
+    m = Model(seed=seed)
+    loss = m.train(data, steps=train_steps, batch=batch, lr=lr, seed=seed + 1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    # iterations per face at the FP32 tolerance, acoustic vs learned start: on a held-out problem family
+    # (four-quadrant problems, not in the training set) and on the training set, all faces and the faces
+    # the default gate sends to the network
+    cap2 = 2_000_000
+    buf2 = torch.zeros((cap2, 8), dtype=torch.float32, device="cuda")
+    count2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for k in range(4):
+        pr = hp.quad(512, 512, seed=1000 + k)
+        s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
+        H.hydro_set_harvest(s.ctx, buf2.data_ptr(), cap2, 0.05, count2.data_ptr())
+        s.advance(20)
+        s.status()
+        s.close()
+    held = buf2[:min(int(count2.item()), cap2)]
+
+    def strong(d):
+        pmax, pmin = torch.maximum(d[:, 2], d[:, 5]), torch.minimum(d[:, 2], d[:, 5])
+        du = d[:, 1] - d[:, 4]
+        return d[(pmax >= math.exp(0.7) * pmin) | (du ** 4 * d[:, 0] * d[:, 3] >= d[:, 2] * d[:, 5])].contiguous()
+
+    iters = {}
+    for name, d in (("held_out_quad_all", held), ("held_out_quad_strong", strong(held)),
+                    ("training_set_all", data[:2_000_000].contiguous()),
+                    ("training_set_strong", strong(data[:2_000_000]))):
+        row = {"faces": int(d.shape[0])}
+        if d.shape[0]:
+            for learned in (False, True):
+                mean, nonconv = H.hydro_mlp_iterations(m.m, d.data_ptr(), d.shape[0], learned)
+                row["learned" if learned else "acoustic"] = mean
+                row["nonconverged_" + ("learned" if learned else "acoustic")] = nonconv
+        iters[name] = row
+    return m, {"samples": n, "harvest_s": t1 - t0, "train_steps": train_steps, "batch": batch, "train_s": t2 - t1,
+               "final_minibatch_loss": loss, "iterations_per_face": iters}
+
+
+def time_learned(model, steps=20, warmup=3):
+    """Config of the learned proposal: 8192^2 Sedov blast with 1 % seeded density noise, FP32, the same
+    steps with the acoustic start (plain) and with the network's start (default gate, and gate always
+    open); zone-updates/s and Riemann iterations per solve at the same tolerance."""
+    import torch
+
+    import hydro_problems as hp
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+
+    pr = hp.sedov(8192, 8192, density_noise=0.01)
+    out = {"workload": "sedov_8192x8192_outflow_1pct_noise", "steps": steps}
+    for name, learned, gate in (("plain", False, None), ("learned", True, (0.35, 1.0)),
+                                ("learned_gate_open", True, (0.0, 0.0))):
+        if learned:
+            model.set_gate(*gate)
+        s = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1 if learned else 0), pr.U)
+        if learned:
+            H.hydro_set_riemann_model(s.ctx, model.m)
+        s.advance(warmup)
+        s.status()
+        _, st0 = s.status()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.advance(steps)
+        b.record(s.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        _, st1 = s.status()
+        s.close()
+        solves, iters = st1[0] - st0[0], st1[1] - st0[1]
+        out[name] = {"value": pr.nx * pr.ny * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "riemann_iters_per_solve": iters / max(solves, 1)}
+    model.set_gate(0.35, 1.0)
+    return out
+
+
 def cpu_baseline(pr, budget_s=12.0, max_steps=50):
     """The oracle as it stands (OpenMP over rows on all host cores), on whole steps of the same workload,
     for about budget_s seconds."""
@@ -289,6 +391,12 @@ def run_ours(args, world, rank, local):
     var = time_device_path(pr, other, max(args.steps // 4, 10), args.warmup, flush)
     e2e = time_e2e(pr, args.precision, max(args.steps // 4, 10), args.warmup)
     ens = time_ensemble() if args.precision == "fp32" else None
+    learned = None
+    if args.precision == "fp32":
+        model, training = harvest_and_train()
+        learned = time_learned(model)
+        learned["training"] = training
+        model.close()
 
     t_step = sum(main["step_ms"]) / 1e3
     t_step = max_over_ranks(t_step, world)
@@ -340,6 +448,7 @@ def run_ours(args, world, rank, local):
                              else var_value / (value / world)}},
         "riemann_iters_per_solve": main["iters_per_solve"],
         "ensemble": ens,
+        "learned_proposal": learned,
     }
     line["roofline"]["hbm_frac_of_measured"] = line["roofline"]["hbm_gbs"] / hbm
     if world == 1:

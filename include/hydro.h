@@ -67,7 +67,8 @@ typedef struct {
   double riemann_tol;               /* relative |dp|/p stopping tolerance (default 1e-14 FP64, 1e-6 FP32) */
   double small_dens, small_pres;    /* floors on working copies only, never on the stored state */
   int precision;                    /* hydro_precision */
-  int use_learned_guess;            /* reserved, must be 0 */
+  int use_learned_guess;            /* 1: start each Riemann iteration from a learned proposal (FP32 only;
+                                       see hydro_set_riemann_model), default 0 */
 } hydro_params;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -168,6 +169,57 @@ hydro_status hydro_sync_status(hydro_ctx* ctx, unsigned long long stats[3]);
  * copies asynchronous; the call returns after enqueueing (upload) or after the copy (download). */
 hydro_status hydro_upload(hydro_ctx* ctx, const void* host);
 hydro_status hydro_download(hydro_ctx* ctx, void* host);
+
+/* ---- Learned starting pressure for the two-shock iteration -----------------------------------------
+ * Not in the paper, which starts the iteration of §3.2 from the acoustic (linearised) estimate.  A small
+ * network (6 -> 64 -> 64 -> 1, ReLU) proposes ln(p_star / p_ref) from the face's left/right (rho, u_n, p) in
+ * reference units (rho_ref = sqrt(rho_L rho_R), p_ref = sqrt(p_L p_R), c_ref = sqrt(p_ref/rho_ref),
+ * velocities relative to their mean); the Newton iteration then runs from that proposal to the same
+ * tolerance, so the answer is still decided by the method.  Training data are faces sampled from CTU
+ * steps (hydro_set_harvest).  FP32 contexts only.  Inference runs on the tensor cores (BF16 weights and
+ * activations, FP32 accumulation), 32 faces per warp; a warp evaluates the network only when one of its
+ * faces has |ln(p_L/p_R)|/2 > gate_dp or |u_L - u_R|/c_ref > gate_du, otherwise its faces start from the
+ * acoustic estimate. */
+typedef struct hydro_mlp hydro_mlp;
+
+/* Create a network with He-normal weights drawn from `seed` (counter-based generator on the device).
+ * Parameter vector (4673 floats): W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3. */
+hydro_status hydro_mlp_create(unsigned long long seed, void* cuda_stream, hydro_mlp** out);
+void hydro_mlp_destroy(hydro_mlp* m);
+hydro_status hydro_mlp_set_weights(hydro_mlp* m, const float* host_theta);
+hydro_status hydro_mlp_get_weights(hydro_mlp* m, float* host_theta);
+/* Gate of the fused inference (defaults 0.35 and 1.0). */
+hydro_status hydro_mlp_set_gate(hydro_mlp* m, double gate_dp, double gate_du);
+/* Gradient (host array of 4673 floats) and loss of the mean squared error of ln(p_star / p_ref) over n
+ * samples.  d_samples: device array [n][8] = (rho_L, u_L, p_L, rho_R, u_R, p_R, p*, iterations). */
+hydro_status hydro_mlp_gradient(hydro_mlp* m, const float* d_samples, long long n, float* host_grad, double* loss);
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on minibatches of `batch` samples
+ * (a multiple of 64) drawn from d_samples with a counter-based generator seeded by `seed`; *last_loss
+ * receives the last minibatch's loss.  Synchronises. */
+hydro_status hydro_mlp_train(hydro_mlp* m, const float* d_samples, long long n, int steps, int batch, double lr,
+                             unsigned long long seed, double* last_loss);
+/* Network outputs y = ln(p_star / p_ref) of n samples into the device array d_out, with the FP32 master weights
+ * (use_tensor_cores = 0) or the BF16 tensor-core inference path (1). */
+hydro_status hydro_mlp_predict(hydro_mlp* m, const float* d_samples, long long n, int use_tensor_cores, float* d_out);
+/* Diagnostic: mean FP32 two-shock iterations per sample (tolerance tol, cap maxiter, EOS gamma) of n
+ * device samples when started from the acoustic estimate (learned = 0) or from the network (learned = 1,
+ * tensor-core inference, no gate); *nonconv receives the unconverged count.  Synchronises. */
+hydro_status hydro_mlp_iterations(hydro_mlp* m, const float* d_samples, long long n, int learned, double gamma,
+                                  double tol, int maxiter, double* mean_iters, long long* nonconv);
+/* Device address of the packed inference weights (for the CTU kernels). */
+const void* hydro_mlp_device_blob(const hydro_mlp* m);
+const char* hydro_mlp_last_error(const hydro_mlp* m);
+
+/* Use network m as the starting pressure of every Riemann solve of ctx's steps (the context must have been
+ * created with use_learned_guess = 1; m = NULL clears it).  m must outlive its use. */
+hydro_status hydro_set_riemann_model(hydro_ctx* ctx, const hydro_mlp* m);
+
+/* Record Riemann problems during steps: each face solve is kept with probability `rate` (hash of the face
+ * and the step), writing 8 floats (rho_L, u_L, p_L, rho_R, u_R, p_R, p*, iterations) at slot
+ * atomicAdd(d_count, 1) of the device buffer d_buf while the slot is < capacity.  d_count is a caller-owned
+ * device counter (zero it before use).  d_buf = NULL stops recording.  FP32 contexts only. */
+hydro_status hydro_set_harvest(hydro_ctx* ctx, void* d_buf, unsigned long long capacity, double rate,
+                               unsigned long long* d_count);
 
 /* ---- Ensembles of independent problems (uneven grids, own time steps) ----------------------------
  * Not in the paper, which runs one problem at a time; this batches many independent copies of the §2

@@ -18,6 +18,7 @@
 #pragma once
 
 #include "hydro_device.cuh"
+#include "mlp.cuh"
 
 namespace hydro {
 
@@ -53,13 +54,52 @@ struct StepFactors {
   }
 };
 
+// Identity of a face within one step, for the harvest's sampling hash.
+__device__ __forceinline__ unsigned int face_key(int bx, int by, int stage, int e) {
+  return hash32((unsigned int)bx * 0x9E3779B1u ^ hash32((unsigned int)by * 0x85EBCA77u + (unsigned int)stage)) ^
+         (unsigned int)e * 0xC2B2AE3Du;
+}
+
+// One Riemann solve of a face (every lane of the warp calls this; `active` lanes have a face).
+//  FACE_PLAIN:   acoustic start.
+//  FACE_LEARNED: start from the network's proposal where the warp's gate opens (warp-collective).
+//  FACE_HARVEST: acoustic start, and a hash-sampled subset of faces records inputs, p* and iterations.
+template <typename R, int MODE>
+__device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R b[4], bool active,
+                                           const FaceHook& hook, const MlpBlob* wsm, unsigned int key, R F[4],
+                                           TileCounters& cnt) {
+  static_assert(MODE == FACE_PLAIN || is_f32<R>(), "the harvest and the learned proposal are FP32 paths");
+  R guess = (R)0;
+  if constexpr (MODE == FACE_LEARNED) guess = learned_guess(a, b, active, wsm);
+  if (!active) return;
+  int it;
+  bool ok;
+  R pst;
+  riemann(s, a, b, guess, F, it, ok, &pst);
+  cnt.solves++;
+  cnt.iters += it;
+  cnt.nonconv += ok ? 0 : 1;
+  if constexpr (MODE == FACE_HARVEST) {
+    if (hash32(key ^ hook.hseed) < hook.hthresh) {
+      const unsigned long long k = atomicAdd(hook.hcount, 1ull);
+      if (k < hook.hcap) {
+        float* d = hook.hbuf + 8 * k;
+        d[0] = a[0]; d[1] = a[1]; d[2] = a[3]; d[3] = b[0]; d[4] = b[1]; d[5] = b[3]; d[6] = pst;
+        d[7] = (float)it;
+      }
+    }
+  }
+}
+
 // One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
 // smem_raw must hold TileLayout<R, TX, TY>::bytes.  Starts and ends with a block-wide barrier-free
-// state, so consecutive calls by the same block need one __syncthreads() between them.
-template <typename R, int TX, int TY, int NT>
+// state, so consecutive calls by the same block need one __syncthreads() between them.  MODE selects
+// the face-solve variant (face_solve); wsm is the network in shared memory for FACE_LEARNED.
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
                                          const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
-                                         unsigned char* smem_raw, TileCounters& cnt) {
+                                         unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
+                                         const MlpBlob* wsm = nullptr) {
   using L = TileLayout<R, TX, TY>;
   constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
   R* sq = reinterpret_cast<R*>(smem_raw);  // region A, stages 0-2: [4][QY][QX] primitives
@@ -162,39 +202,46 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   //         y faces: ly in [4, TY+5), columns [3, TX+5).  Results overwrite region A.
   {
     constexpr int nXF = (TX + 1) * SY, nYF = (TY + 1) * SX;
-    for (int e = tid; e < nXF + nYF; e += NT) {
-      R a[4], bq[4], F[4];
-      int it;
-      bool ok;
-      if (e < nXF) {
-        const int fx = e % (TX + 1), ry = e / (TX + 1);  // face index 0..TX <-> lx = fx + 4; row ly = ry + 3
-        const int cL = ry * SX + fx;                      // cell lx-1 = fx + 3 -> s index fx
-        const int cR = cL + 1;
+    // warp-uniform trip count: every lane of a warp runs the same iterations (the learned proposal is a
+    // warp-collective tensor-core computation); lanes past the end only take part in it
+    for (int e0 = tid - (tid & 31); e0 < nXF + nYF; e0 += NT) {
+      const int e = e0 + (tid & 31);
+      const bool active = e < nXF + nYF;
+      R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4];
+      if (active) {
+        if (e < nXF) {
+          const int fx = e % (TX + 1), ry = e / (TX + 1);  // face index 0..TX <-> lx = fx + 4; row ly = ry + 3
+          const int cL = ry * SX + fx;                      // cell lx-1 = fx + 3 -> s index fx
+          const int cR = cL + 1;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          a[m] = sxl[m * nC + cL];
-          bq[m] = sxr[m * nC + cR];
+          for (int m = 0; m < 4; ++m) {
+            a[m] = sxl[m * nC + cL];
+            bq[m] = sxr[m * nC + cR];
+          }
+        } else {
+          const int f = e - nXF;
+          const int cxs = f % SX, fy = f / SX;  // column s index; face 0..TY <-> ly = fy + 4
+          const int cL = fy * SX + cxs;          // cell ly-1 = fy + 3
+          const int cR = cL + SX;
+          a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
+          bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
         }
-        riemann(s, a, bq, (R)0, F, it, ok);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
-      } else {
-        const int f = e - nXF;
-        const int cxs = f % SX, fy = f / SX;  // column s index; face 0..TY <-> ly = fy + 4
-        const int cL = fy * SX + cxs;          // cell ly-1 = fy + 3
-        const int cR = cL + SX;
-        a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
-        bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
-        riemann(s, a, bq, (R)0, F, it, ok);
-        const int o = fy * SX + cxs;
-        sfyh[0 * (TY + 1) * SX + o] = F[0];
-        sfyh[1 * (TY + 1) * SX + o] = F[2];
-        sfyh[2 * (TY + 1) * SX + o] = F[1];
-        sfyh[3 * (TY + 1) * SX + o] = F[3];
       }
-      cnt.solves++;
-      cnt.iters += it;
-      cnt.nonconv += ok ? 0 : 1;
+      face_solve<R, MODE>(s, a, bq, active, hook, wsm, face_key(bx, by, 0, e), F, cnt);
+      if (active) {
+        if (e < nXF) {
+          const int fx = e % (TX + 1), ry = e / (TX + 1);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
+        } else {
+          const int f = e - nXF;
+          const int o = (f / SX) * SX + f % SX;
+          sfyh[0 * (TY + 1) * SX + o] = F[0];
+          sfyh[1 * (TY + 1) * SX + o] = F[2];
+          sfyh[2 * (TY + 1) * SX + o] = F[1];
+          sfyh[3 * (TY + 1) * SX + o] = F[3];
+        }
+      }
     }
   }
   __syncthreads();
@@ -202,26 +249,52 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   // ---- 4. transverse correction + final solves + artificial viscosity at the tile's faces
   {
     constexpr int nXF = (TX + 1) * TY, nYF = (TY + 1) * TX;
-    for (int e = tid; e < nXF + nYF; e += NT) {
-      R a[4], bq[4], F[4], UL[4], UR[4];
-      int it;
-      bool ok;
-      if (e < nXF) {
-        const int fx = e % (TX + 1), ty = e / (TX + 1);  // face lx = fx + 4, row ly = ty + 4
-        const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
-        // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
-        const int fL = ty * SX + fx, fR = fL + 1;
-        prim_to_cons(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
-        prim_to_cons(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+    for (int e0 = tid - (tid & 31); e0 < nXF + nYF; e0 += NT) {
+      const int e = e0 + (tid & 31);
+      const bool active = e < nXF + nYF;
+      R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4], UL[4], UR[4];
+      if (active) {
+        if (e < nXF) {
+          const int fx = e % (TX + 1), ty = e / (TX + 1);  // face lx = fx + 4, row ly = ty + 4
+          const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
+          // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
+          const int fL = ty * SX + fx, fR = fL + 1;
+          prim_to_cons(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
+          prim_to_cons(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const R* fy = sfyh + k * (TY + 1) * SX;
-          UL[k] = UL[k] - hy * (fy[fL + SX] - fy[fL]);
-          UR[k] = UR[k] - hy * (fy[fR + SX] - fy[fR]);
+          for (int k = 0; k < 4; ++k) {
+            const R* fy = sfyh + k * (TY + 1) * SX;
+            UL[k] = UL[k] - hy * (fy[fL + SX] - fy[fL]);
+            UR[k] = UR[k] - hy * (fy[fR + SX] - fy[fR]);
+          }
+          cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
+          cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
+        } else {
+          const int f = e - nXF;
+          const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
+          const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
+          // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
+          const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
+          prim_to_cons(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
+          prim_to_cons(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const R* fxh = sfxh + k * SY * (TX + 1);
+            UL[k] = UL[k] - hx * (fxh[fL + 1] - fxh[fL]);
+            UR[k] = UR[k] - hx * (fxh[fR + 1] - fxh[fR]);
+          }
+          R ql[4], qrr[4];
+          cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], ql[0], ql[1], ql[2], ql[3]);
+          cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], qrr[0], qrr[1], qrr[2], qrr[3]);
+          a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
+          bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
         }
-        cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
-        cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
-        riemann(s, a, bq, (R)0, F, it, ok);
+      }
+      face_solve<R, MODE>(s, a, bq, active, hook, wsm, face_key(bx, by, 1, e), F, cnt);
+      if (!active) continue;
+      if (e < nXF) {
+        const int fx = e % (TX + 1), ty = e / (TX + 1);
+        const int cL = (ty + 1) * SX + fx, cR = cL + 1;
         // artificial viscosity from the cell-centred velocities of the time-n state
         if (s.cvisc > (R)0) {
           R div;
@@ -242,22 +315,6 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         const int f = e - nXF;
         const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
         const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
-        // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
-        const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
-        prim_to_cons(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
-        prim_to_cons(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const R* fxh = sfxh + k * SY * (TX + 1);
-          UL[k] = UL[k] - hx * (fxh[fL + 1] - fxh[fL]);
-          UR[k] = UR[k] - hx * (fxh[fR + 1] - fxh[fR]);
-        }
-        R ql[4], qrr[4];
-        cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], ql[0], ql[1], ql[2], ql[3]);
-        cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], qrr[0], qrr[1], qrr[2], qrr[3]);
-        a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
-        bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
-        riemann(s, a, bq, (R)0, F, it, ok);
         R G[4] = {F[0], F[2], F[1], F[3]};
         if (s.cvisc > (R)0) {
           R div;
@@ -276,9 +333,6 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
 #pragma unroll
         for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
       }
-      cnt.solves++;
-      cnt.iters += it;
-      cnt.nonconv += ok ? 0 : 1;
     }
   }
   __syncthreads();

@@ -24,6 +24,11 @@ struct hydro_ctx {
   DevScratch* scr;  // device
   double* partials; // device, totals per-block partials
   DevScratch* host_scr;  // pinned host mirror for reads
+  // optional face-solve variants (FP32 contexts)
+  hydro::FaceHook hook;  // harvest buffer and counter, network weights
+  int harvest;           // 1: sample Riemann inputs and star pressures during steps
+  const hydro_mlp* mlp;  // learned starting pressure, used when p.use_learned_guess == 1
+  unsigned int step_calls;
   char err[512];
 };
 
@@ -59,7 +64,8 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
   if (p->precision != HYDRO_FP64 && p->precision != HYDRO_FP32) BAD("precision must be HYDRO_FP64 or HYDRO_FP32");
   if (p->precision == HYDRO_FP32 && (p->small_pres < 1e-30 || p->small_dens < 1e-30))
     BAD("FP32 floors must be normal float numbers (>= 1e-30)");
-  if (p->use_learned_guess != 0) BAD("use_learned_guess is reserved and must be 0");
+  if (p->use_learned_guess != 0 && p->use_learned_guess != 1) BAD("use_learned_guess must be 0 or 1");
+  if (p->use_learned_guess == 1 && p->precision != HYDRO_FP32) BAD("the learned proposal is an FP32 path");
   return 1;
 #undef BAD
 }
@@ -240,13 +246,59 @@ hydro_status hydro_cfl_dt(hydro_ctx* c, double* dt_out) {
   return HYDRO_OK;
 }
 
+// one CTU step on the context's stream with the face-solve variant its settings select
+static cudaError_t launch_step(hydro_ctx* c, const hydro::StepScalars& sc_host, const hydro::StepScalars* sc_dev) {
+  int mode = hydro::FACE_PLAIN;
+  if (c->p.use_learned_guess == 1) {
+    mode = hydro::FACE_LEARNED;
+    c->hook.mlp = (const hydro::MlpBlob*)hydro_mlp_device_blob(c->mlp);
+  } else if (c->harvest) {
+    mode = hydro::FACE_HARVEST;
+    c->hook.hseed = hydro::host_hash32(c->step_calls * 0x9E3779B1u + 0x6A09E667u);
+  }
+  ++c->step_calls;
+  return hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], sc_host, sc_dev, c->scr,
+                         c->stream, mode, &c->hook);
+}
+
+static hydro_status check_model(hydro_ctx* c) {
+  if (c->p.use_learned_guess == 1 && !c->mlp) {
+    set_err(c, "use_learned_guess = 1 needs a model (hydro_set_riemann_model)");
+    return HYDRO_EINVAL;
+  }
+  return HYDRO_OK;
+}
+
 hydro_status hydro_step(hydro_ctx* c, double dt) {
   if (!c || !(dt > 0.0) || !(dt < 1e300)) return HYDRO_EINVAL;
-  cudaError_t e =
-      hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur],
-                      hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy), nullptr, c->scr, c->stream);
+  if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  cudaError_t e = launch_step(c, hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy), nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "ctu_step");
   c->cur = 1 - c->cur;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_set_harvest(hydro_ctx* c, void* d_buf, unsigned long long capacity, double rate,
+                               unsigned long long* d_count) {
+  if (!c) return HYDRO_EINVAL;
+  if (!d_buf) {
+    c->harvest = 0;
+    return HYDRO_OK;
+  }
+  if (c->p.precision != HYDRO_FP32 || !d_count || capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
+    return HYDRO_EINVAL;
+  c->hook.hbuf = (float*)d_buf;
+  c->hook.hcount = d_count;
+  c->hook.hcap = capacity;
+  c->hook.hthresh = rate >= 1.0 ? 0xFFFFFFFFu : (unsigned int)(rate * 4294967296.0);
+  c->harvest = 1;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_set_riemann_model(hydro_ctx* c, const hydro_mlp* m) {
+  if (!c) return HYDRO_EINVAL;
+  if (m && c->p.precision != HYDRO_FP32) return HYDRO_EINVAL;
+  c->mlp = m;
   return HYDRO_OK;
 }
 
@@ -258,8 +310,8 @@ hydro_status hydro_cfl_dt_async(hydro_ctx* c, double tmax) {
 
 hydro_status hydro_step_device_dt(hydro_ctx* c) {
   if (!c) return HYDRO_EINVAL;
-  cudaError_t e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], hydro::StepScalars{},
-                                  &c->scr->sc, c->scr, c->stream);
+  if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  cudaError_t e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
   if (e != cudaSuccess) return cuda_fail(c, e, "step_device_dt");
   c->cur = 1 - c->cur;
   return HYDRO_OK;
@@ -267,12 +319,11 @@ hydro_status hydro_step_device_dt(hydro_ctx* c) {
 
 hydro_status hydro_advance(hydro_ctx* c, int nsteps, double tmax) {
   if (!c || nsteps < 0) return HYDRO_EINVAL;
+  if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
   for (int n = 0; n < nsteps; ++n) {
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
-    if (e == cudaSuccess)
-      e = hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], hydro::StepScalars{},
-                          &c->scr->sc, c->scr, c->stream);
+    if (e == cudaSuccess) e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
     if (e != cudaSuccess) return cuda_fail(c, e, "advance");
     c->cur = 1 - c->cur;
   }

@@ -323,7 +323,7 @@ __device__ __forceinline__ void face_flux(const SP<R>& s, R fr, R fu, R fv, R fp
 // side of the contact, Hugoniot star density, shock or linearly interpolated fan.  Returns the flux
 // (mass, normal momentum, transverse momentum, energy); iters/conv report the iteration.
 __device__ __forceinline__ void riemann(const SP<double>& s, const double qL[4], const double qR[4], double guess,
-                                        double F[4], int& iters, bool& conv) {
+                                        double F[4], int& iters, bool& conv, double* pstar_out = nullptr) {
   const double g = s.gamma, g1 = s.g1;
   const double rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
   const double rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
@@ -394,13 +394,14 @@ __device__ __forceinline__ void riemann(const SP<double>& s, const double qL[4],
     }
   }
   face_flux(s, fr, fu, fv, fp, F);
+  if (pstar_out) *pstar_out = pst;
 }
 
 // FP32 form of the same solver.  With a_K = 1 + (gamma+1)/(2 gamma)(p/p_K - 1) and t_K = 1/sqrt(a_K):
 // 1/W_K = t_K / C_K, W_K = C_K a_K t_K, and the Newton step -(u*_R - u*_L) / (1/Z_L + 1/Z_R) uses
 // 1/Z_K = (a_K + 1) t_K^3 / (2 C_K); one rsqrt per side and one reciprocal per iteration.
 __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], const float qR[4], float guess,
-                                        float F[4], int& iters, bool& conv) {
+                                        float F[4], int& iters, bool& conv, float* pstar_out = nullptr) {
   const float g = s.gamma, g1 = s.g1;
   const float rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
   const float rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
@@ -483,6 +484,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     }
   }
   face_flux(s, fr, fu, fv, fp, F);
+  if (pstar_out) *pstar_out = pst;
 }
 
 // CFL constraint of one interior cell at offset o (Eq. 6 with |u|+c): min(dx/(|u|+c), dy/(|v|+c)), folded

@@ -4,6 +4,7 @@
 
 #include "../../include/hydro.h"
 #include "hydro_device.cuh"
+#include "mlp.cuh"
 
 namespace hydro {
 
@@ -23,8 +24,20 @@ cudaError_t conserved_totals(int precision, const KParams& P, const void* U, dou
                              cudaStream_t stream);
 
 // One fused CTU step Uin -> Uout with the time-step factors from sc_dev if not NULL, else sc_host.
+// mode: FACE_PLAIN, FACE_HARVEST or FACE_LEARNED (the last two FP32 only; hook carries their buffers).
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
-                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
+                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode = 0,
+                     const FaceHook* hook = nullptr);
+
+// Host copy of the device hash32 (mlp.cuh), for per-step sampling seeds.
+inline unsigned int host_hash32(unsigned int x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
 
 // Kernel parameters of one problem from the public parameters (validated by the caller).
 void fill_kparams(const hydro_params* p, KParams* k);

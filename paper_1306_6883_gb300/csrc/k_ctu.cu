@@ -22,41 +22,56 @@ __device__ __forceinline__ void flush_counters(TileCounters& cnt, DevScratch* sc
   }
 }
 
-template <typename R, int TX, int TY, int NT>
+template <typename R, int TX, int TY, int NT, int MODE>
 __global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
                                                       StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
-                                                      DevScratch* __restrict__ scr) {
+                                                      DevScratch* __restrict__ scr, FaceHook hook) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the network's weights are read from global memory (L1/L2-resident) only by warps whose gate opens,
+  // which is rare in smooth flow, so no CTA pays to stage them
+  const MlpBlob* wsm = MODE == FACE_LEARNED ? hook.mlp : nullptr;
   SP<R> s;
   s.load(P);
   StepFactors<R> f;
   f.load(sc_dev ? *sc_dev : sc_host);
   TileCounters cnt;
-  ctu_tile<R, TX, TY, NT>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt);
+  ctu_tile<R, TX, TY, NT, MODE>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, hook, wsm);
   flush_counters(cnt, scr);
 }
 
-template <typename R, int TX, int TY, int NT>
+template <typename R, int TX, int TY, int NT, int MODE>
 cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
-                            const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream) {
+                            const StepScalars* sc_dev, DevScratch* scr, const FaceHook& hook, cudaStream_t stream) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
   static bool attr_set = false;  // per instantiation; the attribute is per function, not per device
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr);
+  ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook);
   return cudaGetLastError();
 }
 
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
-                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream) {
+                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode, const FaceHook* hook) {
+  const FaceHook h = hook ? *hook : FaceHook{};
   if (precision == 0)
-    return launch_ctu_step<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev, scr, stream);
-  return launch_ctu_step<float, 32, 16, 256>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev, scr, stream);
+    return launch_ctu_step<double, 16, 16, 256, FACE_PLAIN>(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev,
+                                                             scr, h, stream);
+  switch (mode) {
+    case FACE_HARVEST:
+      return launch_ctu_step<float, 32, 16, 256, FACE_HARVEST>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+                                                                scr, h, stream);
+    case FACE_LEARNED:
+      return launch_ctu_step<float, 32, 16, 256, FACE_LEARNED>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+                                                                scr, h, stream);
+    default:
+      return launch_ctu_step<float, 32, 16, 256, FACE_PLAIN>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+                                                              scr, h, stream);
+  }
 }
 
 }  // namespace hydro

@@ -62,6 +62,23 @@ SIGNATURES = {
     "hydro_conserved_totals_noalloc": (ctypes.c_int, [_PP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "hydro_upload": (ctypes.c_int, [_VP, _VP]),
     "hydro_download": (ctypes.c_int, [_VP, _VP]),
+    "hydro_mlp_create": (ctypes.c_int, [ctypes.c_ulonglong, _VP, ctypes.POINTER(_VP)]),
+    "hydro_mlp_destroy": (None, [_VP]),
+    "hydro_mlp_set_weights": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "hydro_mlp_get_weights": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "hydro_mlp_set_gate": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double]),
+    "hydro_mlp_gradient": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "hydro_mlp_train": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
+    "hydro_mlp_predict": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.c_int, _VP]),
+    "hydro_mlp_iterations": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_longlong)]),
+    "hydro_mlp_device_blob": (_VP, [_VP]),
+    "hydro_mlp_last_error": (ctypes.c_char_p, [_VP]),
+    "hydro_set_riemann_model": (ctypes.c_int, [_VP, _VP]),
+    "hydro_set_harvest": (ctypes.c_int, [_VP, _VP, ctypes.c_ulonglong, ctypes.c_double, _VP]),
     "hydro_batch_create": (ctypes.c_int, [ctypes.c_int, _PP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP,
                                           ctypes.POINTER(_VP)]),
     "hydro_batch_destroy": (None, [_VP]),
@@ -265,3 +282,80 @@ def hydro_batch_conserved_totals(b, member):
     out = (ctypes.c_double * 4)()
     _bcheck(load().hydro_batch_conserved_totals(b, int(member), out), b, "hydro_batch_conserved_totals")
     return list(out)
+
+
+# ---------------------------------------------------------------------------------------------------- learned proposal
+MLP_NPARAM = 4673
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def _mcheck(status, m, what):
+    if status != HYDRO_OK:
+        msg = load().hydro_mlp_last_error(m).decode() if m else ""
+        raise HydroError(status, f"{what}: {msg}")
+
+
+def hydro_mlp_create(seed, stream_ptr):
+    m = _VP()
+    _mcheck(load().hydro_mlp_create(int(seed), _VP(stream_ptr), ctypes.byref(m)), None, "hydro_mlp_create")
+    return m
+
+
+def hydro_mlp_destroy(m):
+    load().hydro_mlp_destroy(m)
+
+
+def hydro_mlp_set_weights(m, theta):
+    import numpy as np
+    a = np.ascontiguousarray(theta, dtype=np.float32)
+    assert a.size == MLP_NPARAM
+    _mcheck(load().hydro_mlp_set_weights(m, a.ctypes.data_as(_FP)), m, "hydro_mlp_set_weights")
+
+
+def hydro_mlp_get_weights(m):
+    import numpy as np
+    a = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _mcheck(load().hydro_mlp_get_weights(m, a.ctypes.data_as(_FP)), m, "hydro_mlp_get_weights")
+    return a
+
+
+def hydro_mlp_set_gate(m, gate_dp, gate_du):
+    _mcheck(load().hydro_mlp_set_gate(m, float(gate_dp), float(gate_du)), m, "hydro_mlp_set_gate")
+
+
+def hydro_mlp_gradient(m, d_samples_ptr, n):
+    import numpy as np
+    g = np.zeros(MLP_NPARAM, dtype=np.float32)
+    loss = ctypes.c_double()
+    _mcheck(load().hydro_mlp_gradient(m, _VP(d_samples_ptr), int(n), g.ctypes.data_as(_FP), ctypes.byref(loss)), m,
+            "hydro_mlp_gradient")
+    return g, loss.value
+
+
+def hydro_mlp_train(m, d_samples_ptr, n, steps, batch, lr, seed):
+    loss = ctypes.c_double()
+    _mcheck(load().hydro_mlp_train(m, _VP(d_samples_ptr), int(n), int(steps), int(batch), float(lr), int(seed),
+                                   ctypes.byref(loss)), m, "hydro_mlp_train")
+    return loss.value
+
+
+def hydro_mlp_predict(m, d_samples_ptr, n, use_tensor_cores, d_out_ptr):
+    _mcheck(load().hydro_mlp_predict(m, _VP(d_samples_ptr), int(n), 1 if use_tensor_cores else 0, _VP(d_out_ptr)),
+            m, "hydro_mlp_predict")
+
+
+def hydro_mlp_iterations(m, d_samples_ptr, n, learned, gamma=1.4, tol=1e-6, maxiter=16):
+    mean, nonconv = ctypes.c_double(), ctypes.c_longlong()
+    _mcheck(load().hydro_mlp_iterations(m, _VP(d_samples_ptr), int(n), 1 if learned else 0, float(gamma), float(tol),
+                                        int(maxiter), ctypes.byref(mean), ctypes.byref(nonconv)), m,
+            "hydro_mlp_iterations")
+    return mean.value, nonconv.value
+
+
+def hydro_set_riemann_model(ctx, m):
+    _check(load().hydro_set_riemann_model(ctx, m), ctx, "hydro_set_riemann_model")
+
+
+def hydro_set_harvest(ctx, d_buf_ptr, capacity, rate, d_count_ptr):
+    _check(load().hydro_set_harvest(ctx, _VP(d_buf_ptr) if d_buf_ptr else None, int(capacity), float(rate),
+                                    _VP(d_count_ptr) if d_count_ptr else None), ctx, "hydro_set_harvest")

@@ -166,3 +166,60 @@ class Ensemble:
         buf = self.bufs[i][0] if ptr == self.bufs[i][0].data_ptr() else self.bufs[i][1]
         torch.cuda.synchronize()
         return buf.view(4, NY, pitch)[:, :, :NX].cpu().numpy().copy()
+
+
+class Model:
+    """The learned starting-pressure network (hydro_mlp_*), trained on the GPU by the library's kernels."""
+
+    def __init__(self, seed=0, stream=None, device="cuda"):
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.m = H.hydro_mlp_create(seed, self.stream.cuda_stream)
+
+    def close(self):
+        if self.m is not None:
+            H.hydro_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def weights(self):
+        return H.hydro_mlp_get_weights(self.m)
+
+    def set_weights(self, theta):
+        H.hydro_mlp_set_weights(self.m, theta)
+
+    def set_gate(self, gate_dp, gate_du):
+        H.hydro_mlp_set_gate(self.m, gate_dp, gate_du)
+
+    def gradient(self, samples):
+        """samples: CUDA float32 tensor [n, 8]."""
+        return H.hydro_mlp_gradient(self.m, samples.data_ptr(), samples.shape[0])
+
+    def train(self, samples, steps, batch=4096, lr=1e-3, seed=1):
+        return H.hydro_mlp_train(self.m, samples.data_ptr(), samples.shape[0], steps, batch, lr, seed)
+
+    def predict(self, samples, tensor_cores=False):
+        out = torch.empty(samples.shape[0], dtype=torch.float32, device=samples.device)
+        H.hydro_mlp_predict(self.m, samples.data_ptr(), samples.shape[0], tensor_cores, out.data_ptr())
+        return out
+
+
+class Harvest:
+    """Device buffer that records Riemann problems (inputs, p*, iterations) during a Solver's steps."""
+
+    def __init__(self, solver, capacity, rate):
+        self.solver = solver
+        self.buf = torch.zeros((capacity, 8), dtype=torch.float32, device="cuda")
+        self.count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        H.hydro_set_harvest(solver.ctx, self.buf.data_ptr(), capacity, rate, self.count.data_ptr())
+
+    def stop(self):
+        H.hydro_set_harvest(self.solver.ctx, 0, 0, 0.0, 0)
+
+    def samples(self):
+        n = min(int(self.count.item()), self.buf.shape[0])
+        return self.buf[:n]

@@ -1,0 +1,196 @@
+"""The learned starting pressure of the two-shock iteration: harvest, GPU training kernels (gradients checked
+against the FP64 reference MLP), tensor-core inference, and the CTU step that uses it -- whose answer must
+stay the method's (the iteration still converges to the same tolerance)."""
+import numpy as np
+import pytest
+
+import hydro_problems as hp
+import oracle
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+NG = 4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_6883_gb300 import build
+    build.build()
+    t.cuda.set_device(0)
+    return t
+
+
+def _random_faces(n, seed):
+    """Synthetic Riemann problems with their converged star pressures from the FP64 oracle."""
+    rng = np.random.default_rng(seed)
+    P = oracle.params(8, 8, riemann_tol=1e-12)
+    out = np.zeros((n, 8), dtype=np.float32)
+    k = 0
+    while k < n:
+        rl, rr = np.exp(rng.uniform(np.log(0.1), np.log(2.0), 2))
+        pl, pr = np.exp(rng.uniform(np.log(0.01), np.log(10.0), 2))
+        ul, ur = rng.uniform(-1.5, 1.5, 2)
+        L = np.float32([rl, ul, 0.0, pl]).astype(np.float64)
+        R = np.float32([rr, ur, 0.0, pr]).astype(np.float64)
+        r = oracle.riemann(P, L, R)
+        if not r["converged"] or r["pstar"] < 1e-6:
+            continue
+        out[k] = [L[0], L[1], L[3], R[0], R[1], R[3], r["pstar"], r["iters"]]
+        k += 1
+    return out
+
+
+def _oracle_xt(s):
+    x, pref = omlp.features(*[s[:, i].astype(np.float64) for i in range(6)])
+    return x, np.log(s[:, 6].astype(np.float64) / pref)
+
+
+def test_gpu_gradient_matches_the_fp64_reference(torch):
+    from paper_1306_6883_gb300.solver import Model
+    s = _random_faces(300, seed=1)
+    m = Model(seed=7)
+    theta = m.weights().astype(np.float64)
+    d = torch.from_numpy(s).cuda()
+    g_gpu, loss_gpu = m.gradient(d)
+    x, t = _oracle_xt(s)
+    g_ref = omlp.gradient(theta, x, t)
+    assert loss_gpu == pytest.approx(omlp.loss(theta, x, t), rel=1e-4)
+    scale = np.abs(g_ref).max()
+    assert np.abs(g_gpu - g_ref).max() <= 1e-3 * scale, np.abs(g_gpu - g_ref).max() / scale
+    # every parameter block is exercised
+    for lo, hi in ((0, 384), (384, 448), (448, 4544), (4544, 4608), (4608, 4672), (4672, 4673)):
+        assert np.abs(g_gpu[lo:hi]).max() > 0
+    m.close()
+
+
+def test_predictions_match_the_reference_forward(torch):
+    from paper_1306_6883_gb300.solver import Model
+    s = _random_faces(500, seed=2)
+    m = Model(seed=3)
+    theta = m.weights().astype(np.float64)
+    d = torch.from_numpy(s).cuda()
+    x, _ = _oracle_xt(s)
+    y_ref, _ = omlp.forward(theta, x)
+    y32 = m.predict(d).cpu().numpy()
+    assert np.abs(y32 - y_ref).max() <= 1e-4 * (1 + np.abs(y_ref).max())
+    # BF16 weights and activations: about 3 significant digits
+    ytc = m.predict(d, tensor_cores=True).cpu().numpy()
+    assert np.abs(ytc - y_ref).max() <= 0.03 * (1 + np.abs(y_ref).max())
+    m.close()
+
+
+def test_training_lowers_the_loss_and_proposes_good_starts(torch):
+    from paper_1306_6883_gb300.solver import Model
+    train = torch.from_numpy(_random_faces(20000, seed=3)).cuda()
+    held = _random_faces(2000, seed=4)
+    m = Model(seed=5)
+    _, loss0 = m.gradient(torch.from_numpy(held).cuda())
+    m.train(train, steps=1500, batch=1024, lr=2e-3, seed=9)
+    _, loss1 = m.gradient(torch.from_numpy(held).cuda())
+    assert loss1 < 0.05 * loss0, (loss0, loss1)
+    # the trained proposal is closer to p* than the acoustic estimate on held-out faces
+    x, t = _oracle_xt(held)
+    y = m.predict(torch.from_numpy(held).cuda(), tensor_cores=True).cpu().numpy()
+    P = oracle.params(8, 8)
+    ac = []
+    for r in held:
+        cl = np.sqrt(1.4 * r[2] * r[0])
+        cr = np.sqrt(1.4 * r[5] * r[3])
+        p0 = max((cr * r[2] + cl * r[5] + cl * cr * (r[1] - r[4])) / (cl + cr), 1e-20)
+        ac.append(p0)
+    _, pref = omlp.features(*[held[:, i].astype(np.float64) for i in range(6)])
+    err_ml = np.abs(y - t)
+    err_ac = np.abs(np.log(np.array(ac) / pref) - t)
+    assert np.median(err_ml) < np.median(err_ac), (np.median(err_ml), np.median(err_ac))
+    m.close()
+
+
+def test_harvest_records_valid_riemann_problems(torch):
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Harvest, Solver, params_for
+    pr = hp.sod(64, 64)
+    s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
+    hv = Harvest(s, capacity=20000, rate=0.25)
+    s.advance(5)
+    st, stats = s.status()
+    smp = hv.samples().cpu().numpy()
+    n_total = int(hv.count.item())
+    # about a quarter of the 5 steps' solves were sampled
+    assert 0.2 * stats[0] < n_total < 0.3 * stats[0]
+    assert smp.shape[0] == min(n_total, 20000) and np.all(np.isfinite(smp))
+    P = oracle.params(8, 8, riemann_tol=1e-12)
+    for r in smp[:: max(1, len(smp) // 200)]:
+        res = oracle.riemann(P, [r[0], r[1], 0.0, r[2]], [r[3], r[4], 0.0, r[5]])
+        assert r[6] == pytest.approx(res["pstar"], rel=2e-5, abs=1e-12)
+    s.close()
+
+
+def _step(pr, learned_model=None, nsteps=1):
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+    s = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1 if learned_model else 0), pr.U)
+    if learned_model:
+        H.hydro_set_riemann_model(s.ctx, learned_model.m)
+    s.fill_ghost()
+    Uin = s.state_numpy()
+    dt = s.cfl_dt()
+    s.step(dt)
+    if nsteps > 1:
+        s.advance(nsteps - 1)
+    st, stats = s.status(raise_on_error=False)
+    out = s.state_numpy()
+    s.close()
+    return Uin, out, dt, st, stats
+
+
+def test_learned_start_leaves_the_answer_to_the_method(torch):
+    from paper_1306_6883_gb300.solver import Model
+    m = Model(seed=11)
+    m.train(torch.from_numpy(_random_faces(20000, seed=6)).cuda(), steps=800, batch=1024, lr=2e-3, seed=3)
+    m.set_gate(0.0, 0.0)  # every warp evaluates the network
+    for pr in (hp.quad(96, 80, seed=12), hp.sedov(96, 96, r_init=0.05), hp.sod(64, 64)):
+        Uin, plain, dt, st0, s0 = _step(pr)
+        _, learned, dt1, st1, s1 = _step(pr, m)
+        assert st0 == 0 and st1 == 0 and dt == dt1
+        # same converged fluxes to the FP32 tolerance: agreement with each other and with the oracle
+        ref = Uin.astype(np.float64)
+        po = oracle.params(pr.nx, pr.ny, bc=pr.bc)
+        oracle.fill_ghost(po, ref)
+        oracle.step(po, ref, dt)
+        for got in (plain, learned):
+            g = got[:, NG:-NG, NG:-NG].astype(np.float64)
+            r = ref[:, NG:-NG, NG:-NG]
+            scale = np.where(np.abs(r).reshape(4, -1).max(axis=1) > 0, np.abs(r).reshape(4, -1).max(axis=1), 1.0)
+            assert np.all(np.abs(g - r).reshape(4, -1).max(axis=1) <= 2e-5 * scale)
+        assert s1[0] == s0[0] and s1[2] == 0
+    m.close()
+
+
+def test_an_untrained_network_does_not_change_the_answer(torch):
+    # whatever the start, the iteration converges to the same star pressure (same result, no failures)
+    from paper_1306_6883_gb300.solver import Model
+    m = Model(seed=13)
+    m.set_gate(0.0, 0.0)
+    pr = hp.quad(64, 64, seed=14)
+    _, plain, _, _, s0 = _step(pr)
+    _, learned, _, st, s1 = _step(pr, m)
+    assert st == 0 and s1[2] == 0 and s1[0] == s0[0]
+    scale = np.abs(plain[:, NG:-NG, NG:-NG]).reshape(4, -1).max(axis=1)
+    err = np.abs(learned - plain)[:, NG:-NG, NG:-NG].reshape(4, -1).max(axis=1) / np.where(scale > 0, scale, 1)
+    assert np.all(err <= 4e-5), err
+    m.close()
+
+
+def test_learned_mode_requires_a_model(torch):
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+    pr = hp.sod(16, 8)
+    s = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1), pr.U)
+    s.fill_ghost()
+    with pytest.raises(H.HydroError) as e:
+        s.step(s.cfl_dt())
+    assert e.value.status == H.HYDRO_EINVAL
+    s.close()
