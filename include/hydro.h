@@ -130,7 +130,17 @@ hydro_status hydro_step_device_dt(hydro_ctx* ctx);
  * into device memory, clamp it so the simulated time does not pass tmax (tmax <= 0: no clamp), and step
  * with it.  No host synchronisation; time and step count stay on the device (hydro_get_time). */
 hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
-/* Equivalent to nsteps x {hydro_fill_ghost, hydro_cfl_dt_async(tmax), hydro_step_device_dt}. */
+/* Same results as nsteps x {hydro_fill_ghost, hydro_cfl_dt_async(tmax), hydro_step_device_dt}, run as
+ * nsteps x hydro_step_fused(tmax); the ghost cells of the final state are not filled. */
+
+/* One step of the driver loop as a single kernel launch: the step kernel reads ghost cells through the
+ * boundary conditions' map of the interior (the values hydro_fill_ghost would write, so no fill pass),
+ * and reduces the CFL time step of the state it writes (so no dt pass); its last block advances the
+ * device time by this step's dt and keeps the next step's dt (clamped to reach tmax when tmax > 0).  The
+ * first call after any other state change (hydro_step, hydro_step_device_dt, hydro_upload) computes this
+ * step's dt with one extra reduction.  FP32 contexts with a learned model or a harvest fall back to the
+ * three separate passes.  Asynchronous. */
+hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
 /* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */
 hydro_status hydro_get_time(hydro_ctx* ctx, double* t, long long* nsteps);

@@ -181,7 +181,8 @@ void oracle_trace(const oracle_params* p, double sigma, const double q[4], const
  *   W_K(p) = C_K sqrt(1 + (gamma+1)/(2 gamma) (p/p_K - 1)),
  * the star velocity seen from each side is u*_L = u_L - (p - p_L)/W_L, u*_R = u_R + (p - p_R)/W_R, and p*
  * solves u*_L(p) = u*_R(p).  Newton iteration with slopes Z_K = 2 W_K^3 / (W_K^2 + C_K^2)
- * (= |dp/du*| along each Hugoniot), started from the acoustic guess, stopped when |dp| <= tol p.
+ * (= |dp/du*| along each Hugoniot), started from the acoustic guess, stopped when |dp| <= tol p or when
+ * the velocity mismatch |dp| (1/Z_L + 1/Z_R) of the step is <= tol (|u_L| + |u_R| + c_L + c_R).
  * Sampling at x/t = 0: upwind side o from the sign of u*; star density from the Hugoniot
  * 1/rho* = 1/rho_o - (p* - p_o)/W_o^2; a shock (p* > p_o) moving at u_o -+ W_o/rho_o, else a fan between
  * u_o -+ c_o and u* -+ c*, interpolated linearly when the face lies inside it. */
@@ -193,6 +194,10 @@ int oracle_riemann(const oracle_params* p, const double qL[4], const double qR[4
   double rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
   double cl = sqrt(g * pl * rl);
   double cr = sqrt(g * pr * rr);
+  /* velocity scale |u_L| + |u_R| + c_L + c_R (c = C/rho): a Newton step |dp| equals a velocity mismatch
+   * |dp| (1/Z_L + 1/Z_R); the iteration also stops once that mismatch is below tol times this scale,
+   * which rounding allows even when p* << rho u^2 (where |dp| <= tol p* may be out of reach) */
+  double vscale = fabs(ul) + fabs(ur) + cl / rl + cr / rr;
   double pst;
   if (guess > 0.0) {
     pst = guess;
@@ -213,7 +218,7 @@ int oracle_riemann(const oracle_params* p, const double qL[4], const double qR[4
     double dp = fabs(pnew - pst);
     pst = pnew;
     ++it;
-    if (dp <= p->riemann_tol * pst) {
+    if (dp <= p->riemann_tol * pst || dp * (zl + zr) / (zl * zr) <= p->riemann_tol * vscale) {
       converged = 1;
       break;
     }

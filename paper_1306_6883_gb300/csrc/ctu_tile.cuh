@@ -94,12 +94,14 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
 // One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
 // smem_raw must hold TileLayout<R, TX, TY>::bytes.  Starts and ends with a block-wide barrier-free
 // state, so consecutive calls by the same block need one __syncthreads() between them.  MODE selects
-// the face-solve variant (face_solve); wsm is the network in shared memory for FACE_LEARNED.
-template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
+// the face-solve variant (face_solve); wsm is the network's weights for FACE_LEARNED.  FUSED: ghost cells
+// come from the boundary-condition map of the interior (no ghost fill needed) and the CFL constraint of
+// every new cell is folded into *cfl_min (no separate dt pass needed).
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false>
 __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
                                          const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
                                          unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
-                                         const MlpBlob* wsm = nullptr) {
+                                         const MlpBlob* wsm = nullptr, R* cfl_min = nullptr) {
   using L = TileLayout<R, TX, TY>;
   constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
   R* sq = reinterpret_cast<R*>(smem_raw);  // region A, stages 0-2: [4][QY][QX] primitives
@@ -121,13 +123,12 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   const int y0 = P.ng + by * TY;
   const size_t plane = (size_t)P.NY * P.pitch;
 
-  // ---- 0. load the tile (clamped to the array; clamped cells only feed cells outside the grid)
+  // ---- 0. load the tile.  FUSED: ghost cells are taken from the interior cells the boundary conditions
+  // map them to (the values a ghost fill would have written); otherwise the ghost cells are read as filled
+  // and indices past the array are clamped (such cells only feed cells outside the grid)
   for (int e = tid; e < QX * QY; e += NT) {
     const int lx = e % QX, ly = e / QX;
-    int gi = x0 - 4 + lx, gj = y0 - 4 + ly;
-    gi = gi < P.NX - 1 ? gi : P.NX - 1;
-    gj = gj < P.NY - 1 ? gj : P.NY - 1;
-    const size_t o = (size_t)gj * P.pitch + gi;
+    const size_t o = cell_offset<FUSED>(P, x0 - 4 + lx, y0 - 4 + ly);
     R rho, u, v, p;
     cons_to_prim(s, __ldg(Uin + o), __ldg(Uin + o + plane), __ldg(Uin + o + 2 * plane), __ldg(Uin + o + 3 * plane),
                  rho, u, v, p);
@@ -304,10 +305,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
           else
             div = (su[cR] - su[cL]) / s.dx + dvy / (4.0 * s.dy);
           const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
-          const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx (may be clamped)
-          const size_t o = (size_t)(gj < P.NY - 1 ? gj : P.NY - 1) * P.pitch + (gi < P.NX - 1 ? gi : P.NX - 1);
+          const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
+          const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi - 1, gj);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + o - 1 + k * plane) - __ldg(Uin + o + k * plane));
+          for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = F[k];  // only this face read sxl[cL]
@@ -325,10 +326,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             div = (sv[cR] - sv[cL]) / s.dy + dux / (4.0 * s.dx);
           const R av = s.cvisc * M<R>::mx(-div * s.dy, (R)0);
           const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
-          const size_t o = (size_t)(gj < P.NY - 1 ? gj : P.NY - 1) * P.pitch + (gi < P.NX - 1 ? gi : P.NX - 1);
+          const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi, gj - 1);
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            G[k] += av * (__ldg(Uin + o - P.pitch + k * plane) - __ldg(Uin + o + k * plane));
+            G[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
@@ -355,14 +356,16 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       Un[k] = __ldg(Uin + o + k * plane) + d;
       Uout[o + k * plane] = Un[k];
     }
-    if (!finite4(Un[0], Un[1], Un[2], Un[3])) {
+    if constexpr (FUSED) {
+      // the CFL constraint of the new state (Eq. 6), for the next step's time step
+      cfl_value(s, Un[0], Un[1], Un[2], Un[3], *cfl_min, flags);
+    } else if (!finite4(Un[0], Un[1], Un[2], Un[3])) {
       flags |= STATUS_NONFINITE;
     } else {
       const R ke = M<R>::dv((R)0.5 * (Un[1] * Un[1] + Un[2] * Un[2]), Un[0]);
       if (!(Un[0] > (R)0) || !(Un[3] - ke > (R)0)) flags |= STATUS_NEGATIVE;
     }
   }
-
 }
 
 }  // namespace hydro

@@ -29,6 +29,9 @@ struct hydro_ctx {
   int harvest;           // 1: sample Riemann inputs and star pressures during steps
   const hydro_mlp* mlp;  // learned starting pressure, used when p.use_learned_guess == 1
   unsigned int step_calls;
+  // fused steps: the factors of the next step are in scr->scf[fused_parity] when fused_valid
+  int fused_parity;
+  int fused_valid;
   char err[512];
 };
 
@@ -275,6 +278,35 @@ hydro_status hydro_step(hydro_ctx* c, double dt) {
   cudaError_t e = launch_step(c, hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy), nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "ctu_step");
   c->cur = 1 - c->cur;
+  c->fused_valid = 0;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
+  if (!c) return HYDRO_EINVAL;
+  if (c->p.use_learned_guess == 1 || c->harvest) {  // the optional face variants use the separate passes
+    if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+    cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
+    if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
+    if (e == cudaSuccess) e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance");
+    c->cur = 1 - c->cur;
+    c->fused_valid = 0;
+    return HYDRO_OK;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->fused_valid)  // factors of this step from the current state, time unchanged
+    e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 0, &c->scr->scf[c->fused_parity],
+                      c->stream);
+  if (e == cudaSuccess)
+    e = hydro::ctu_step_fused(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur],
+                              &c->scr->scf[c->fused_parity], &c->scr->scf[1 - c->fused_parity], c->scr, tmax,
+                              c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step_fused");
+  ++c->step_calls;
+  c->cur = 1 - c->cur;
+  c->fused_parity = 1 - c->fused_parity;
+  c->fused_valid = 1;
   return HYDRO_OK;
 }
 
@@ -314,18 +346,16 @@ hydro_status hydro_step_device_dt(hydro_ctx* c) {
   cudaError_t e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
   if (e != cudaSuccess) return cuda_fail(c, e, "step_device_dt");
   c->cur = 1 - c->cur;
+  c->fused_valid = 0;
   return HYDRO_OK;
 }
 
 hydro_status hydro_advance(hydro_ctx* c, int nsteps, double tmax) {
   if (!c || nsteps < 0) return HYDRO_EINVAL;
-  if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  c->fused_valid = 0;  // tmax may differ from the previous call's
   for (int n = 0; n < nsteps; ++n) {
-    cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
-    if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
-    if (e == cudaSuccess) e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
-    if (e != cudaSuccess) return cuda_fail(c, e, "advance");
-    c->cur = 1 - c->cur;
+    hydro_status s = hydro_step_fused(c, tmax);
+    if (s != HYDRO_OK) return s;
   }
   return HYDRO_OK;
 }
@@ -371,6 +401,7 @@ hydro_status hydro_upload(hydro_ctx* c, const void* host) {
   const size_t w = (size_t)c->kp.NX * es, pitchb = (size_t)c->kp.pitch * es;
   cudaError_t e = cudaMemcpy2DAsync(c->state[c->cur], pitchb, host, w, w, (size_t)4 * c->kp.NY,
                                     cudaMemcpyHostToDevice, c->stream);
+  c->fused_valid = 0;
   return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "upload");
 }
 

@@ -66,6 +66,12 @@ struct DevScratch {
   unsigned int pad_;
   unsigned long long stats[3];     // riemann solves, iterations, unconverged solves
   double totals[4];                // last conserved totals
+  // fused steps: factors of the current and of the next step (alternating), next-dt accumulator and
+  // last-block detection of the step kernel
+  StepScalars scf[2];
+  unsigned long long dtn_min_bits;
+  unsigned int step_blocks_done;
+  unsigned int pad2_;
 };
 
 enum : unsigned int {
@@ -329,6 +335,8 @@ __device__ __forceinline__ void riemann(const SP<double>& s, const double qL[4],
   const double rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
   const double cl = sqrt(g * pl * rl);
   const double cr = sqrt(g * pr * rr);
+  // stop also once the step's velocity mismatch |dp| (1/Z_L + 1/Z_R) is below tol times the velocity scale
+  const double vscale = fabs(ul) + fabs(ur) + cl / rl + cr / rr;
   double pst = guess > 0.0 ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) / (cl + cr);
   pst = pst < s.small_pres ? s.small_pres : pst;
   int it = 0;
@@ -345,7 +353,7 @@ __device__ __forceinline__ void riemann(const SP<double>& s, const double qL[4],
     double dp = fabs(pnew - pst);
     pst = pnew;
     ++it;
-    if (dp <= s.tol * pst) {
+    if (dp <= s.tol * pst || dp * (zl + zr) / (zl * zr) <= s.tol * vscale) {
       ok = true;
       break;
     }
@@ -490,9 +498,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
 // CFL constraint of one interior cell at offset o (Eq. 6 with |u|+c): min(dx/(|u|+c), dy/(|v|+c)), folded
 // into rbest; non-finite and non-positive cells set status bits instead.
 template <typename R>
-__device__ __forceinline__ void cfl_cell(const SP<R>& s, const R* __restrict__ U, size_t o, size_t plane, R& rbest,
-                                         unsigned int& flags) {
-  const R U0 = U[o], U1 = U[o + plane], U2 = U[o + 2 * plane], U3 = U[o + 3 * plane];
+__device__ __forceinline__ void cfl_value(const SP<R>& s, R U0, R U1, R U2, R U3, R& rbest, unsigned int& flags) {
   if (!finite4(U0, U1, U2, U3)) {
     flags |= STATUS_NONFINITE;
     return;
@@ -508,6 +514,29 @@ __device__ __forceinline__ void cfl_cell(const SP<R>& s, const R* __restrict__ U
   const R ty = M<R>::dv(s.dy, M<R>::ab(v) + cs);
   const R t = M<R>::mn(tx, ty);
   rbest = t < rbest ? t : rbest;
+}
+
+template <typename R>
+__device__ __forceinline__ void cfl_cell(const SP<R>& s, const R* __restrict__ U, size_t o, size_t plane, R& rbest,
+                                         unsigned int& flags) {
+  cfl_value(s, U[o], U[o + plane], U[o + 2 * plane], U[o + 3 * plane], rbest, flags);
+}
+
+// Source cell of a tile cell at padded index (gi, gj).  BCMAP: ghost and out-of-array positions map to
+// the interior cell the boundary conditions assign them (periodic wrap, outflow clamp), i.e. the value a
+// ghost fill would have written; otherwise the padded array is read as is, clamped to its extent.
+template <bool BCMAP>
+__device__ __forceinline__ size_t cell_offset(const KParams& P, int gi, int gj) {
+  if constexpr (BCMAP) {
+    int ki = gi - P.ng, kj = gj - P.ng;
+    if (ki < 0 || ki >= P.nx) ki = P.bc[0] == 1 ? ((ki % P.nx) + P.nx) % P.nx : (ki < 0 ? 0 : P.nx - 1);
+    if (kj < 0 || kj >= P.ny) kj = P.bc[2] == 1 ? ((kj % P.ny) + P.ny) % P.ny : (kj < 0 ? 0 : P.ny - 1);
+    return (size_t)(kj + P.ng) * P.pitch + (ki + P.ng);
+  } else {
+    gi = gi < P.NX - 1 ? gi : P.NX - 1;
+    gj = gj < P.NY - 1 ? gj : P.NY - 1;
+    return (size_t)gj * P.pitch + gi;
+  }
 }
 
 }  // namespace hydro

@@ -14,8 +14,15 @@ cudaError_t fill_ghost(int precision, const KParams& P, void* U, cudaStream_t st
 // CFL reduction.  Writes scr->dt = cfl * min(...), clamped to tmax - scr->t when tmax > 0 and, if
 // advance_time, adds it to scr->t and increments scr->nsteps.  Sets status bits for non-finite or
 // non-positive cells.  The min accumulator and block counter are reset by the last block.
+// sc_out (optional): also receives the step factors.
 cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* scr, double tmax, int advance_time,
-                   double* partial_unused, cudaStream_t stream);
+                   StepScalars* sc_out, cudaStream_t stream);
+
+// One fused CTU step (ghost cells from the boundary map, CFL of the new state folded in): reads the step
+// factors at sc_cur; the last block adds sc_cur->dt to the time, counts the step and writes the next step's
+// factors (dt = cfl * min, clamped to tmax - t when tmax > 0) to sc_next.
+cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
+                           StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
 
 // Conserved totals into scr->totals (deterministic two-level reduction; partials has room for
 // totals_max_blocks() * 4 doubles).

@@ -61,7 +61,8 @@ constexpr int DT_MAX_BLOCKS = 4 * 152;
 
 template <typename R>
 __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* __restrict__ U,
-                                                           DevScratch* __restrict__ scr, double tmax, int advance) {
+                                                           DevScratch* __restrict__ scr, double tmax, int advance,
+                                                           StepScalars* __restrict__ sc_out) {
   SP<R> s;
   s.load(P);
   const size_t plane = (size_t)P.NY * P.pitch;
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
     }
     scr->dt = dt;
     scr->sc = make_step_scalars(dt, P.dx, P.dy);
+    if (sc_out) *sc_out = scr->sc;
     if (advance) {
       scr->t = scr->t + dt;
       scr->nsteps = scr->nsteps + 1;
@@ -125,14 +127,14 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
 }
 
 cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* scr, double tmax, int advance_time,
-                   double*, cudaStream_t stream) {
+                   StepScalars* sc_out, cudaStream_t stream) {
   const long long ncell = (long long)P.nx * P.ny;
   long long b = (ncell + DT_THREADS - 1) / DT_THREADS;
   const int blocks = (int)(b < DT_MAX_BLOCKS ? b : DT_MAX_BLOCKS);
   if (precision == 0)
-    cfl_dt_kernel<double><<<blocks, DT_THREADS, 0, stream>>>(P, (const double*)U, scr, tmax, advance_time);
+    cfl_dt_kernel<double><<<blocks, DT_THREADS, 0, stream>>>(P, (const double*)U, scr, tmax, advance_time, sc_out);
   else
-    cfl_dt_kernel<float><<<blocks, DT_THREADS, 0, stream>>>(P, (const float*)U, scr, tmax, advance_time);
+    cfl_dt_kernel<float><<<blocks, DT_THREADS, 0, stream>>>(P, (const float*)U, scr, tmax, advance_time, sc_out);
   return cudaGetLastError();
 }
 
@@ -209,6 +211,8 @@ __global__ void init_scratch_kernel(DevScratch* scr) {
   scr->status = 0u;
   scr->stats[0] = scr->stats[1] = scr->stats[2] = 0ull;
   for (int k = 0; k < 4; ++k) scr->totals[k] = 0.0;
+  scr->dtn_min_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
+  scr->step_blocks_done = 0u;
 }
 
 cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream) {

@@ -1,4 +1,6 @@
 // Single-problem fused CTU step kernel: one CTA per tile (the tile itself is in ctu_tile.cuh).
+#include <float.h>
+
 #include "ctu_tile.cuh"
 #include "hydro_kernels.h"
 
@@ -53,6 +55,85 @@ cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepS
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook);
   return cudaGetLastError();
+}
+
+// Fused step: the tile reads ghost cells through the boundary map and folds the CFL constraint of its new
+// cells into a block minimum; the last block to finish advances the time by this step's dt and writes
+// the next step's factors, so a run needs one launch per step and no ghost-fill or dt pass.
+template <typename R, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) ctu_step_fused_kernel(KParams P, const R* __restrict__ Uin,
+                                                            R* __restrict__ Uout, const StepScalars* __restrict__ sc_cur,
+                                                            StepScalars* __restrict__ sc_next,
+                                                            DevScratch* __restrict__ scr, double tmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SP<R> s;
+  s.load(P);
+  StepFactors<R> f;
+  f.load(*sc_cur);
+  TileCounters cnt;
+  R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
+  ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
+                                            nullptr, &cmin);
+  flush_counters(cnt, scr);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const R o = __shfl_xor_sync(0xffffffffu, cmin, off);
+    cmin = o < cmin ? o : cmin;
+  }
+  __shared__ R wmin[NT / 32];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = cmin;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R b = wmin[0];
+    for (int k = 1; k < NT / 32; ++k) b = wmin[k] < b ? wmin[k] : b;
+    atomicMin(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong((double)b));
+    __threadfence();
+    last = atomicAdd(&scr->step_blocks_done, 1u) == gridDim.x * gridDim.y - 1u;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long bits =
+        atomicExch(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
+    const double t = scr->t + sc_cur->dt;
+    scr->t = t;
+    scr->nsteps = scr->nsteps + 1;
+    double dt = P.cfl * __longlong_as_double((long long)bits);
+    if (tmax > 0.0) {
+      const double left = tmax - t;
+      dt = dt > left ? left : dt;
+      dt = dt < 0.0 ? 0.0 : dt;
+    }
+    scr->dt = dt;
+    *sc_next = make_step_scalars(dt, P.dx, P.dy);
+    scr->step_blocks_done = 0u;
+  }
+}
+
+template <typename R, int TX, int TY, int NT>
+cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
+                                  StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+  const size_t smem = TileLayout<R, TX, TY>::bytes;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ctu_step_fused_kernel<R, TX, TY, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax);
+  return cudaGetLastError();
+}
+
+cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
+                           StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+  if (precision == 0)
+    return launch_ctu_step_fused<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax,
+                                                      stream);
+  return launch_ctu_step_fused<float, 32, 16, 256>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax,
+                                                   stream);
 }
 
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,

@@ -85,8 +85,10 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Network output y for the face of every lane of the warp (all 32 lanes must call it).
-__device__ __forceinline__ float mlp_warp_forward(const float x[6], const MlpBlob* __restrict__ w) {
+// Network output y for the face of every lane of the warp (all 32 lanes must call it).  Not inlined: the
+// CTU face loops call it rarely (gated), and keeping its unrolled tensor-core code and registers out of
+// those loops leaves their register allocation and instruction footprint as in the plain kernel.
+static __device__ __noinline__ float mlp_warp_forward(const float x[6], const MlpBlob* __restrict__ w) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float yv[2][2];  // [m tile][row half] partial outputs of rows 16 mt + g + 8 half
   // one m tile at a time keeps the live fragments to ~40 registers (weights are re-read from shared memory)

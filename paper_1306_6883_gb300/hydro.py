@@ -56,6 +56,7 @@ SIGNATURES = {
     "hydro_advance": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double]),
     "hydro_cfl_dt_async": (ctypes.c_int, [_VP, ctypes.c_double]),
     "hydro_step_device_dt": (ctypes.c_int, [_VP]),
+    "hydro_step_fused": (ctypes.c_int, [_VP, ctypes.c_double]),
     "hydro_get_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "hydro_conserved_totals": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "hydro_sync_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -176,6 +177,10 @@ def hydro_cfl_dt_async(ctx, tmax=0.0):
 
 def hydro_step_device_dt(ctx):
     _check(load().hydro_step_device_dt(ctx), ctx, "hydro_step_device_dt")
+
+
+def hydro_step_fused(ctx, tmax=0.0):
+    _check(load().hydro_step_fused(ctx, float(tmax)), ctx, "hydro_step_fused")
 
 
 def hydro_get_time(ctx):

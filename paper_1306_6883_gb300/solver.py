@@ -59,6 +59,9 @@ class Solver:
     def step_device_dt(self):
         H.hydro_step_device_dt(self.ctx)
 
+    def step_fused(self, tmax=0.0):
+        H.hydro_step_fused(self.ctx, tmax)
+
     def upload(self, host_tensor):
         """Enqueue a copy of a pinned host tensor (4, NY, NX) into the current state."""
         H.hydro_upload(self.ctx, host_tensor.data_ptr())

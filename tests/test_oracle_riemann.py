@@ -136,6 +136,28 @@ def test_supersonic_flow_takes_the_upwind_state():
     np.testing.assert_array_equal(r["face"], q)
 
 
+def test_strong_expansions_converge_and_match_bisection():
+    # p* << rho u^2: rounding bounds |dp| near the root by ~eps rho u c, so the velocity-scale stopping
+    # rule is what ends these iterations; the root still agrees with an independent bisection
+    rng = np.random.default_rng(22)
+    for _ in range(500):
+        rho, c_over_u = float(np.exp(rng.uniform(-1, 1))), 10 ** rng.uniform(-2.5, -0.5)
+        u = rng.uniform(0.5, 3.0)
+        p = rho * (c_over_u * u) ** 2 / G
+        L, R = [rho, -0.3 * u, 0.0, p], [rho * 1.3, 0.2 * u, 0.0, 0.7 * p]
+        r = oracle.riemann(P, L, R)
+        assert r["converged"] and r["iters"] <= 12
+        f = lambda x: _two_shock_residual(x, (L[0], L[1], L[3]), (R[0], R[1], R[3]))
+        if f(1e-20) >= 0:
+            assert r["pstar"] == 1e-20
+            continue
+        lo, hi = 1e-20, max(L[3], R[3])
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if f(mid) < 0 else (lo, mid)
+        assert r["pstar"] == pytest.approx(0.5 * (lo + hi), rel=1e-9)
+
+
 def test_nonconvergence_is_reported():
     p1 = oracle.params(8, 8, riemann_maxiter=1, riemann_tol=1e-14)
     r = oracle.riemann(p1, [1.0, 0.0, 0.0, 1.0], [0.125, 0.0, 0.0, 0.1])
