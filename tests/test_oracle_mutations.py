@@ -1,0 +1,59 @@
+"""The pins catch plausible mistakes: each case plants one mistake in a copy of the oracle's C source (on the
+CPU, in a temporary directory), rebuilds it and runs the pin suite against it, which must fail."""
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "transverse correction dropped": [
+        ("UL[k] = UL[k] - hy * (AT(fyh, k, j + 1, f - 1) - AT(fyh, k, j, f - 1));\n"
+         "        UR[k] = UR[k] - hy * (AT(fyh, k, j + 1, f) - AT(fyh, k, j, f));", "UL[k] = UL[k]; UR[k] = UR[k];"),
+        ("UL[k] = UL[k] - hx * (AT(fxh, k, gg - 1, i + 1) - AT(fxh, k, gg - 1, i));\n"
+         "        UR[k] = UR[k] - hx * (AT(fxh, k, gg, i + 1) - AT(fxh, k, gg, i));", "UL[k] = UL[k]; UR[k] = UR[k];")],
+    "transverse factor 1 instead of 1/2": [
+        ("const double hx = 0.5 * dt / dx, hy = 0.5 * dt / dy;", "const double hx = dt / dx, hy = dt / dy;")],
+    "tracing reference speed": [
+        ("double sl = q[m] + 0.5 * (1.0 - sigma * lam[3]) * dq[m];", "double sl = q[m] + 0.5 * (1.0 - sigma * lam[0]) * dq[m];")],
+    "left eigenvector sign": [
+        ("{{0.0, -0.5 * rho / c, 0.0, 0.5 / (c * c)},", "{{0.0, 0.5 * rho / c, 0.0, 0.5 / (c * c)},")],
+    "fourth-order slope constant": [("double d4 = (4.0 / 3.0) * dc", "double d4 = (1.0) * dc")],
+    "flattening compression test": [("int compress = (um1 - up1) > 0.0;", "int compress = (um1 - up1) < 0.0;")],
+    "shock mass flux": [("const double g1 = (g + 1.0) / (2.0 * g);", "const double g1 = (g + 1.0) / (2.0);")],
+    "star density sign": [("double rst = 1.0 / (1.0 / ro - (pst - po) / (wo * wo));",
+                           "double rst = 1.0 / (1.0 / ro + (pst - po) / (wo * wo));")],
+    "energy flux": [("F[3] = un * (rhoE + pres);", "F[3] = un * (rhoE);")],
+    "artificial viscosity strength": [
+        ("double av = p->cvisc * fmax(-div * dx, 0.0);", "double av = 10 * p->cvisc * fmax(-div * dx, 0.0);"),
+        ("double av = p->cvisc * fmax(-div * dy, 0.0);", "double av = 10 * p->cvisc * fmax(-div * dy, 0.0);")],
+}
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS))
+def test_pins_catch_the_planted_mistake(name):
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    d = tempfile.mkdtemp(prefix="oracle_mut_")
+    try:
+        for sub in ("oracle", "tests", "hydro_problems"):
+            shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub),
+                            ignore=shutil.ignore_patterns("*.so", "__pycache__", "test_oracle_mutations.py"))
+        shutil.copy(os.path.join(ROOT, "pytest.ini"), d)
+        path = os.path.join(d, "oracle", "oracle.c")
+        src = open(path).read()
+        for a, b in MUTATIONS[name]:
+            assert src.count(a) == 1, a
+            src = src.replace(a, b)
+        open(path, "w").write(src)
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                            "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py"],
+                           cwd=d, capture_output=True, text=True, timeout=600)
+        assert r.returncode != 0, f"mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
+        assert "FAILED" in r.stdout
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
