@@ -9,8 +9,9 @@
 //   3. Riemann solves on the traced (hat) states at all faces the transverse terms need
 //   4. transverse correction + final Riemann solves + artificial viscosity at the tile's faces
 //   5. conservative update (Eq. 5), written to the other state buffer
-// Global traffic per cell is one read of U (plus the halo and an L1/L2 re-read of U^n at the faces for
-// the viscosity term) and one write of U^{n+1}.
+// Global traffic per cell is one read of U (plus the halo) and one write of U^{n+1}.  FP32 tiles keep U^n
+// of the traced cells in shared memory for the viscosity term and the update; FP64 tiles (whose shared
+// memory is twice as large per cell) re-read it through L1/L2.
 //
 // Shared memory is reused across stages: the hat fluxes of stage 3 overwrite the primitive tile (dead
 // after stage 2; the velocities the viscosity needs are kept separately), and each final flux of stage 4
@@ -26,13 +27,18 @@ template <typename R, int TX, int TY>
 struct TileLayout {
   static constexpr int QX = TX + 8, QY = TY + 8;  // primitive tile with a 4-cell halo
   static constexpr int SX = TX + 2, SY = TY + 2;  // cells whose face states are traced
+  static constexpr int QP = QX;  // row pitch of the primitive tile
+  // FP32 tiles keep the conserved values of the traced cells for the viscosity term (no global re-read);
+  // FP64 tiles re-read them from L2 to keep 3 CTAs per SM
+  static constexpr bool SMEM_U = sizeof(R) == 4;
   static constexpr int nC = SX * SY;
-  static constexpr int nQ = 4 * QX * QY;
+  static constexpr int nQ = 4 * QP * QY;
   static constexpr int nFXH = 4 * SY * (TX + 1);  // hat x fluxes: rows [3, TY+5), faces [4, TX+5)
   static constexpr int nFYH = 4 * (TY + 1) * SX;  // hat y fluxes: faces [4, TY+5), columns [3, TX+5)
   static constexpr int nA = (nQ + nC) > (nFXH + nFYH) ? (nQ + nC) : (nFXH + nFYH);  // region A
   static constexpr int nS = 4 * nC;               // one traced-state family
-  static constexpr int elems = nA + 4 * nS + 2 * nC;
+  static constexpr int nU = SMEM_U ? 4 * nC : 0;
+  static constexpr int elems = nA + 4 * nS + 2 * nC + nU;
   static constexpr size_t bytes = sizeof(R) * (size_t)elems;
 };
 
@@ -103,8 +109,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
                                          unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
                                          const MlpBlob* wsm = nullptr, R* cfl_min = nullptr) {
   using L = TileLayout<R, TX, TY>;
-  constexpr int QX = L::QX, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
-  R* sq = reinterpret_cast<R*>(smem_raw);  // region A, stages 0-2: [4][QY][QX] primitives
+  constexpr int QX = L::QX, QP = L::QP, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
+  // row width of the y-face items of stage 4 and the cells of stage 5: SX when that makes every warp one
+  // row (consecutive, conflict-free shared-memory addresses; lanes past TX idle), else TX
+  constexpr int RW = SX % 32 == 0 ? SX : TX;
+  R* sq = reinterpret_cast<R*>(smem_raw);  // region A, stages 0-2: [4][QY][QP] primitives (row pitch QP)
   R* sxi = sq + L::nQ;                      //                         [SY][SX] flattening
   R* sfxh = sq;                             // region A, stages 3-4: [4][SY][TX+1] hat x fluxes
   R* sfyh = sq + L::nFXH;                   //                         [4][TY+1][SX] hat y fluxes
@@ -114,6 +123,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   R* syr = syl + L::nS;                     // upper state at j-1/2
   R* su = syr + L::nS;                      // [SY][SX] cell velocities for the viscosity
   R* sv = su + nC;
+  R* sU = sv + nC;                          // [4][SY][SX] conserved values of the traced cells (FP32)
 
   const R sigx = f.sigx, sigy = f.sigy, hx = f.hx, hy = f.hy;
   const R ux = sigx, uy = sigy;  // update factors dt/dx, dt/dy (Eq. 5)
@@ -130,22 +140,33 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     const int lx = e % QX, ly = e / QX;
     const size_t o = cell_offset<FUSED>(P, x0 - 4 + lx, y0 - 4 + ly);
     R rho, u, v, p;
-    cons_to_prim(s, __ldg(Uin + o), __ldg(Uin + o + plane), __ldg(Uin + o + 2 * plane), __ldg(Uin + o + 3 * plane),
-                 rho, u, v, p);
-    sq[e] = rho;
-    sq[QX * QY + e] = u;
-    sq[2 * QX * QY + e] = v;
-    sq[3 * QX * QY + e] = p;
+    const R U0 = __ldg(Uin + o), U1 = __ldg(Uin + o + plane), U2 = __ldg(Uin + o + 2 * plane),
+            U3 = __ldg(Uin + o + 3 * plane);
+    cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
+    if constexpr (L::SMEM_U) {
+      if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
+        const int c = (ly - 3) * SX + (lx - 3);
+        sU[c] = U0;
+        sU[nC + c] = U1;
+        sU[2 * nC + c] = U2;
+        sU[3 * nC + c] = U3;
+      }
+    }
+    const int d = ly * QP + lx;
+    sq[d] = rho;
+    sq[QP * QY + d] = u;
+    sq[2 * QP * QY + d] = v;
+    sq[3 * QP * QY + d] = p;
   }
   __syncthreads();
 
-  const R* qu = sq + QX * QY;
-  const R* qv = sq + 2 * QX * QY;
-  const R* qp = sq + 3 * QX * QY;
+  const R* qu = sq + QP * QY;
+  const R* qv = sq + 2 * QP * QY;
+  const R* qp = sq + 3 * QP * QY;
   // ---- 1. flattening xi = min(xi_x, xi_y) on cells lx in [3, TX+5), ly in [3, TY+5); keep u, v there
   for (int e = tid; e < nC; e += NT) {
     const int cx = e % SX + 3, cy = e / SX + 3;
-    const int b = cy * QX + cx;
+    const int b = cy * QP + cx;
     R xi = (R)1;
     if (s.flatten) {
       auto chix = [&](int m) {
@@ -153,11 +174,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
                               s.small_pres);
       };
       auto chiy = [&](int m) {
-        return flatten_chi<R>(qp[b + (m - 2) * QX], qp[b + (m - 1) * QX], qp[b + (m + 1) * QX], qp[b + (m + 2) * QX],
-                              qv[b + (m - 1) * QX], qv[b + (m + 1) * QX], s.small_pres);
+        return flatten_chi<R>(qp[b + (m - 2) * QP], qp[b + (m - 1) * QP], qp[b + (m + 1) * QP], qp[b + (m + 2) * QP],
+                              qv[b + (m - 1) * QP], qv[b + (m + 1) * QP], s.small_pres);
       };
       const int sx = (qp[b + 1] - qp[b - 1]) >= (R)0 ? 1 : -1;
-      const int sy = (qp[b + QX] - qp[b - QX]) >= (R)0 ? 1 : -1;
+      const int sy = (qp[b + QP] - qp[b - QP]) >= (R)0 ? 1 : -1;
       const R xix = M<R>::mn(chix(0), chix(-sx));
       const R xiy = M<R>::mn(chiy(0), chiy(-sy));
       xi = M<R>::mn(xix, xiy);
@@ -168,20 +189,23 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   }
   __syncthreads();
 
-  // ---- 2. slopes + tracing for the same cells; items [0, nC) trace in x, [nC, 2 nC) in y
-  for (int e = tid; e < 2 * nC; e += NT) {
-    const bool ydir = e >= nC;
-    const int c = ydir ? e - nC : e;
+  // ---- 2. slopes + tracing for the same cells; items [0, nC) trace in x, [nCa, nCa + nC) in y (the y
+  // items start at a warp boundary so no warp mixes the two directions)
+  constexpr int nCa = (nC + 31) / 32 * 32;
+  for (int e = tid; e < nCa + nC; e += NT) {
+    const bool ydir = e >= nCa;
+    const int c = ydir ? e - nCa : e;
+    if (c >= nC) continue;
     const int cx = c % SX + 3, cy = c / SX + 3;
-    const int b = cy * QX + cx;
-    const int st = ydir ? QX : 1;
+    const int b = cy * QP + cx;
+    const int st = ydir ? QP : 1;
     const R xi = sxi[c];
     R q[4], dq[4];
     // face frame: (rho, un, ut, p); in y un = v, ut = u
     const int kmap[4] = {0, ydir ? 2 : 1, ydir ? 1 : 2, 3};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const R* a = sq + kmap[m] * QX * QY + b;
+      const R* a = sq + kmap[m] * QP * QY + b;
       q[m] = a[0];
       dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
     }
@@ -202,17 +226,20 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   // ---- 3. hat Riemann solves.  x faces: lx in [4, TX+5) between cells lx-1 and lx, rows [3, TY+5).
   //         y faces: ly in [4, TY+5), columns [3, TX+5).  Results overwrite region A.
   {
-    constexpr int nXF = (TX + 1) * SY, nYF = (TY + 1) * SX;
+    // x-face items run over rows of SX (the last item of each row idle) so a warp's shared-memory reads
+    // stay on consecutive addresses of the SX-wide arrays; y-face items start at a warp boundary
+    constexpr int nXI = SX * SY, nXIa = (nXI + 31) / 32 * 32, nYF = (TY + 1) * SX;
     // warp-uniform trip count: every lane of a warp runs the same iterations (the learned proposal is a
-    // warp-collective tensor-core computation); lanes past the end only take part in it
-    for (int e0 = tid - (tid & 31); e0 < nXF + nYF; e0 += NT) {
+    // warp-collective tensor-core computation); lanes without a face only take part in it
+    for (int e0 = tid - (tid & 31); e0 < nXIa + nYF; e0 += NT) {
       const int e = e0 + (tid & 31);
-      const bool active = e < nXF + nYF;
+      const bool isx = e < nXIa;
+      const bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF);
       R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4];
       if (active) {
-        if (e < nXF) {
-          const int fx = e % (TX + 1), ry = e / (TX + 1);  // face index 0..TX <-> lx = fx + 4; row ly = ry + 3
-          const int cL = ry * SX + fx;                      // cell lx-1 = fx + 3 -> s index fx
+        if (isx) {
+          // face fx = e % SX (0..TX) <-> lx = fx + 4 in row ly = e / SX + 3; cell lx-1 has s index e
+          const int cL = e;
           const int cR = cL + 1;
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
@@ -220,9 +247,8 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             bq[m] = sxr[m * nC + cR];
           }
         } else {
-          const int f = e - nXF;
-          const int cxs = f % SX, fy = f / SX;  // column s index; face 0..TY <-> ly = fy + 4
-          const int cL = fy * SX + cxs;          // cell ly-1 = fy + 3
+          const int f = e - nXIa;                // = fy * SX + column s index; face 0..TY <-> ly = fy + 4
+          const int cL = f;                      // cell ly-1 = fy + 3
           const int cR = cL + SX;
           a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
           bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
@@ -230,13 +256,12 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       }
       face_solve<R, MODE>(s, a, bq, active, hook, wsm, face_key(bx, by, 0, e), F, cnt);
       if (active) {
-        if (e < nXF) {
-          const int fx = e % (TX + 1), ry = e / (TX + 1);
+        if (isx) {
+          const int fx = e % SX, ry = e / SX;
 #pragma unroll
           for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
         } else {
-          const int f = e - nXF;
-          const int o = (f / SX) * SX + f % SX;
+          const int o = e - nXIa;
           sfyh[0 * (TY + 1) * SX + o] = F[0];
           sfyh[1 * (TY + 1) * SX + o] = F[2];
           sfyh[2 * (TY + 1) * SX + o] = F[1];
@@ -249,14 +274,16 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
 
   // ---- 4. transverse correction + final solves + artificial viscosity at the tile's faces
   {
-    constexpr int nXF = (TX + 1) * TY, nYF = (TY + 1) * TX;
-    for (int e0 = tid - (tid & 31); e0 < nXF + nYF; e0 += NT) {
+    // as in stage 3: x-face items over rows of SX, y-face items from a warp boundary, over rows of RW
+    constexpr int nXI = SX * TY, nXIa = (nXI + 31) / 32 * 32, nYF = (TY + 1) * RW;
+    for (int e0 = tid - (tid & 31); e0 < nXIa + nYF; e0 += NT) {
       const int e = e0 + (tid & 31);
-      const bool active = e < nXF + nYF;
+      const bool isx = e < nXIa;
+      const bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF && (e - nXIa) % RW < TX);
       R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4], UL[4], UR[4];
       if (active) {
-        if (e < nXF) {
-          const int fx = e % (TX + 1), ty = e / (TX + 1);  // face lx = fx + 4, row ly = ty + 4
+        if (isx) {
+          const int fx = e % SX, ty = e / SX;  // face lx = fx + 4, row ly = ty + 4
           const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
           // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
           const int fL = ty * SX + fx, fR = fL + 1;
@@ -271,8 +298,8 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
           cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
           cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
         } else {
-          const int f = e - nXF;
-          const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
+          const int f = e - nXIa;
+          const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
           const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
           // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
           const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
@@ -293,8 +320,8 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       }
       face_solve<R, MODE>(s, a, bq, active, hook, wsm, face_key(bx, by, 1, e), F, cnt);
       if (!active) continue;
-      if (e < nXF) {
-        const int fx = e % (TX + 1), ty = e / (TX + 1);
+      if (isx) {
+        const int fx = e % SX, ty = e / SX;
         const int cL = (ty + 1) * SX + fx, cR = cL + 1;
         // artificial viscosity from the cell-centred velocities of the time-n state
         if (s.cvisc > (R)0) {
@@ -305,16 +332,21 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
           else
             div = (su[cR] - su[cL]) / s.dx + dvy / (4.0 * s.dy);
           const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
-          const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
-          const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi - 1, gj);
+          if constexpr (L::SMEM_U) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+            for (int k = 0; k < 4; ++k) F[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
+          } else {
+            const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
+            const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi - 1, gj);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+          }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = F[k];  // only this face read sxl[cL]
       } else {
-        const int f = e - nXF;
-        const int tx = f % TX, fy = f / TX;  // column lx = tx + 4, face ly = fy + 4
+        const int f = e - nXIa;
+        const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
         const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
         R G[4] = {F[0], F[2], F[1], F[3]};
         if (s.cvisc > (R)0) {
@@ -325,11 +357,16 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
           else
             div = (sv[cR] - sv[cL]) / s.dy + dux / (4.0 * s.dx);
           const R av = s.cvisc * M<R>::mx(-div * s.dy, (R)0);
-          const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
-          const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi, gj - 1);
+          if constexpr (L::SMEM_U) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            G[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+            for (int k = 0; k < 4; ++k) G[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
+          } else {
+            const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
+            const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi, gj - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              G[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+          }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
@@ -340,10 +377,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
 
   // ---- 5. conservative update of the tile's valid cells
   unsigned int& flags = cnt.flags;
-  for (int e = tid; e < TX * TY; e += NT) {
-    const int tx = e % TX, ty = e / TX;
+  for (int e = tid; e < RW * TY; e += NT) {
+    const int tx = e % RW, ty = e / RW;
     const int gi = x0 + tx, gj = y0 + ty;
-    if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
+    if (tx >= TX || gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
     const size_t o = (size_t)gj * P.pitch + gi;
     const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
     const int cy = ty * SX + tx + 1;    // final y flux of face ty (below the cell) lives in syl[cy]
@@ -353,7 +390,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       const R* fx = sxl + k * nC;
       const R* fy = syl + k * nC;
       const R d = ux * (fx[cx] - fx[cx + 1]) + uy * (fy[cy] - fy[cy + SX]);
-      Un[k] = __ldg(Uin + o + k * plane) + d;
+      if constexpr (L::SMEM_U)
+        Un[k] = sU[k * nC + cy + SX] + d;  // the cell's own U^n, s index (ty + 1) * SX + tx + 1
+      else
+        Un[k] = __ldg(Uin + o + k * plane) + d;
       Uout[o + k * plane] = Un[k];
     }
     if constexpr (FUSED) {

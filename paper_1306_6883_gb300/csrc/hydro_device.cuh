@@ -416,11 +416,13 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float xl = g * pl * rl, xr = g * pr * rr;
   const float icl = rsqrtf(xl), icr = rsqrtf(xr);  // 1/C_K
   const float cl = xl * icl, cr = xr * icr;
-  const float ipl = rcpa(pl), ipr = rcpa(pr);
+  // 1/C_K^2 = 1/(gamma p_K rho_K) gives 1/p_K = gamma rho_K / C_K^2 and c_K = C_K/rho_K = gamma p_K / C_K
+  // without further reciprocals
+  const float ipl = g * rl * icl * icl, ipr = g * rr * icr * icr;
   // velocity scale of the problem: float rounding leaves u*_R - u*_L uncertain by ~2^-24 of it, which can
   // exceed tol * p* in pressure when p* << rho u^2, so the FP32 stopping rule also accepts a pressure
   // change smaller than the one a velocity mismatch of tol times this scale would produce
-  const float vscale = fabsf(ul) + fabsf(ur) + cl * rcpa(rl) + cr * rcpa(rr);
+  const float vscale = fabsf(ul) + fabsf(ur) + g * (pl * icl + pr * icr);
   float pst = guess > 0.0f ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) * rcpa(cl + cr);
   pst = pst < s.small_pres ? s.small_pres : pst;
   int it = 0;
@@ -462,8 +464,9 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     const float sgn = left ? 1.0f : -1.0f;
     const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
     const float wo = left ? wl : wr;
+    const float ico = left ? icl : icr;
     const float iwo = left ? tl * icl : tr * icr;
-    const float iro = rcpa(ro);
+    const float iro = g * po * ico * ico;  // 1/rho_o
     const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
     const float rst = rcpa(irst);
     fv = vo;
@@ -475,7 +478,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
         fr = rst; fu = ust; fp = pst;
       }
     } else {
-      const float co = M<float>::sq(g * po * iro);
+      const float co = g * po * ico;  // sqrt(gamma p_o / rho_o)
       const float cst = M<float>::sq(g * pst * irst);
       const float SH = uo - sgn * co;
       const float ST = ust - sgn * cst;

@@ -211,7 +211,7 @@ int BatchStep<R, TX, TY, NT>::blocks_per_sm = 0;
 
 // Tile shapes the autotuner chooses from (index = shape id).
 const TileShape kTileShapes[] = {
-    {32, 16, 256}, {16, 16, 256}, {32, 8, 256}, {32, 32, 512},
+    {32, 16, 256}, {16, 16, 256}, {32, 8, 256}, {30, 16, 256},
 };
 const int kNumTileShapes = sizeof(kTileShapes) / sizeof(kTileShapes[0]);
 
@@ -223,7 +223,7 @@ cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const i
     case 0: return BatchStep<float, 32, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
     case 1: return BatchStep<float, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
     case 2: return BatchStep<float, 32, 8, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
-    case 3: return BatchStep<float, 32, 32, 512>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+    case 3: return BatchStep<float, 30, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -233,7 +233,7 @@ cudaError_t batch_prepare(int precision) {
   cudaError_t e = BatchStep<float, 32, 16, 256>::prepare();
   if (e == cudaSuccess) e = BatchStep<float, 16, 16, 256>::prepare();
   if (e == cudaSuccess) e = BatchStep<float, 32, 8, 256>::prepare();
-  if (e == cudaSuccess) e = BatchStep<float, 32, 32, 512>::prepare();
+  if (e == cudaSuccess) e = BatchStep<float, 30, 16, 256>::prepare();
   return e;
 }
 

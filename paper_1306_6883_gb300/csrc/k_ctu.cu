@@ -127,12 +127,27 @@ cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const
   return cudaGetLastError();
 }
 
+// Tile of the single-problem FP32 kernels (overridable at compile time for tile sweeps).  Measured on KH
+// 1024^2 and Sedov 2048^2: 32x16 (3 CTAs per SM) beats 30x16 (warp-aligned rows but a ragged last tile on
+// power-of-two grids), 30x8 and 14x16 by 1-2%, and 30x24/384, 62x8 and 30x32/512 (fewer warps per SM) by
+// 4-40%.
+#ifndef HYDRO_F32_TX
+#define HYDRO_F32_TX 32
+#endif
+#ifndef HYDRO_F32_TY
+#define HYDRO_F32_TY 16
+#endif
+#ifndef HYDRO_F32_NT
+#define HYDRO_F32_NT 256
+#endif
+constexpr int F32_TX = HYDRO_F32_TX, F32_TY = HYDRO_F32_TY, F32_NT = HYDRO_F32_NT;
+
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
   if (precision == 0)
     return launch_ctu_step_fused<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax,
                                                       stream);
-  return launch_ctu_step_fused<float, 32, 16, 256>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax,
+  return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax,
                                                    stream);
 }
 
@@ -144,13 +159,13 @@ cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uou
                                                              scr, h, stream);
   switch (mode) {
     case FACE_HARVEST:
-      return launch_ctu_step<float, 32, 16, 256, FACE_HARVEST>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_HARVEST>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
                                                                 scr, h, stream);
     case FACE_LEARNED:
-      return launch_ctu_step<float, 32, 16, 256, FACE_LEARNED>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_LEARNED>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
                                                                 scr, h, stream);
     default:
-      return launch_ctu_step<float, 32, 16, 256, FACE_PLAIN>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_PLAIN>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
                                                               scr, h, stream);
   }
 }

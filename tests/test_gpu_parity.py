@@ -199,8 +199,19 @@ def test_device_driver_loop_equals_the_host_loop():
                                       ((5, 70), ("periodic", "periodic", "outflow", "outflow"))])
 def test_fused_step_equals_the_three_passes(precision, shape, bc):
     # one launch per step (ghost cells through the boundary map, dt folded into the step) must give the
-    # same state and time as ghost fill + dt reduction + step, bit for bit
+    # same state and time as ghost fill + dt reduction + step.  FP64: bit for bit.  FP32: the two kernels
+    # are compiled separately and the compiler may fuse a different multiply-add pair of the same source
+    # expression in each (one rounding of 2^-24 relative at a face), so after 7 steps the states agree to a
+    # few hundred FP32 rounding units of each field's magnitude and the times to a few rounding units
     H, Solver, params_for = _mods()
+
+    def same(A, B):
+        if precision == 0:
+            np.testing.assert_array_equal(A, B)
+        else:
+            scale = np.abs(A).max(axis=(1, 2), keepdims=True)
+            assert np.all(np.abs(A - B) <= 2.0 ** -24 * 256 * scale), np.abs(A - B).max()
+
     nx, ny = shape
     pr = hp.quad(nx, ny, seed=nx + ny)
     pr = hp.Problem("q", nx, ny, pr.U, bc)
@@ -213,8 +224,9 @@ def test_fused_step_equals_the_three_passes(precision, shape, bc):
         b.step_fused(0.0)
     ta, na = a.time()
     tb, nb = b.time()
-    assert (ta, na) == (tb, nb)
-    np.testing.assert_array_equal(_interior(a.state_numpy()), _interior(b.state_numpy()))
+    assert na == nb
+    assert ta == tb if precision == 0 else ta == pytest.approx(tb, rel=2.0 ** -24 * 16)
+    same(_interior(a.state_numpy()), _interior(b.state_numpy()))
     # an upload invalidates the kept dt: the next fused step recomputes it from the new state
     U2 = hp.quad(nx, ny, seed=99).U
     a.set_state(U2)
@@ -223,7 +235,7 @@ def test_fused_step_equals_the_three_passes(precision, shape, bc):
     a.cfl_dt_async(0.0)
     a.step_device_dt()
     b.step_fused(0.0)
-    np.testing.assert_array_equal(_interior(a.state_numpy()), _interior(b.state_numpy()))
+    same(_interior(a.state_numpy()), _interior(b.state_numpy()))
     a.status()
     b.status()
     a.close()
