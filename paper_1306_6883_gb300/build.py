@@ -18,6 +18,10 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+# Translation units compiled with -fmad=false: each multiply and add rounds on its own, in source order.
+# They hold the FP64 kernels (which then round exactly like the plain C implementation of the method) and
+# the dt, ghost and totals kernels (memory-bound; both precisions).
+EXACT_UNITS = {"k_ctu_f64.cu", "k_batch_f64.cu", "k_aux.cu", "k_totals_noalloc.cu"}
 
 
 def _nvcc():
@@ -51,7 +55,8 @@ def build(force=False, verbose=False, extra_flags=()):
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        exact = ["-fmad=false"] if os.path.basename(src) in EXACT_UNITS else []
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *exact, *extra_flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,0 +1,143 @@
+// Single-problem CTU step kernels and their launch templates: one CTA per tile (the tile itself is in
+// ctu_tile.cuh).  Instantiated for FP32 in k_ctu.cu and for FP64 in k_ctu_f64.cu, which is compiled without
+// multiply-add contraction.
+#pragma once
+#include <float.h>
+
+#include "ctu_tile.cuh"
+#include "hydro_kernels.h"
+
+namespace hydro {
+
+// Per-block reduction of the tile counters into the context's scratch, one atomic per warp.
+__device__ __forceinline__ void flush_counters(TileCounters& cnt, DevScratch* scr) {
+  if (cnt.nonconv) cnt.flags |= STATUS_NONCONV;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    cnt.solves += __shfl_xor_sync(0xffffffffu, cnt.solves, off);
+    cnt.iters += __shfl_xor_sync(0xffffffffu, cnt.iters, off);
+    cnt.nonconv += __shfl_xor_sync(0xffffffffu, cnt.nonconv, off);
+    cnt.flags |= __shfl_xor_sync(0xffffffffu, cnt.flags, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&scr->stats[0], (unsigned long long)cnt.solves);
+    atomicAdd(&scr->stats[1], (unsigned long long)cnt.iters);
+    if (cnt.nonconv) atomicAdd(&scr->stats[2], (unsigned long long)cnt.nonconv);
+    if (cnt.flags) atomicOr(&scr->status, cnt.flags);
+  }
+}
+
+#ifndef HYDRO_F32_MINB
+#define HYDRO_F32_MINB 3
+#endif
+// Resident blocks per SM the register allocator must allow: shared memory admits three tiles per SM in
+// both precisions, and three blocks of 384 (FP32) or 256 (FP64) threads need <= 56 or <= 85 registers.
+template <typename R>
+constexpr int min_blocks() {
+  return is_f32<R>() ? HYDRO_F32_MINB : 3;
+}
+
+template <typename R, int TX, int TY, int NT, int MODE>
+__global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
+                                                      StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
+                                                      DevScratch* __restrict__ scr, FaceHook hook) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the network's weights are read from global memory (L1/L2-resident) only by warps whose gate opens,
+  // which is rare in smooth flow, so no CTA pays to stage them
+  const MlpBlob* wsm = MODE == FACE_LEARNED ? hook.mlp : nullptr;
+  SP<R> s;
+  s.load(P);
+  StepFactors<R> f;
+  f.load(sc_dev ? *sc_dev : sc_host);
+  TileCounters cnt;
+  ctu_tile<R, TX, TY, NT, MODE>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, hook, wsm);
+  flush_counters(cnt, scr);
+}
+
+template <typename R, int TX, int TY, int NT, int MODE>
+cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
+                            const StepScalars* sc_dev, DevScratch* scr, const FaceHook& hook, cudaStream_t stream) {
+  const size_t smem = TileLayout<R, TX, TY>::bytes;
+  static bool attr_set = false;  // per instantiation; the attribute is per function, not per device
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook);
+  return cudaGetLastError();
+}
+
+// Fused step: the tile reads ghost cells through the boundary map and folds the CFL constraint of its new
+// cells into a block minimum; the last block to finish advances the time by this step's dt and writes
+// the next step's factors, so a run needs one launch per step and no ghost-fill or dt pass.
+template <typename R, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KParams P, const R* __restrict__ Uin,
+                                                            R* __restrict__ Uout, const StepScalars* __restrict__ sc_cur,
+                                                            StepScalars* __restrict__ sc_next,
+                                                            DevScratch* __restrict__ scr, double tmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SP<R> s;
+  s.load(P);
+  StepFactors<R> f;
+  f.load(*sc_cur);
+  TileCounters cnt;
+  R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
+  ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
+                                            nullptr, &cmin);
+  flush_counters(cnt, scr);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const R o = __shfl_xor_sync(0xffffffffu, cmin, off);
+    cmin = o < cmin ? o : cmin;
+  }
+  __shared__ R wmin[NT / 32];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = cmin;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R b = wmin[0];
+    for (int k = 1; k < NT / 32; ++k) b = wmin[k] < b ? wmin[k] : b;
+    atomicMin(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong((double)b));
+    __threadfence();
+    last = atomicAdd(&scr->step_blocks_done, 1u) == gridDim.x * gridDim.y - 1u;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long bits =
+        atomicExch(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
+    const double t = scr->t + sc_cur->dt;
+    scr->t = t;
+    scr->nsteps = scr->nsteps + 1;
+    double dt = P.cfl * __longlong_as_double((long long)bits);
+    if (tmax > 0.0) {
+      const double left = tmax - t;
+      dt = dt > left ? left : dt;
+      dt = dt < 0.0 ? 0.0 : dt;
+    }
+    scr->dt = dt;
+    *sc_next = make_step_scalars(dt, P.dx, P.dy);
+    scr->step_blocks_done = 0u;
+  }
+}
+
+template <typename R, int TX, int TY, int NT>
+cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
+                                  StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+  const size_t smem = TileLayout<R, TX, TY>::bytes;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ctu_step_fused_kernel<R, TX, TY, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

@@ -33,4 +33,11 @@ cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const i
 // set the kernel attributes of every shape (call once before any stream capture)
 cudaError_t batch_prepare(int precision);
 
+// FP64 forms (k_batch_f64.cu, compiled without multiply-add contraction)
+cudaError_t batch_dt_f64(const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
+                         cudaStream_t stream);
+cudaError_t batch_step_f64(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
+                           DevScratch* agg, cudaStream_t stream, int* grid_out);
+cudaError_t batch_prepare_f64();
+
 }  // namespace hydro

@@ -36,6 +36,12 @@ cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uou
                      const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode = 0,
                      const FaceHook* hook = nullptr);
 
+// FP64 forms of the two step launches (k_ctu_f64.cu, compiled without multiply-add contraction).
+cudaError_t ctu_step_fused_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
+                               StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
+cudaError_t ctu_step_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,
+                         const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
+
 // Host copy of the device hash32 (mlp.cuh), for per-step sampling seeds.
 inline unsigned int host_hash32(unsigned int x) {
   x ^= x >> 16;

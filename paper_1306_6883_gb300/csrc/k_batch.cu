@@ -1,153 +1,7 @@
-// Batched kernels for ensembles of independent problems on uneven grids (one problem per member, each with
-// its own CFL time step): ghost fill and dt reduction over all members at once, and a persistent CTU step
-// kernel whose CTAs pull tiles of any member from a work queue.
-#include <float.h>
-
-#include "ctu_tile.cuh"
-#include "hydro_batch_internal.h"
+// Batched kernels: the FP32 instantiations and the precision dispatch (FP64 in k_batch_f64.cu).
+#include "batch_kernels.cuh"
 
 namespace hydro {
-
-// ---------------------------------------------------------------------------------------------------
-// Ghost cells of every member.  Block b fills 256 consecutive ghost cells of member tab[b].x starting at
-// tab[b].y, enumerated as in the single-problem kernel (bottom band, top band, left, right).
-template <typename R>
-__global__ void __launch_bounds__(256) batch_fill_kernel(const BatchMember* __restrict__ mem, const int2* __restrict__ tab,
-                                                        int parity) {
-  const int2 t = tab[blockIdx.x];
-  const BatchMember& m = mem[t.x];
-  const KParams& P = m.P;
-  R* U = (R*)m.U[parity];
-  const int band = P.ng * P.NX;
-  const int side = P.ny * P.ng;
-  const int n = 2 * band + 2 * side;
-  const int e = t.y + threadIdx.x;
-  if (e >= n) return;
-  int i, j;
-  if (e < band) {
-    j = e / P.NX; i = e % P.NX;
-  } else if (e < 2 * band) {
-    const int f = e - band;
-    j = P.ng + P.ny + f / P.NX; i = f % P.NX;
-  } else if (e < 2 * band + side) {
-    const int f = e - 2 * band;
-    j = P.ng + f / P.ng; i = f % P.ng;
-  } else {
-    const int f = e - 2 * band - side;
-    j = P.ng + f / P.ng; i = P.ng + P.nx + f % P.ng;
-  }
-  const int si = map_index(i, P.ng, P.nx, P.bc[0], P.bc[1]);
-  const int sj = map_index(j, P.ng, P.ny, P.bc[2], P.bc[3]);
-  const size_t plane = (size_t)P.NY * P.pitch;
-  const size_t d = (size_t)j * P.pitch + i, s = (size_t)sj * P.pitch + si;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) U[d + k * plane] = U[s + k * plane];
-}
-
-// ---------------------------------------------------------------------------------------------------
-// CFL dt of every member.  Block b reduces BATCH_DT_CELLS cells of member tab[b].x from cell tab[b].y;
-// tab[b].z is the member's block count, so the member's last block finalises its dt, step factors and
-// time, and resets the member's accumulator.
-template <typename R>
-__global__ void __launch_bounds__(256) batch_dt_kernel(const BatchMember* __restrict__ mem, const int4* __restrict__ tab,
-                                                      int parity, int advance) {
-  const int4 t = tab[blockIdx.x];
-  const BatchMember& m = mem[t.x];
-  const KParams& P = m.P;
-  const R* U = (const R*)m.U[parity];
-  DevScratch* scr = m.scr;
-  SP<R> s;
-  s.load(P);
-  const size_t plane = (size_t)P.NY * P.pitch;
-  const int ncell = P.nx * P.ny;
-  R rbest = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
-  unsigned int flags = 0;
-  const int end = min(t.y + BATCH_DT_CELLS, ncell);
-  for (int e = t.y + threadIdx.x; e < end; e += 256) {
-    const int j = e / P.nx, i = e % P.nx;
-    cfl_cell(s, U, (size_t)(j + P.ng) * P.pitch + (i + P.ng), plane, rbest, flags);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const R o = __shfl_xor_sync(0xffffffffu, rbest, off);
-    rbest = o < rbest ? o : rbest;
-    flags |= __shfl_xor_sync(0xffffffffu, flags, off);
-  }
-  __shared__ R wmin[8];
-  __shared__ unsigned int wflags[8];
-  __shared__ bool last;
-  if ((threadIdx.x & 31) == 0) {
-    wmin[threadIdx.x >> 5] = rbest;
-    wflags[threadIdx.x >> 5] = flags;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R b = wmin[0];
-    unsigned int f = wflags[0];
-    for (int k = 1; k < 8; ++k) {
-      b = wmin[k] < b ? wmin[k] : b;
-      f |= wflags[k];
-    }
-    atomicMin(&scr->dt_min_bits, (unsigned long long)__double_as_longlong((double)b));
-    if (f) atomicOr(&scr->status, f);
-    __threadfence();
-    last = (atomicAdd(&scr->dt_blocks_done, 1u) == (unsigned int)t.z - 1u);
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long bits = atomicExch(&scr->dt_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
-    const double dt = P.cfl * __longlong_as_double((long long)bits);
-    scr->dt = dt;
-    scr->sc = make_step_scalars(dt, P.dx, P.dy);
-    if (advance) {
-      scr->t = scr->t + dt;
-      scr->nsteps = scr->nsteps + 1;
-    }
-    scr->dt_blocks_done = 0u;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------------
-// Persistent CTU step over a tile list (member, tile x, tile y), largest members first: each CTA takes
-// the next tile from an atomic queue until the list is exhausted.
-template <typename R, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) batch_step_kernel(const BatchMember* __restrict__ mem,
-                                                       const int4* __restrict__ tiles, int ntiles,
-                                                       unsigned int* __restrict__ queue, int parity,
-                                                       DevScratch* __restrict__ agg) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int cur;
-  TileCounters cnt;
-  while (true) {
-    if (threadIdx.x == 0) cur = (int)atomicAdd(queue, 1u);
-    __syncthreads();
-    const int k = cur;
-    if (k >= ntiles) break;
-    const int4 t = tiles[k];
-    const BatchMember& m = mem[t.x];
-    SP<R> s;
-    s.load(m.P);
-    StepFactors<R> f;
-    f.load(m.scr->sc);
-    ctu_tile<R, TX, TY, NT>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z, smem_raw, cnt);
-    __syncthreads();  // the tile's last shared-memory reads finish before the next tile's loads
-  }
-  if (cnt.nonconv) cnt.flags |= STATUS_NONCONV;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    cnt.solves += __shfl_xor_sync(0xffffffffu, cnt.solves, off);
-    cnt.iters += __shfl_xor_sync(0xffffffffu, cnt.iters, off);
-    cnt.nonconv += __shfl_xor_sync(0xffffffffu, cnt.nonconv, off);
-    cnt.flags |= __shfl_xor_sync(0xffffffffu, cnt.flags, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&agg->stats[0], (unsigned long long)cnt.solves);
-    atomicAdd(&agg->stats[1], (unsigned long long)cnt.iters);
-    if (cnt.nonconv) atomicAdd(&agg->stats[2], (unsigned long long)cnt.nonconv);
-    if (cnt.flags) atomicOr(&agg->status, cnt.flags);
-  }
-}
 
 // ---------------------------------------------------------------------------------------------------
 // launchers
@@ -165,75 +19,36 @@ cudaError_t batch_fill(int precision, const BatchMember* mem, const int2* tab, i
 cudaError_t batch_dt(int precision, const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
                      cudaStream_t stream) {
   if (nblocks <= 0) return cudaSuccess;
-  if (precision == 0)
-    batch_dt_kernel<double><<<nblocks, 256, 0, stream>>>(mem, tab, parity, advance);
-  else
-    batch_dt_kernel<float><<<nblocks, 256, 0, stream>>>(mem, tab, parity, advance);
+  if (precision == 0) return batch_dt_f64(mem, tab, nblocks, parity, advance, stream);
+  batch_dt_kernel<float><<<nblocks, 256, 0, stream>>>(mem, tab, parity, advance);
   return cudaGetLastError();
 }
 
-template <typename R, int TX, int TY, int NT>
-struct BatchStep {
-  static int blocks_per_sm;  // occupancy of this instantiation, set by prepare()
-  static cudaError_t prepare() {
-    if (blocks_per_sm > 0) return cudaSuccess;
-    const size_t smem = TileLayout<R, TX, TY>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<R, TX, TY, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<R, TX, TY, NT>, NT, smem);
-    if (e != cudaSuccess) return e;
-    blocks_per_sm = b > 0 ? b : 1;
-    return cudaSuccess;
-  }
-  static cudaError_t launch(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
-                            DevScratch* agg, cudaStream_t stream, int* grid_out) {
-    cudaError_t e = prepare();
-    if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    int grid = nsm * blocks_per_sm;
-    if (grid > ntiles) grid = ntiles;
-    if (grid_out) *grid_out = grid;
-    if (grid <= 0) return cudaSuccess;
-    e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), stream);
-    if (e != cudaSuccess) return e;
-    batch_step_kernel<R, TX, TY, NT><<<grid, NT, TileLayout<R, TX, TY>::bytes, stream>>>(mem, tiles, ntiles, queue,
-                                                                                         parity, agg);
-    return cudaGetLastError();
-  }
-};
-template <typename R, int TX, int TY, int NT>
-int BatchStep<R, TX, TY, NT>::blocks_per_sm = 0;
-
 // Tile shapes the autotuner chooses from (index = shape id).
 const TileShape kTileShapes[] = {
-    {32, 16, 256}, {16, 16, 256}, {32, 8, 256}, {30, 16, 256},
+    {32, 16, 384}, {16, 16, 256}, {32, 8, 256}, {32, 16, 256},
 };
 const int kNumTileShapes = sizeof(kTileShapes) / sizeof(kTileShapes[0]);
 
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
                        unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out) {
   if (precision == 0)  // the FP64 path keeps one shape (its cost is the FP64 pipe, not the tile)
-    return BatchStep<double, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+    return batch_step_f64(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
   switch (shape) {
-    case 0: return BatchStep<float, 32, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+    case 0: return BatchStep<float, 32, 16, 384>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
     case 1: return BatchStep<float, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
     case 2: return BatchStep<float, 32, 8, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
-    case 3: return BatchStep<float, 30, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+    case 3: return BatchStep<float, 32, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t batch_prepare(int precision) {
-  if (precision == 0) return BatchStep<double, 16, 16, 256>::prepare();
-  cudaError_t e = BatchStep<float, 32, 16, 256>::prepare();
+  if (precision == 0) return batch_prepare_f64();
+  cudaError_t e = BatchStep<float, 32, 16, 384>::prepare();
   if (e == cudaSuccess) e = BatchStep<float, 16, 16, 256>::prepare();
   if (e == cudaSuccess) e = BatchStep<float, 32, 8, 256>::prepare();
-  if (e == cudaSuccess) e = BatchStep<float, 30, 16, 256>::prepare();
+  if (e == cudaSuccess) e = BatchStep<float, 32, 16, 256>::prepare();
   return e;
 }
 

@@ -1,136 +1,13 @@
-// Single-problem fused CTU step kernel: one CTA per tile (the tile itself is in ctu_tile.cuh).
-#include <float.h>
-
-#include "ctu_tile.cuh"
-#include "hydro_kernels.h"
+// Single-problem CTU step: the FP32 instantiations and the precision dispatch (FP64 in k_ctu_f64.cu).
+#include "ctu_kernels.cuh"
 
 namespace hydro {
 
-// Per-block reduction of the tile counters into the context's scratch, one atomic per warp.
-__device__ __forceinline__ void flush_counters(TileCounters& cnt, DevScratch* scr) {
-  if (cnt.nonconv) cnt.flags |= STATUS_NONCONV;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    cnt.solves += __shfl_xor_sync(0xffffffffu, cnt.solves, off);
-    cnt.iters += __shfl_xor_sync(0xffffffffu, cnt.iters, off);
-    cnt.nonconv += __shfl_xor_sync(0xffffffffu, cnt.nonconv, off);
-    cnt.flags |= __shfl_xor_sync(0xffffffffu, cnt.flags, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&scr->stats[0], (unsigned long long)cnt.solves);
-    atomicAdd(&scr->stats[1], (unsigned long long)cnt.iters);
-    if (cnt.nonconv) atomicAdd(&scr->stats[2], (unsigned long long)cnt.nonconv);
-    if (cnt.flags) atomicOr(&scr->status, cnt.flags);
-  }
-}
-
-template <typename R, int TX, int TY, int NT, int MODE>
-__global__ void __launch_bounds__(NT) ctu_step_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
-                                                      StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
-                                                      DevScratch* __restrict__ scr, FaceHook hook) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the network's weights are read from global memory (L1/L2-resident) only by warps whose gate opens,
-  // which is rare in smooth flow, so no CTA pays to stage them
-  const MlpBlob* wsm = MODE == FACE_LEARNED ? hook.mlp : nullptr;
-  SP<R> s;
-  s.load(P);
-  StepFactors<R> f;
-  f.load(sc_dev ? *sc_dev : sc_host);
-  TileCounters cnt;
-  ctu_tile<R, TX, TY, NT, MODE>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, hook, wsm);
-  flush_counters(cnt, scr);
-}
-
-template <typename R, int TX, int TY, int NT, int MODE>
-cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
-                            const StepScalars* sc_dev, DevScratch* scr, const FaceHook& hook, cudaStream_t stream) {
-  const size_t smem = TileLayout<R, TX, TY>::bytes;
-  static bool attr_set = false;  // per instantiation; the attribute is per function, not per device
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook);
-  return cudaGetLastError();
-}
-
-// Fused step: the tile reads ghost cells through the boundary map and folds the CFL constraint of its new
-// cells into a block minimum; the last block to finish advances the time by this step's dt and writes
-// the next step's factors, so a run needs one launch per step and no ghost-fill or dt pass.
-template <typename R, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) ctu_step_fused_kernel(KParams P, const R* __restrict__ Uin,
-                                                            R* __restrict__ Uout, const StepScalars* __restrict__ sc_cur,
-                                                            StepScalars* __restrict__ sc_next,
-                                                            DevScratch* __restrict__ scr, double tmax) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SP<R> s;
-  s.load(P);
-  StepFactors<R> f;
-  f.load(*sc_cur);
-  TileCounters cnt;
-  R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
-  ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
-                                            nullptr, &cmin);
-  flush_counters(cnt, scr);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const R o = __shfl_xor_sync(0xffffffffu, cmin, off);
-    cmin = o < cmin ? o : cmin;
-  }
-  __shared__ R wmin[NT / 32];
-  __shared__ bool last;
-  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = cmin;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R b = wmin[0];
-    for (int k = 1; k < NT / 32; ++k) b = wmin[k] < b ? wmin[k] : b;
-    atomicMin(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong((double)b));
-    __threadfence();
-    last = atomicAdd(&scr->step_blocks_done, 1u) == gridDim.x * gridDim.y - 1u;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long bits =
-        atomicExch(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
-    const double t = scr->t + sc_cur->dt;
-    scr->t = t;
-    scr->nsteps = scr->nsteps + 1;
-    double dt = P.cfl * __longlong_as_double((long long)bits);
-    if (tmax > 0.0) {
-      const double left = tmax - t;
-      dt = dt > left ? left : dt;
-      dt = dt < 0.0 ? 0.0 : dt;
-    }
-    scr->dt = dt;
-    *sc_next = make_step_scalars(dt, P.dx, P.dy);
-    scr->step_blocks_done = 0u;
-  }
-}
-
-template <typename R, int TX, int TY, int NT>
-cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
-                                  StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
-  const size_t smem = TileLayout<R, TX, TY>::bytes;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ctu_step_fused_kernel<R, TX, TY, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax);
-  return cudaGetLastError();
-}
-
 // Tile of the single-problem FP32 kernels (overridable at compile time for tile sweeps).  Measured on KH
-// 1024^2 and Sedov 2048^2: 32x16 (3 CTAs per SM) beats 30x16 (warp-aligned rows but a ragged last tile on
-// power-of-two grids), 30x8 and 14x16 by 1-2%, and 30x24/384, 62x8 and 30x32/512 (fewer warps per SM) by
-// 4-40%.
+// 1024^2 and Sedov 2048^2 at 256 threads: 32x16 (3 CTAs per SM) beats 30x16 (warp-aligned rows but a ragged
+// last tile on power-of-two grids), 30x8 and 14x16 by 1-2%, and 30x24/384, 62x8 and 30x32/512 (fewer warps
+// per SM) by 4-40%.  With 384 threads (36 warps per SM at 56 registers) 32x16 gains another 6-8%; more
+// threads per tile force spills or fewer tiles per SM and lose.
 #ifndef HYDRO_F32_TX
 #define HYDRO_F32_TX 32
 #endif
@@ -138,31 +15,28 @@ cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const
 #define HYDRO_F32_TY 16
 #endif
 #ifndef HYDRO_F32_NT
-#define HYDRO_F32_NT 256
+#define HYDRO_F32_NT 384
 #endif
 constexpr int F32_TX = HYDRO_F32_TX, F32_TY = HYDRO_F32_TY, F32_NT = HYDRO_F32_NT;
 
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
-  if (precision == 0)
-    return launch_ctu_step_fused<double, 16, 16, 256>(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax,
-                                                      stream);
+  if (precision == 0) return ctu_step_fused_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream);
   return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax,
                                                    stream);
 }
 
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
                      const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode, const FaceHook* hook) {
+  if (precision == 0) return ctu_step_f64(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev, scr, stream);
   const FaceHook h = hook ? *hook : FaceHook{};
-  if (precision == 0)
-    return launch_ctu_step<double, 16, 16, 256, FACE_PLAIN>(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev,
-                                                             scr, h, stream);
   switch (mode) {
     case FACE_HARVEST:
       return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_HARVEST>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
                                                                 scr, h, stream);
     case FACE_LEARNED:
-      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_LEARNED>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
+      // 256 threads: the network's warp-collective forward pass needs more than 56 registers
+      return launch_ctu_step<float, F32_TX, F32_TY, 256, FACE_LEARNED>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
                                                                 scr, h, stream);
     default:
       return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_PLAIN>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,

