@@ -9,7 +9,10 @@
 
 namespace hydro {
 
-// Per-block reduction of the tile counters into the context's scratch, one atomic per warp.
+// Per-block reduction of the tile counters into the context's scratch: warp shuffles, then one thread adds
+// the block's sums (one atomic per counter and block; per-warp atomics on the same words cost ~4 % of a
+// KH 1024^2 step).  Called by every thread of the block.
+template <int NT>
 __device__ __forceinline__ void flush_counters(TileCounters& cnt, DevScratch* scr) {
   if (cnt.nonconv) cnt.flags |= STATUS_NONCONV;
 #pragma unroll
@@ -19,11 +22,28 @@ __device__ __forceinline__ void flush_counters(TileCounters& cnt, DevScratch* sc
     cnt.nonconv += __shfl_xor_sync(0xffffffffu, cnt.nonconv, off);
     cnt.flags |= __shfl_xor_sync(0xffffffffu, cnt.flags, off);
   }
+  __shared__ unsigned int part[NT / 32][4];
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&scr->stats[0], (unsigned long long)cnt.solves);
-    atomicAdd(&scr->stats[1], (unsigned long long)cnt.iters);
-    if (cnt.nonconv) atomicAdd(&scr->stats[2], (unsigned long long)cnt.nonconv);
-    if (cnt.flags) atomicOr(&scr->status, cnt.flags);
+    const int w = threadIdx.x >> 5;
+    part[w][0] = cnt.solves;
+    part[w][1] = cnt.iters;
+    part[w][2] = cnt.nonconv;
+    part[w][3] = cnt.flags;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long solves = 0, iters = 0, nonconv = 0;
+    unsigned int flags = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      solves += part[w][0];
+      iters += part[w][1];
+      nonconv += part[w][2];
+      flags |= part[w][3];
+    }
+    atomicAdd(&scr->stats[0], solves);
+    atomicAdd(&scr->stats[1], iters);
+    if (nonconv) atomicAdd(&scr->stats[2], nonconv);
+    if (flags) atomicOr(&scr->status, flags);
   }
 }
 
@@ -51,7 +71,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_kernel(KParams P
   f.load(sc_dev ? *sc_dev : sc_host);
   TileCounters cnt;
   ctu_tile<R, TX, TY, NT, MODE>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, hook, wsm);
-  flush_counters(cnt, scr);
+  flush_counters<NT>(cnt, scr);
 }
 
 template <typename R, int TX, int TY, int NT, int MODE>
@@ -87,7 +107,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
   ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
                                             nullptr, &cmin);
-  flush_counters(cnt, scr);
+  flush_counters<NT>(cnt, scr);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const R o = __shfl_xor_sync(0xffffffffu, cmin, off);

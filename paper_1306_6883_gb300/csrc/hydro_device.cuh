@@ -498,25 +498,50 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   if (pstar_out) *pstar_out = pst;
 }
 
-// CFL constraint of one interior cell at offset o (Eq. 6 with |u|+c): min(dx/(|u|+c), dy/(|v|+c)), folded
-// into rbest; non-finite and non-positive cells set status bits instead.
+// CFL constraint of one interior cell (Eq. 6 with |u|+c): min(dx/(|u|+c), dy/(|v|+c)), folded into rbest;
+// non-finite and non-positive cells set status bits instead.  FP64 evaluates the formula as written (the
+// order the exact-rounding FP64 kernels share with the plain C implementation).  FP32 forms the same
+// minimum as the reciprocal of the larger signal rate max((|u|+c)/dx, (|v|+c)/dy), with c^2 = gamma p / rho
+// from the reciprocal of rho already formed for the velocities: one reciprocal square root and two
+// reciprocals per cell instead of four divisions.
 template <typename R>
 __device__ __forceinline__ void cfl_value(const SP<R>& s, R U0, R U1, R U2, R U3, R& rbest, unsigned int& flags) {
   if (!finite4(U0, U1, U2, U3)) {
     flags |= STATUS_NONFINITE;
     return;
   }
-  R rho, u, v, p;
-  cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
-  {
-    const R ke = M<R>::dv((R)0.5 * (U1 * U1 + U2 * U2), U0);
-    if (!(U0 > (R)0) || !(U3 - ke > (R)0)) flags |= STATUS_NEGATIVE;
+  if constexpr (is_f32<R>()) {
+    const float rho = U0 < s.small_dens ? s.small_dens : U0;
+    const float ir = rcpa(rho);
+    const float u = U1 * ir, v = U2 * ir;
+    const float ke = 0.5f * rho * (u * u + v * v);
+    if (!(U0 > 0.0f) || !(U3 - ke > 0.0f)) flags |= STATUS_NEGATIVE;
+    float p;
+    if (ke > 0.999f * U3) {  // as cons_to_prim: recover e = E - rho |u|^2 / 2 in double
+      const double rd = (double)rho, ud = (double)U1 / rd, vd = (double)U2 / rd;
+      p = (float)(((double)s.gm1) * ((double)U3 - 0.5 * rd * (ud * ud + vd * vd)));
+    } else {
+      p = s.gm1 * (U3 - ke);
+    }
+    p = p < s.small_pres ? s.small_pres : p;
+    const float c2 = s.gamma * p * ir;
+    const float cs = c2 * rsqrtf(c2);
+    const float rate = fmaxf((fabsf(u) + cs) * s.idx, (fabsf(v) + cs) * s.idy);
+    const float t = rcpa(rate);
+    rbest = t < rbest ? t : rbest;
+  } else {
+    R rho, u, v, p;
+    cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
+    {
+      const R ke = (0.5 * (U1 * U1 + U2 * U2)) / U0;
+      if (!(U0 > (R)0) || !(U3 - ke > (R)0)) flags |= STATUS_NEGATIVE;
+    }
+    const R cs = sqrt((s.gamma * p) / rho);
+    const R tx = s.dx / (fabs(u) + cs);
+    const R ty = s.dy / (fabs(v) + cs);
+    const R t = fmin(tx, ty);
+    rbest = t < rbest ? t : rbest;
   }
-  const R cs = M<R>::sq(M<R>::dv(s.gamma * p, rho));
-  const R tx = M<R>::dv(s.dx, M<R>::ab(u) + cs);
-  const R ty = M<R>::dv(s.dy, M<R>::ab(v) + cs);
-  const R t = M<R>::mn(tx, ty);
-  rbest = t < rbest ? t : rbest;
 }
 
 template <typename R>
