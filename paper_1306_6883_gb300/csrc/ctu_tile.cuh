@@ -190,38 +190,45 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   __syncthreads();
 
   // ---- 2. slopes + tracing for the same cells; items [0, nC) trace in x, [nCa, nCa + nC) in y (the y
-  // items start at a warp boundary so no warp mixes the two directions)
-  constexpr int nCa = (nC + 31) / 32 * 32;
-  for (int e = tid; e < nCa + nC; e += NT) {
-    const bool ydir = e >= nCa;
-    const int c = ydir ? e - nCa : e;
-    if (c >= nC) continue;
-    const int cx = c % SX + 3, cy = c / SX + 3;
-    const int b = cy * QP + cx;
-    const int st = ydir ? QP : 1;
-    const R xi = sxi[c];
-    R q[4], dq[4];
-    // face frame: (rho, un, ut, p); in y un = v, ut = u
-    const int kmap[4] = {0, ydir ? 2 : 1, ydir ? 1 : 2, 3};
+  // items start at a warp boundary, so the direction is uniform over a warp and each direction's code has
+  // its shared-memory offsets as constants)
+  {
+    auto trace_cell = [&](auto ydir, int c) {
+      constexpr bool YD = decltype(ydir)::value;
+      constexpr int st = YD ? QP : 1;
+      // face frame (rho, un, ut, p) -> planes of the (rho, u, v, p) arrays; in y un = v, ut = u
+      constexpr int k1 = YD ? 2 : 1, k2 = YD ? 1 : 2;
+      const int b = (c / SX + 3) * QP + c % SX + 3;
+      const R xi = sxi[c];
+      R q[4], dq[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const R* a = sq + kmap[m] * QP * QY + b;
-      q[m] = a[0];
-      dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
-    }
-    R ql[4], qrr[4];
-    trace<R>(s, ydir ? sigy : sigx, q, dq, ql, qrr);
-    R* dl = ydir ? syl : sxl;
-    R* dr = ydir ? syr : sxr;
-    // store in (rho, u, v, p) order
+      for (int m = 0; m < 4; ++m) {
+        const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
+        const R* a = sq + k * QP * QY + b;
+        q[m] = a[0];
+        dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+      }
+      R ql[4], qrr[4];
+      trace<R>(s, YD ? sigy : sigx, q, dq, ql, qrr);
+      R* dl = YD ? syl : sxl;
+      R* dr = YD ? syr : sxr;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      dl[kmap[m] * nC + c] = ql[m];
-      dr[kmap[m] * nC + c] = qrr[m];
+      for (int m = 0; m < 4; ++m) {  // stored in (rho, u, v, p) order
+        const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
+        dl[k * nC + c] = ql[m];
+        dr[k * nC + c] = qrr[m];
+      }
+    };
+    constexpr int nCa = (nC + 31) / 32 * 32;
+    for (int e = tid; e < nCa + nC; e += NT) {
+      if (e < nCa) {
+        if (e < nC) trace_cell(std::false_type{}, e);
+      } else {
+        trace_cell(std::true_type{}, e - nCa);
+      }
     }
   }
   __syncthreads();
-
 
   // ---- 3. hat Riemann solves.  x faces: lx in [4, TX+5) between cells lx-1 and lx, rows [3, TY+5).
   //         y faces: ly in [4, TY+5), columns [3, TX+5).  Results overwrite region A.

@@ -189,26 +189,28 @@ __device__ __forceinline__ void prim_to_cons(const SP<R>& s, R rho, R u, R v, R 
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Limited slopes (§3.1, fourth-order MC limiter of Colella 1985).
+// Limited slopes (§3.1, fourth-order MC limiter of Colella 1985).  Written without data-dependent branches
+// (the zero-slope cases are selects) so that a warp whose cells disagree on the limiter's case does not
+// run both paths; the arithmetic and its order are those of the definition.
 template <typename R>
 __device__ __forceinline__ R mc2(R qm, R q0, R qp) {
-  R dl = q0 - qm, dr = qp - q0, dc = (R)0.5 * (qp - qm);
-  if (!(dl * dr > (R)0)) return (R)0;
-  R dlim = (R)2 * M<R>::mn(M<R>::ab(dl), M<R>::ab(dr));
-  R mag = M<R>::mn(M<R>::ab(dc), dlim);
-  return dc >= (R)0 ? mag : -mag;
+  const R dl = q0 - qm, dr = qp - q0, dc = (R)0.5 * (qp - qm);
+  const R dlim = (R)2 * M<R>::mn(M<R>::ab(dl), M<R>::ab(dr));
+  const R mag = M<R>::mn(M<R>::ab(dc), dlim);
+  const R lim = dc >= (R)0 ? mag : -mag;
+  return dl * dr > (R)0 ? lim : (R)0;
 }
 
 template <typename R>
 __device__ __forceinline__ R slope(int limiter, R qm2, R qm1, R q0, R qp1, R qp2) {
-  if (limiter == 0) return (R)0;
+  if (limiter == 0) return (R)0;  // uniform over the launch
   if (limiter == 1) return mc2(qm1, q0, qp1);
-  R dl = q0 - qm1, dr = qp1 - q0, dc = (R)0.5 * (qp1 - qm1);
-  if (!(dl * dr > (R)0)) return (R)0;
-  R dlim = (R)2 * M<R>::mn(M<R>::ab(dl), M<R>::ab(dr));
-  R d4 = ((R)4 / (R)3) * dc - ((R)1 / (R)6) * (mc2(q0, qp1, qp2) + mc2(qm2, qm1, q0));
-  R mag = M<R>::mn(M<R>::ab(d4), dlim);
-  return d4 >= (R)0 ? mag : -mag;
+  const R dl = q0 - qm1, dr = qp1 - q0, dc = (R)0.5 * (qp1 - qm1);
+  const R dlim = (R)2 * M<R>::mn(M<R>::ab(dl), M<R>::ab(dr));
+  const R d4 = ((R)4 / (R)3) * dc - ((R)1 / (R)6) * (mc2(q0, qp1, qp2) + mc2(qm2, qm1, q0));
+  const R mag = M<R>::mn(M<R>::ab(d4), dlim);
+  const R lim = d4 >= (R)0 ? mag : -mag;
+  return dl * dr > (R)0 ? lim : (R)0;
 }
 
 // Flattening shock detector on one line (§3.2, Colella 1990): chi in [0, 1].
@@ -422,7 +424,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   // velocity scale of the problem: float rounding leaves u*_R - u*_L uncertain by ~2^-24 of it, which can
   // exceed tol * p* in pressure when p* << rho u^2, so the FP32 stopping rule also accepts a pressure
   // change smaller than the one a velocity mismatch of tol times this scale would produce
-  const float vscale = fabsf(ul) + fabsf(ur) + g * (pl * icl + pr * icr);
+  const float tolv = s.tol * (fabsf(ul) + fabsf(ur) + g * (pl * icl + pr * icr));
   float pst = guess > 0.0f ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) * rcpa(cl + cr);
   pst = pst < s.small_pres ? s.small_pres : pst;
   int it = 0;
@@ -433,15 +435,16 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     const float iwl = tl * icl, iwr = tr * icr;
     const float usl = ul - (pst - pl) * iwl;
     const float usr = ur + (pst - pr) * iwr;
-    const float izl = 0.5f * (al + 1.0f) * tl * tl * iwl;
-    const float izr = 0.5f * (ar + 1.0f) * tr * tr * iwr;
+    // (a_K + 1) t_K^2 / 2 = (1 + 1/a_K) / 2 = (1 + t_K^2) / 2
+    const float izl = fmaf(0.5f, tl * tl, 0.5f) * iwl;
+    const float izr = fmaf(0.5f, tr * tr, 0.5f) * iwr;
     const float iz = izl + izr;  // 1 / (Z_L Z_R / (Z_L + Z_R))
     float pnew = pst - (usr - usl) * rcpa(iz);
     pnew = pnew < s.small_pres ? s.small_pres : pnew;
     const float dp = fabsf(pnew - pst);
     pst = pnew;
     ++it;
-    if (dp <= s.tol * pst || dp * iz <= s.tol * vscale) {
+    if (dp <= s.tol * pst || dp * iz <= tolv) {
       ok = true;
       break;
     }
@@ -465,7 +468,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
     const float wo = left ? wl : wr;
     const float ico = left ? icl : icr;
-    const float iwo = left ? tl * icl : tr * icr;
+    const float iwo = (left ? tl : tr) * ico;
     const float iro = g * po * ico * ico;  // 1/rho_o
     const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
     const float rst = rcpa(irst);
