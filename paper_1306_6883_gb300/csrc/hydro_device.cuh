@@ -456,46 +456,33 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float wl = cl * al * tl, wr = cr * ar * tr;
   const float ust = ((wl * ul + wr * ur) + (pl - pr)) * rcpa(wl + wr);
 
-  float fr, fu, fv, fp;
+  // sampling at x/t = 0 (the same cases as the FP64 solver), written as selects: shock or fan per face
+  // varies within a warp, and a branch per case would run both paths
+  const bool left = ust > 0.0f;
+  const float sgn = left ? 1.0f : -1.0f;
+  const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
+  const float wo = left ? wl : wr;
+  const float ico = left ? icl : icr;
+  const float iwo = (left ? tl : tr) * ico;
+  const float iro = g * po * ico * ico;             // 1/rho_o
+  const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
+  const float rst = rcpa(irst);
+  const bool shock = pst > po;
+  const float S = uo - sgn * wo * iro;                   // shock speed
+  const float SH = uo - sgn * (g * po * ico);            // fan head u_o -+ c_o, c_o = sqrt(gamma p_o / rho_o)
+  const float ST = ust - sgn * M<float>::sq(g * pst * irst);  // fan tail u* -+ c*
+  const bool take_o = shock ? sgn * S >= 0.0f : sgn * SH >= 0.0f;
+  const bool take_star = shock ? !take_o : sgn * ST <= 0.0f;
+  const float frac = SH * rcpa(SH - ST);  // inside the fan only (selected away elsewhere)
+  float fr = take_o ? ro : take_star ? rst : ro + frac * (rst - ro);
+  float fu = take_o ? uo : take_star ? ust : uo + frac * (ust - uo);
+  float fp = take_o ? po : take_star ? pst : po + frac * (pst - po);
+  float fv = vo;
   if (ust == 0.0f) {
     fr = 0.5f * (rl + rr);
     fu = 0.0f;
     fv = 0.5f * (vl + vr);
     fp = pst;
-  } else {
-    const bool left = ust > 0.0f;
-    const float sgn = left ? 1.0f : -1.0f;
-    const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
-    const float wo = left ? wl : wr;
-    const float ico = left ? icl : icr;
-    const float iwo = (left ? tl : tr) * ico;
-    const float iro = g * po * ico * ico;  // 1/rho_o
-    const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
-    const float rst = rcpa(irst);
-    fv = vo;
-    if (pst > po) {
-      const float S = uo - sgn * wo * iro;
-      if (sgn * S >= 0.0f) {
-        fr = ro; fu = uo; fp = po;
-      } else {
-        fr = rst; fu = ust; fp = pst;
-      }
-    } else {
-      const float co = g * po * ico;  // sqrt(gamma p_o / rho_o)
-      const float cst = M<float>::sq(g * pst * irst);
-      const float SH = uo - sgn * co;
-      const float ST = ust - sgn * cst;
-      if (sgn * SH >= 0.0f) {
-        fr = ro; fu = uo; fp = po;
-      } else if (sgn * ST <= 0.0f) {
-        fr = rst; fu = ust; fp = pst;
-      } else {
-        const float frac = SH * rcpa(SH - ST);
-        fr = ro + frac * (rst - ro);
-        fu = uo + frac * (ust - uo);
-        fp = po + frac * (pst - po);
-      }
-    }
   }
   face_flux(s, fr, fu, fv, fp, F);
   if (pstar_out) *pstar_out = pst;
