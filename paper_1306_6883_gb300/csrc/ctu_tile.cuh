@@ -136,27 +136,38 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   // ---- 0. load the tile.  FUSED: ghost cells are taken from the interior cells the boundary conditions
   // map them to (the values a ghost fill would have written); otherwise the ghost cells are read as filled
   // and indices past the array are clamped (such cells only feed cells outside the grid)
-  for (int e = tid; e < QX * QY; e += NT) {
-    const int lx = e % QX, ly = e / QX;
-    const size_t o = cell_offset<FUSED>(P, x0 - 4 + lx, y0 - 4 + ly);
-    R rho, u, v, p;
-    const R U0 = __ldg(Uin + o), U1 = __ldg(Uin + o + plane), U2 = __ldg(Uin + o + 2 * plane),
-            U3 = __ldg(Uin + o + 3 * plane);
-    cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
-    if constexpr (L::SMEM_U) {
-      if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
-        const int c = (ly - 3) * SX + (lx - 3);
-        sU[c] = U0;
-        sU[nC + c] = U1;
-        sU[2 * nC + c] = U2;
-        sU[3 * nC + c] = U3;
-      }
+  // all of a thread's loads are issued before any conversion, so their latencies overlap
+  constexpr int NLD = (QX * QY + NT - 1) / NT;
+  R Ul[NLD][4];
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int e = tid + it * NT;
+    if (e < QX * QY) {
+      const size_t o = cell_offset<FUSED>(P, x0 - 4 + e % QX, y0 - 4 + e / QX);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
     }
-    const int d = ly * QP + lx;
-    sq[d] = rho;
-    sq[QP * QY + d] = u;
-    sq[2 * QP * QY + d] = v;
-    sq[3 * QP * QY + d] = p;
+  }
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int e = tid + it * NT;
+    if (e < QX * QY) {
+      const int lx = e % QX, ly = e / QX;
+      R rho, u, v, p;
+      cons_to_prim(s, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3], rho, u, v, p);
+      if constexpr (L::SMEM_U) {
+        if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
+          const int c = (ly - 3) * SX + (lx - 3);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) sU[k * nC + c] = Ul[it][k];
+        }
+      }
+      const int d = ly * QP + lx;
+      sq[d] = rho;
+      sq[QP * QY + d] = u;
+      sq[2 * QP * QY + d] = v;
+      sq[3 * QP * QY + d] = p;
+    }
   }
   __syncthreads();
 

@@ -456,33 +456,36 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float wl = cl * al * tl, wr = cr * ar * tr;
   const float ust = ((wl * ul + wr * ur) + (pl - pr)) * rcpa(wl + wr);
 
-  // sampling at x/t = 0 (the same cases as the FP64 solver), written as selects: shock or fan per face
-  // varies within a warp, and a branch per case would run both paths
-  const bool left = ust > 0.0f;
-  const float sgn = left ? 1.0f : -1.0f;
-  const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
-  const float wo = left ? wl : wr;
-  const float ico = left ? icl : icr;
-  const float iwo = (left ? tl : tr) * ico;
-  const float iro = g * po * ico * ico;             // 1/rho_o
-  const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
-  const float rst = rcpa(irst);
-  const bool shock = pst > po;
-  const float S = uo - sgn * wo * iro;                   // shock speed
-  const float SH = uo - sgn * (g * po * ico);            // fan head u_o -+ c_o, c_o = sqrt(gamma p_o / rho_o)
-  const float ST = ust - sgn * M<float>::sq(g * pst * irst);  // fan tail u* -+ c*
-  const bool take_o = shock ? sgn * S >= 0.0f : sgn * SH >= 0.0f;
-  const bool take_star = shock ? !take_o : sgn * ST <= 0.0f;
-  const float frac = SH * rcpa(SH - ST);  // inside the fan only (selected away elsewhere)
-  float fr = take_o ? ro : take_star ? rst : ro + frac * (rst - ro);
-  float fu = take_o ? uo : take_star ? ust : uo + frac * (ust - uo);
-  float fp = take_o ? po : take_star ? pst : po + frac * (pst - po);
-  float fv = vo;
+  // sampling at x/t = 0 (the same cases as the FP64 solver).  A face on the contact (u* = 0; whole warps of
+  // it in a fluid at rest) takes the mean state; otherwise the case (shock, fan head, fan tail, inside the
+  // fan) is chosen by selects, since it varies within a warp and a branch per case would run every path.
+  float fr, fu, fv, fp;
   if (ust == 0.0f) {
     fr = 0.5f * (rl + rr);
     fu = 0.0f;
     fv = 0.5f * (vl + vr);
     fp = pst;
+  } else {
+    const bool left = ust > 0.0f;
+    const float sgn = left ? 1.0f : -1.0f;
+    const float ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
+    const float wo = left ? wl : wr;
+    const float ico = left ? icl : icr;
+    const float iwo = (left ? tl : tr) * ico;
+    const float iro = g * po * ico * ico;             // 1/rho_o
+    const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
+    const float rst = rcpa(irst);
+    const bool shock = pst > po;
+    const float S = uo - sgn * wo * iro;                        // shock speed
+    const float SH = uo - sgn * (g * po * ico);                 // fan head u_o -+ c_o
+    const float ST = ust - sgn * M<float>::sq(g * pst * irst);  // fan tail u* -+ c*
+    const bool take_o = shock ? sgn * S >= 0.0f : sgn * SH >= 0.0f;
+    const bool take_star = shock ? !take_o : sgn * ST <= 0.0f;
+    const float frac = SH * rcpa(SH - ST);  // inside the fan only (selected away elsewhere)
+    fr = take_o ? ro : take_star ? rst : ro + frac * (rst - ro);
+    fu = take_o ? uo : take_star ? ust : uo + frac * (ust - uo);
+    fp = take_o ? po : take_star ? pst : po + frac * (pst - po);
+    fv = vo;
   }
   face_flux(s, fr, fu, fv, fp, F);
   if (pstar_out) *pstar_out = pst;
