@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -32,12 +33,31 @@ sys.path.insert(0, ROOT)
 
 # algorithmic flops per zone-update: counted with an instrumented copy of the FP64 oracle on the
 # Kelvin-Helmholtz workload (+ - * / sqrt = 1 flop each): 973 per zone plus 40 per Newton iteration of
-# the two-shock solver, at 4.008 solves per zone (roofline section)
+# the two-shock solver, at 4.008 solves per zone
 FLOPS_BASE = 973.0
 FLOPS_PER_ITER = 40.0
 SOLVES_PER_ZONE = 4.008
 # measured ALU peaks on this machine's GB300 (FMA = 2 flops; 152 SMs): FP32 70.6 TFLOP/s, FP64 1.16 TFLOP/s
 ALU_PEAK_TFLOPS = {"fp32": 70.6, "fp64": 1.16}
+
+
+# DRAM bytes (read + write) of one launch of the FP32 fused step kernel on the KH 1024^2 workload, from an
+# ncu capture of the kernel built from the sources whose SHA-256 is recorded; reported only while the
+# kernel's sources are unchanged (otherwise the counters describe another kernel and traffic is null)
+TRAFFIC_CAPTURE = {"bytes_per_launch": 17373696 + 4096,
+                   "sources_sha256": "9d84144808ca6e783b1dcb0c91c594acb0ae62497201625a04d2f061494e1b8c"}
+KERNEL_SOURCES = ["paper_1306_6883_gb300/csrc/" + f for f in
+                  ("k_ctu.cu", "ctu_kernels.cuh", "ctu_tile.cuh", "hydro_device.cuh", "mlp.cuh", "hydro_kernels.h")
+                  ] + ["include/hydro.h"]
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -64,10 +84,9 @@ class Clocks:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"hydro_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -428,10 +447,10 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "ctu_step_fused_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"measured {args.precision} FMA throughput (152 SMs), see DESIGN.md",
+                     "peak_source": f"measured {args.precision} FMA-chain throughput on all 152 SMs",
                      "flops_per_zone": flops_zone, "kernel_ms": kern_ms,
                      "hbm_gbs": bytes_zone * zones / (kern_ms * 1e-3) / 1e9, "hbm_frac_of_measured": None,
-                     "traffic": None},
+                     "traffic": None, "traffic_note": None},
         "cpu_baseline": None,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"]},
@@ -445,6 +464,14 @@ def run_ours(args, world, rank, local):
         "learned_proposal": learned,
     }
     line["roofline"]["hbm_frac_of_measured"] = line["roofline"]["hbm_gbs"] / hbm
+    if args.precision == "fp32" and wname == "kh_1024x1024_periodic":
+        if kernel_sources_sha256() == TRAFFIC_CAPTURE["sources_sha256"]:
+            line["roofline"]["traffic"] = TRAFFIC_CAPTURE["bytes_per_launch"]
+            line["roofline"]["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch; "
+                                                "the new state stays in L2 and is written back after the launch")
+        else:
+            line["roofline"]["traffic_note"] = "kernel sources changed since the last ncu capture"
+
     if world == 1:
         line["cpu_baseline"] = cpu_baseline(pr)
     print(json.dumps(line), flush=True)
