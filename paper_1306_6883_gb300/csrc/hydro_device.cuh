@@ -102,7 +102,7 @@ struct M<double> {
 template <>
 struct M<float> {
   // arguments are strictly positive wherever sq / rs are used (floored pressures and densities)
-  static __device__ __forceinline__ float sq(float x) { return x * rsqrtf(x); }
+  static __device__ __forceinline__ float sq(float x);
   static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float mn(float a, float b) { return fminf(a, b); }
   static __device__ __forceinline__ float mx(float a, float b) { return fmaxf(a, b); }
@@ -115,6 +115,16 @@ __device__ __forceinline__ float rcpa(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+
+// approximate reciprocal square root, subnormals flushed (one MUFU.RSQ, no subnormal fix-up): every
+// argument in the FP32 path is a product of floored densities and pressures (>= 1e-30), never subnormal
+__device__ __forceinline__ float rsqa(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float M<float>::sq(float x) { return x * rsqa(x); }
 
 // Per-precision copies of the scalar parameters used in the stencil.
 template <typename R>
@@ -250,7 +260,7 @@ __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], con
   if constexpr (is_f32<R>()) {
     const float ir = rcpa(rho);
     const float x = s.gamma * pres * ir;  // c^2
-    const float ic = rsqrtf(x);           // 1/c
+    const float ic = rsqa(x);           // 1/c
     c = x * ic;
     c2 = c * c;
     roc = 0.5f * rho * ic;
@@ -416,7 +426,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
   const float rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
   const float xl = g * pl * rl, xr = g * pr * rr;
-  const float icl = rsqrtf(xl), icr = rsqrtf(xr);  // 1/C_K
+  const float icl = rsqa(xl), icr = rsqa(xr);  // 1/C_K
   const float cl = xl * icl, cr = xr * icr;
   // 1/C_K^2 = 1/(gamma p_K rho_K) gives 1/p_K = gamma rho_K / C_K^2 and c_K = C_K/rho_K = gamma p_K / C_K
   // without further reciprocals
@@ -431,7 +441,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   bool ok = false;
   while (it < s.maxiter) {
     const float al = 1.0f + g1 * (pst * ipl - 1.0f), ar = 1.0f + g1 * (pst * ipr - 1.0f);
-    const float tl = rsqrtf(al), tr = rsqrtf(ar);
+    const float tl = rsqa(al), tr = rsqa(ar);
     const float iwl = tl * icl, iwr = tr * icr;
     const float usl = ul - (pst - pl) * iwl;
     const float usr = ur + (pst - pr) * iwr;
@@ -452,7 +462,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   iters = it;
   conv = ok;
   const float al = 1.0f + g1 * (pst * ipl - 1.0f), ar = 1.0f + g1 * (pst * ipr - 1.0f);
-  const float tl = rsqrtf(al), tr = rsqrtf(ar);
+  const float tl = rsqa(al), tr = rsqa(ar);
   const float wl = cl * al * tl, wr = cr * ar * tr;
   const float ust = ((wl * ul + wr * ur) + (pl - pr)) * rcpa(wl + wr);
 
@@ -518,7 +528,7 @@ __device__ __forceinline__ void cfl_value(const SP<R>& s, R U0, R U1, R U2, R U3
     }
     p = p < s.small_pres ? s.small_pres : p;
     const float c2 = s.gamma * p * ir;
-    const float cs = c2 * rsqrtf(c2);
+    const float cs = c2 * rsqa(c2);
     const float rate = fmaxf((fabsf(u) + cs) * s.idx, (fabsf(v) + cs) * s.idy);
     const float t = rcpa(rate);
     rbest = t < rbest ? t : rbest;
