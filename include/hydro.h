@@ -282,6 +282,12 @@ const char* hydro_last_error(const hydro_ctx* ctx);
 /* Library build string (compute capability and options), never NULL. */
 const char* hydro_build_info(void);
 
+/* 1 if the context's step kernels load tiles by TMA bulk tensor copies (FP32 contexts with ng a multiple of
+ * 4 on a driver that provides the tensor-map encoder; tiles whose halo leaves the interior, or the padded
+ * array for the unfused step, are still loaded cell by cell), 0 otherwise or if ctx is NULL.  No paper
+ * counterpart: how the data reaches shared memory does not change what a step computes. */
+int hydro_tma_enabled(const hydro_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

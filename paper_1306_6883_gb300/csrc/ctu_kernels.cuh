@@ -60,8 +60,9 @@ constexpr int min_blocks() {
 template <typename R, int TX, int TY, int NT, int MODE>
 __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
                                                       StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
-                                                      DevScratch* __restrict__ scr, FaceHook hook) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                      DevScratch* __restrict__ scr, FaceHook hook,
+                                                      const __grid_constant__ CUtensorMap tmap, int use_tma) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   // the network's weights are read from global memory (L1/L2-resident) only by warps whose gate opens,
   // which is rare in smooth flow, so no CTA pays to stage them
   const MlpBlob* wsm = MODE == FACE_LEARNED ? hook.mlp : nullptr;
@@ -70,13 +71,15 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_kernel(KParams P
   StepFactors<R> f;
   f.load(sc_dev ? *sc_dev : sc_host);
   TileCounters cnt;
-  ctu_tile<R, TX, TY, NT, MODE>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, hook, wsm);
+  ctu_tile<R, TX, TY, NT, MODE>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, hook, wsm, nullptr,
+                                use_tma ? &tmap : nullptr);
   flush_counters<NT>(cnt, scr);
 }
 
 template <typename R, int TX, int TY, int NT, int MODE>
 cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
-                            const StepScalars* sc_dev, DevScratch* scr, const FaceHook& hook, cudaStream_t stream) {
+                            const StepScalars* sc_dev, DevScratch* scr, const FaceHook& hook, const CUtensorMap* tmap,
+                            cudaStream_t stream) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
   static bool attr_set = false;  // per instantiation; the attribute is per function, not per device
   if (!attr_set) {
@@ -86,7 +89,8 @@ cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepS
     attr_set = true;
   }
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook);
+  ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook,
+                                                                    tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -97,8 +101,9 @@ template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KParams P, const R* __restrict__ Uin,
                                                             R* __restrict__ Uout, const StepScalars* __restrict__ sc_cur,
                                                             StepScalars* __restrict__ sc_next,
-                                                            DevScratch* __restrict__ scr, double tmax) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                            DevScratch* __restrict__ scr, double tmax,
+                                                            const __grid_constant__ CUtensorMap tmap, int use_tma) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   SP<R> s;
   s.load(P);
   StepFactors<R> f;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   TileCounters cnt;
   R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
   ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
-                                            nullptr, &cmin);
+                                            nullptr, &cmin, use_tma ? &tmap : nullptr);
   flush_counters<NT>(cnt, scr);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -146,7 +151,8 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
 
 template <typename R, int TX, int TY, int NT>
 cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
-                                  StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+                                  StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
+                                  cudaStream_t stream) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
   static bool attr_set = false;
   if (!attr_set) {
@@ -156,7 +162,8 @@ cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const
     attr_set = true;
   }
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax);
+  ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
+                                                                   tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 
 #include "hydro_device.cuh"
 #include "mlp.cuh"
+#include "tma.cuh"
 
 namespace hydro {
 
@@ -107,7 +108,8 @@ template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED 
 __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
                                          const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
                                          unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
-                                         const MlpBlob* wsm = nullptr, R* cfl_min = nullptr) {
+                                         const MlpBlob* wsm = nullptr, R* cfl_min = nullptr,
+                                         const CUtensorMap* tmap = nullptr) {
   using L = TileLayout<R, TX, TY>;
   constexpr int QX = L::QX, QP = L::QP, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
   // row width of the y-face items of stage 4 and the cells of stage 5: SX when that makes every warp one
@@ -136,40 +138,90 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   // ---- 0. load the tile.  FUSED: ghost cells are taken from the interior cells the boundary conditions
   // map them to (the values a ghost fill would have written); otherwise the ghost cells are read as filled
   // and indices past the array are clamped (such cells only feed cells outside the grid)
-  // all of a thread's loads are issued before any conversion, so their latencies overlap
-  constexpr int NLD = (QX * QY + NT - 1) / NT;
-  R Ul[NLD][4];
-#pragma unroll
-  for (int it = 0; it < NLD; ++it) {
-    const int e = tid + it * NT;
-    if (e < QX * QY) {
-      const size_t o = cell_offset<FUSED>(P, x0 - 4 + e % QX, y0 - 4 + e / QX);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
-    }
+  // FP32 tiles whose padded box lies where the array holds the values the step needs (FUSED: the interior,
+  // so that no boundary map applies; otherwise the ghost-filled array) arrive by one TMA copy of the
+  // [4][QY][QX] box into the primitive area and are converted there in place; other tiles are loaded cell
+  // by cell.
+  bool tma_tile = false;
+  if constexpr (is_f32<R>()) {
+    static_assert(QP == QX, "the TMA box is stored densely");
+    // the bulk tensor copy's shared-memory destination must be 128-byte aligned
+    if (tmap != nullptr && (smem_addr(sq) & 127u) == 0)
+      tma_tile = FUSED ? (x0 - 4 >= P.ng && x0 - 4 + QX <= P.ng + P.nx && y0 - 4 >= P.ng && y0 - 4 + QY <= P.ng + P.ny)
+                       : (x0 - 4 + QX <= P.NX && y0 - 4 + QY <= P.NY);
   }
-#pragma unroll
-  for (int it = 0; it < NLD; ++it) {
-    const int e = tid + it * NT;
-    if (e < QX * QY) {
+  if (tma_tile) {
+    __shared__ unsigned long long tma_bar;
+    const unsigned int bar = smem_addr(&tma_bar);
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
+      tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
+    }
+    __syncthreads();
+    const bool landed = mbar_wait(bar, 0);
+    if (__syncthreads_or(!landed)) {
+      // the copy did not complete within the poll budget: report it, give it one more budget to land
+      // (the shared memory must not be released under it) and leave this tile
+      cnt.flags |= STATUS_TIMEOUT;
+      mbar_wait(bar, 0);
+      return;
+    }
+    for (int e = tid; e < QX * QY; e += NT) {
       const int lx = e % QX, ly = e / QX;
-      R rho, u, v, p;
-      cons_to_prim(s, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3], rho, u, v, p);
-      if constexpr (L::SMEM_U) {
-        if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
-          const int c = (ly - 3) * SX + (lx - 3);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) sU[k * nC + c] = Ul[it][k];
-        }
-      }
       const int d = ly * QP + lx;
+      const R U0 = sq[d], U1 = sq[QP * QY + d], U2 = sq[2 * QP * QY + d], U3 = sq[3 * QP * QY + d];
+      R rho, u, v, p;
+      cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
+      if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
+        const int c = (ly - 3) * SX + (lx - 3);
+        sU[c] = U0;
+        sU[nC + c] = U1;
+        sU[2 * nC + c] = U2;
+        sU[3 * nC + c] = U3;
+      }
       sq[d] = rho;
       sq[QP * QY + d] = u;
       sq[2 * QP * QY + d] = v;
       sq[3 * QP * QY + d] = p;
     }
+    __syncthreads();
+  } else {
+    // all of a thread's loads are issued before any conversion, so their latencies overlap
+    constexpr int NLD = (QX * QY + NT - 1) / NT;
+    R Ul[NLD][4];
+#pragma unroll
+    for (int it = 0; it < NLD; ++it) {
+      const int e = tid + it * NT;
+      if (e < QX * QY) {
+        const size_t o = cell_offset<FUSED>(P, x0 - 4 + e % QX, y0 - 4 + e / QX);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NLD; ++it) {
+      const int e = tid + it * NT;
+      if (e < QX * QY) {
+        const int lx = e % QX, ly = e / QX;
+        R rho, u, v, p;
+        cons_to_prim(s, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3], rho, u, v, p);
+        if constexpr (L::SMEM_U) {
+          if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
+            const int c = (ly - 3) * SX + (lx - 3);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sU[k * nC + c] = Ul[it][k];
+          }
+        }
+        const int d = ly * QP + lx;
+        sq[d] = rho;
+        sq[QP * QY + d] = u;
+        sq[2 * QP * QY + d] = v;
+        sq[3 * QP * QY + d] = p;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   const R* qu = sq + QP * QY;
   const R* qv = sq + 2 * QP * QY;

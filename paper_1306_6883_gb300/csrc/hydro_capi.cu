@@ -1,6 +1,7 @@
 // C-ABI layer (include/hydro.h): parameter validation, context, scratch, and kernel launches on the
 // caller's stream.  The calls follow the single driver loop of the paper (§2): fill boundary conditions,
 // get the time step, evolve one step.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -32,8 +33,56 @@ struct hydro_ctx {
   // fused steps: the factors of the next step are in scr->scf[fused_parity] when fused_valid
   int fused_parity;
   int fused_valid;
+  // FP32: TMA descriptors of the two state buffers (tile loads by bulk tensor copy) when tma_ok
+  CUtensorMap tmap[2];
+  int tma_ok;
   char err[512];
 };
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link against the driver library).
+typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static encode_tiled_fn tensor_map_encoder() {
+  static encode_tiled_fn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (encode_tiled_fn)f;
+  }
+  return fn;
+}
+
+// Describe each FP32 state buffer as a 3-D tensor (x over the padded width, y over the padded height, the 4
+// conserved components) with the step kernel's (TX+8) x (TY+8) x 4 tile box.  TMA wants 16-byte aligned
+// bases and strides (the buffers are 256-byte aligned and rows are padded to 128 bytes) and 16-byte aligned
+// x coordinates: tile boxes start at x = ng - 4 + k * TX, so ng must be a multiple of 4.  Returns 0 (tiles
+// then load cell by cell) when any condition or the encoder is missing.
+static int make_tensor_maps(hydro_ctx* c) {
+  if (c->p.precision != HYDRO_FP32 || c->p.ng % 4 != 0) return 0;
+  if ((hydro::f32_tile_x() * sizeof(float)) % 16 != 0) return 0;
+  encode_tiled_fn enc = tensor_map_encoder();
+  if (!enc) return 0;
+  const cuuint64_t row = (cuuint64_t)c->kp.pitch * sizeof(float);
+  const cuuint64_t dims[3] = {(cuuint64_t)c->kp.NX, (cuuint64_t)c->kp.NY, 4};
+  const cuuint64_t strides[2] = {row, row * (cuuint64_t)c->kp.NY};
+  const cuuint32_t box[3] = {(cuuint32_t)hydro::f32_tile_x() + 8, (cuuint32_t)hydro::f32_tile_y() + 8, 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (row % 16 != 0 || box[0] * sizeof(float) % 16 != 0) return 0;
+  for (int b = 0; b < 2; ++b) {
+    if ((uintptr_t)c->state[b] % 16 != 0) return 0;
+    if (enc(&c->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->state[b], dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return 0;
+  }
+  return 1;
+}
 
 static size_t elem_size(int precision) { return precision == HYDRO_FP32 ? sizeof(float) : sizeof(double); }
 
@@ -187,6 +236,7 @@ hydro_status hydro_init(const hydro_params* p, void* d_state, void* d_state_alt,
   c->stream = (cudaStream_t)cuda_stream;
   c->err[0] = 0;
   hydro::fill_kparams(p, &c->kp);
+  c->tma_ok = make_tensor_maps(c);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     delete c;
@@ -231,6 +281,7 @@ static hydro_status status_from_flags(unsigned int f) {
   if (f & hydro::STATUS_NONFINITE) return HYDRO_ENONFINITE;
   if (f & hydro::STATUS_NEGATIVE) return HYDRO_ENEGATIVE;
   if (f & hydro::STATUS_NONCONV) return HYDRO_ENONCONV;
+  if (f & hydro::STATUS_TIMEOUT) return HYDRO_ETIMEOUT;
   return HYDRO_OK;
 }
 
@@ -261,7 +312,7 @@ static cudaError_t launch_step(hydro_ctx* c, const hydro::StepScalars& sc_host, 
   }
   ++c->step_calls;
   return hydro::ctu_step(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur], sc_host, sc_dev, c->scr,
-                         c->stream, mode, &c->hook);
+                         c->stream, mode, &c->hook, c->tma_ok ? &c->tmap[c->cur] : nullptr);
 }
 
 static hydro_status check_model(hydro_ctx* c) {
@@ -301,7 +352,7 @@ hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
   if (e == cudaSuccess)
     e = hydro::ctu_step_fused(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur],
                               &c->scr->scf[c->fused_parity], &c->scr->scf[1 - c->fused_parity], c->scr, tmax,
-                              c->stream);
+                              c->tma_ok ? &c->tmap[c->cur] : nullptr, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step_fused");
   ++c->step_calls;
   c->cur = 1 - c->cur;
@@ -417,6 +468,11 @@ hydro_status hydro_download(hydro_ctx* c, void* host) {
 
 const char* hydro_last_error(const hydro_ctx* c) { return c ? c->err : "no context"; }
 
-const char* hydro_build_info(void) { return "hydro sm_103a; kernels: fill_ghost, cfl_dt, ctu_step (fp64 16x16, fp32 32x16), totals"; }
+const char* hydro_build_info(void) {
+  return "hydro sm_103a; kernels: fill_ghost, cfl_dt, ctu_step and ctu_step_fused (fp64 16x16/256 exact rounding, "
+         "fp32 32x16/384 with TMA tile loads), batch fill/dt/step, totals, mlp";
+}
+
+int hydro_tma_enabled(const hydro_ctx* c) { return c ? c->tma_ok : 0; }
 
 }  // extern "C"

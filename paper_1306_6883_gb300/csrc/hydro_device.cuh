@@ -78,6 +78,7 @@ enum : unsigned int {
   STATUS_NONFINITE = 1u,
   STATUS_NEGATIVE = 2u,
   STATUS_NONCONV = 4u,
+  STATUS_TIMEOUT = 8u,  // a bounded device-side wait ran out (a tile's TMA copy did not land)
 };
 
 template <typename R>

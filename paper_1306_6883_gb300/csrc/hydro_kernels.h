@@ -1,5 +1,6 @@
 // Internal launch interface between the C-ABI layer and the CUDA kernels (not installed).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/hydro.h"
@@ -21,8 +22,12 @@ cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* s
 // One fused CTU step (ghost cells from the boundary map, CFL of the new state folded in): reads the step
 // factors at sc_cur; the last block adds sc_cur->dt to the time, counts the step and writes the next step's
 // factors (dt = cfl * min, clamped to tmax - t when tmax > 0) to sc_next.
+// tmap (FP32 only, may be NULL): TMA descriptor of Uin as a 3-D tensor (x over the padded width, y over the
+// padded height, the 4 conserved components) with a (TX+8) x (TY+8) x 4 box; tiles whose box is valid are
+// then loaded by one bulk tensor copy.
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
-                           StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
+                           StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
+                           cudaStream_t stream);
 
 // Conserved totals into scr->totals (deterministic two-level reduction; partials has room for
 // totals_max_blocks() * 4 doubles).
@@ -34,7 +39,11 @@ cudaError_t conserved_totals(int precision, const KParams& P, const void* U, dou
 // mode: FACE_PLAIN, FACE_HARVEST or FACE_LEARNED (the last two FP32 only; hook carries their buffers).
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
                      const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode = 0,
-                     const FaceHook* hook = nullptr);
+                     const FaceHook* hook = nullptr, const CUtensorMap* tmap = nullptr);
+
+// Tile box of the FP32 single-problem step kernels (the TMA box is (F32_TILE_X + 8) x (F32_TILE_Y + 8) x 4).
+int f32_tile_x();
+int f32_tile_y();
 
 // FP64 forms of the two step launches (k_ctu_f64.cu, compiled without multiply-add contraction).
 cudaError_t ctu_step_fused_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,

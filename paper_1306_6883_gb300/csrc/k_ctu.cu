@@ -19,28 +19,34 @@ namespace hydro {
 #endif
 constexpr int F32_TX = HYDRO_F32_TX, F32_TY = HYDRO_F32_TY, F32_NT = HYDRO_F32_NT;
 
+int f32_tile_x() { return F32_TX; }
+int f32_tile_y() { return F32_TY; }
+
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
-                           StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+                           StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
+                           cudaStream_t stream) {
   if (precision == 0) return ctu_step_fused_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream);
-  return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax,
-                                                   stream);
+  return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr,
+                                                              tmax, tmap, stream);
 }
 
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
-                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode, const FaceHook* hook) {
+                     const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode, const FaceHook* hook,
+                     const CUtensorMap* tmap) {
   if (precision == 0) return ctu_step_f64(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev, scr, stream);
   const FaceHook h = hook ? *hook : FaceHook{};
+  const float* in = (const float*)Uin;
+  float* out = (float*)Uout;
   switch (mode) {
     case FACE_HARVEST:
-      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_HARVEST>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
-                                                                scr, h, stream);
+      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_HARVEST>(P, in, out, sc_host, sc_dev, scr, h, tmap,
+                                                                           stream);
     case FACE_LEARNED:
       // 256 threads: the network's warp-collective forward pass needs more than 56 registers
-      return launch_ctu_step<float, F32_TX, F32_TY, 256, FACE_LEARNED>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
-                                                                scr, h, stream);
+      return launch_ctu_step<float, F32_TX, F32_TY, 256, FACE_LEARNED>(P, in, out, sc_host, sc_dev, scr, h, tmap,
+                                                                        stream);
     default:
-      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_PLAIN>(P, (const float*)Uin, (float*)Uout, sc_host, sc_dev,
-                                                              scr, h, stream);
+      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_PLAIN>(P, in, out, sc_host, sc_dev, scr, h, tmap, stream);
   }
 }
 

@@ -95,6 +95,7 @@ SIGNATURES = {
     "hydro_batch_last_error": (ctypes.c_char_p, [_VP]),
     "hydro_last_error": (ctypes.c_char_p, [_VP]),
     "hydro_build_info": (ctypes.c_char_p, []),
+    "hydro_tma_enabled": (ctypes.c_int, [_VP]),
 }
 
 
@@ -221,6 +222,10 @@ def hydro_download(ctx, host_ptr):
 
 def hydro_build_info():
     return load().hydro_build_info().decode()
+
+
+def hydro_tma_enabled(ctx):
+    return bool(load().hydro_tma_enabled(ctx))
 
 
 # ---------------------------------------------------------------------------------------------------- ensembles

@@ -407,6 +407,34 @@ def test_riemann_nonconvergence_is_reported():
     s.close()
 
 
+@pytest.mark.parametrize("precision,ng,expect", [(1, 4, True), (0, 4, False), (1, 6, False)])
+def test_tile_loads_use_tma_where_they_can(precision, ng, expect):
+    # FP32 contexts whose tile boxes start on 16-byte boundaries (ng a multiple of 4) load interior tiles by
+    # TMA bulk tensor copies; the FP64 path and other ghost widths load cell by cell.  Both give the step
+    # the same values: an FP32 step with ng = 6 (no TMA) equals the ng = 4 step (TMA) bit for bit.
+    H, Solver, params_for = _mods()
+    pr = hp.kh(200, 130, seed=3)
+    p = params_for(pr, precision)
+    p.ng = ng
+    U = np.zeros((4, pr.ny + 2 * ng, pr.nx + 2 * ng))
+    U[:, ng:-ng, ng:-ng] = _interior(pr.U)
+    s = Solver(p, U)
+    assert H.hydro_tma_enabled(s.ctx) == expect
+    s.close()
+    if precision == 1 and ng == 6:
+        outs = []
+        for g in (4, 6):
+            q = params_for(pr, 1)
+            q.ng = g
+            V = np.zeros((4, pr.ny + 2 * g, pr.nx + 2 * g))
+            V[:, g:-g, g:-g] = _interior(pr.U)
+            t = Solver(q, V)
+            t.advance(5)
+            outs.append(t.state_numpy()[:, g:-g, g:-g])
+            t.close()
+        np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_upload_download_roundtrip_is_exact():
     H, Solver, params_for = _mods()
     pr = hp.quad(33, 21, seed=1)
