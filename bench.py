@@ -192,7 +192,9 @@ def time_device_path(pr, precision, steps, warmup, flush):
 
 def time_e2e(pr, precision, steps, warmup):
     """Same metric through the public C-ABI calls with host buffers: every step uploads the state from
-    pinned host memory, fills ghosts, reduces dt (read back), steps, and downloads the new state."""
+    pinned host memory (hydro_upload), advances it one fused step (hydro_step_fused: dt of the uploaded
+    state, then the step) and downloads the new state (hydro_download, which waits for it); the two pinned
+    host buffers alternate as input and output."""
     import torch
 
     from paper_1306_6883_gb300 import hydro as H
@@ -201,29 +203,25 @@ def time_e2e(pr, precision, steps, warmup):
     prec = H.HYDRO_FP32 if precision == "fp32" else H.HYDRO_FP64
     dt_ = torch.float32 if precision == "fp32" else torch.float64
     s = Solver(params_for(pr, prec), pr.U)
-    host_in = torch.from_numpy(np.ascontiguousarray(pr.U)).to(dt_).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
+    host = [torch.from_numpy(np.ascontiguousarray(pr.U)).to(dt_).pin_memory() for _ in range(2)]
 
-    def one():
-        s.upload(host_in)
-        s.fill_ghost()
-        dt = s.cfl_dt()
-        s.step(dt)
-        s.download(host_out)
-        host_in.copy_(host_out)
+    def one(k):
+        s.upload(host[k % 2])
+        s.step_fused()
+        s.download(host[(k + 1) % 2])
 
-    for _ in range(warmup):
-        one()
+    for k in range(warmup):
+        one(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
+    for k in range(steps):
+        one(k)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     s.status()
     s.close()
-    nbytes = host_in.numel() * host_in.element_size()
-    return {"seconds": el, "h2d": nbytes, "d2h": nbytes + 8}
+    nbytes = host[0].numel() * host[0].element_size()
+    return {"seconds": el, "h2d": nbytes, "d2h": nbytes}
 
 
 def time_ensemble(steps=100, warmup=3, n=256, seed=0):

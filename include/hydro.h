@@ -170,13 +170,17 @@ hydro_status hydro_conserved_totals_noalloc(const hydro_params* p, const void* d
                                             double out[4]);
 
 /* Read and clear the device status word: HYDRO_OK, or the first of HYDRO_ENONFINITE, HYDRO_ENEGATIVE,
- * HYDRO_ENONCONV recorded since the last call.  Synchronises.  If stats is not NULL it receives
+ * HYDRO_ENONCONV, HYDRO_ETIMEOUT (a tile's TMA copy did not land within the bounded wait) recorded since
+ * the last call.  Synchronises.  If stats is not NULL it receives
  * {riemann solves, riemann iterations, unconverged solves} accumulated since hydro_init. */
 hydro_status hydro_sync_status(hydro_ctx* ctx, unsigned long long stats[3]);
 
 /* Copy a host array into / out of the current state.  host has the dense layout
  * [4][ny + 2 ng][nx + 2 ng] (no pitch) of the context's element type.  Pinned host memory makes the
- * copies asynchronous; the call returns after enqueueing (upload) or after the copy (download). */
+ * copies asynchronous; the call returns after enqueueing (upload) or after the copy (download).  An upload
+ * from pinned memory the device can address is done by a copy kernel reading the host memory directly
+ * (faster than the copy engine for this pitched copy on a Grace system); the host buffer must then stay
+ * unchanged until the stream has passed the upload. */
 hydro_status hydro_upload(hydro_ctx* ctx, const void* host);
 hydro_status hydro_download(hydro_ctx* ctx, void* host);
 

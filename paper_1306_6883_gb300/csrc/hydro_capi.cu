@@ -450,8 +450,16 @@ hydro_status hydro_upload(hydro_ctx* c, const void* host) {
   if (!c || !host) return HYDRO_EINVAL;
   const size_t es = elem_size(c->p.precision);
   const size_t w = (size_t)c->kp.NX * es, pitchb = (size_t)c->kp.pitch * es;
-  cudaError_t e = cudaMemcpy2DAsync(c->state[c->cur], pitchb, host, w, w, (size_t)4 * c->kp.NY,
-                                    cudaMemcpyHostToDevice, c->stream);
+  // pinned host memory the device can address is read by a copy kernel (about twice the copy engine's
+  // rate for this pitched copy on a Grace system); other host memory goes through the copy engine
+  cudaPointerAttributes at;
+  cudaError_t e;
+  if (cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+    e = hydro::upload_rows(at.devicePointer, c->state[c->cur], w, pitchb, 4 * c->kp.NY, c->stream);
+  else
+    e = cudaMemcpy2DAsync(c->state[c->cur], pitchb, host, w, w, (size_t)4 * c->kp.NY, cudaMemcpyHostToDevice,
+                          c->stream);
+  cudaGetLastError();  // a failed attribute query of unregistered memory leaves no sticky error
   c->fused_valid = 0;
   return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "upload");
 }

@@ -64,6 +64,11 @@ inline unsigned int host_hash32(unsigned int x) {
 // Kernel parameters of one problem from the public parameters (validated by the caller).
 void fill_kparams(const hydro_params* p, KParams* k);
 
+// Copy `rows` dense host rows of row_bytes each (host_dev: device-side address of pinned, mapped host memory)
+// into the device array dst with a row pitch of dst_pitch_bytes.
+cudaError_t upload_rows(const void* host_dev, void* dst, size_t row_bytes, size_t dst_pitch_bytes, int rows,
+                        cudaStream_t stream);
+
 // Scratch initialisation (min accumulator = +inf, counters 0).
 cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream);
 

@@ -220,4 +220,37 @@ cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------------
+// Upload of a dense host array [rows][width bytes] that the device can address (pinned, mapped) into the
+// pitched state: the SMs read the host memory directly over the chip-to-chip link, which on this system
+// moves a pitched copy faster than the copy engine does.  W: 16-byte vectors when every row start is
+// 16-byte aligned on both sides, else 4-byte words (row widths are whole elements of 4 or 8 bytes).
+template <typename W>
+__global__ void __launch_bounds__(256) upload_rows_kernel(const W* __restrict__ src, W* __restrict__ dst,
+                                                         size_t src_pitch, size_t dst_pitch, int width, int rows) {
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const W* s = src + (size_t)r * src_pitch;
+    W* d = dst + (size_t)r * dst_pitch;
+    for (int i = threadIdx.x; i < width; i += blockDim.x) d[i] = s[i];
+  }
+}
+
+cudaError_t upload_rows(const void* host_dev, void* dst, size_t row_bytes, size_t dst_pitch_bytes, int rows,
+                        cudaStream_t stream) {
+  if (rows <= 0 || row_bytes == 0) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = rows < 8 * nsm ? rows : 8 * nsm;
+  if (((uintptr_t)host_dev | (uintptr_t)dst | row_bytes | dst_pitch_bytes) % 16 == 0)
+    upload_rows_kernel<uint4><<<grid, 256, 0, stream>>>((const uint4*)host_dev, (uint4*)dst, row_bytes / 16,
+                                                        dst_pitch_bytes / 16, (int)(row_bytes / 16), rows);
+  else
+    upload_rows_kernel<unsigned int><<<grid, 256, 0, stream>>>((const unsigned int*)host_dev, (unsigned int*)dst,
+                                                               row_bytes / 4, dst_pitch_bytes / 4,
+                                                               (int)(row_bytes / 4), rows);
+  return cudaGetLastError();
+}
+
 }  // namespace hydro
