@@ -260,10 +260,12 @@ def time_ensemble(steps=100, warmup=3, n=256, seed=0):
     return out
 
 
-def harvest_and_train(train_steps=4000, batch=4096, lr=1e-3, seed=0):
+def harvest_and_train(train_steps=6000, batch=4096, lr=1e-3, seed=0):
     """Training set for the learned starting pressure: Riemann problems sampled from FP32 runs of the Sod
     tube (128^2 to t = 0.2), the Kelvin-Helmholtz layer (1024^2, 40 steps) and the Sedov blast (1024^2,
-    300 steps); then `train_steps` Adam steps of the library's training kernels."""
+    300 steps).  Faces are kept at random (hash of face and step) and, in addition, every face past the
+    network's gate (the faces the network will be asked about); training draws its minibatches from an equal
+    mix of gated and other faces.  Then `train_steps` Adam steps of the library's training kernels."""
     import torch
 
     import hydro_problems as hp
@@ -276,17 +278,28 @@ def harvest_and_train(train_steps=4000, batch=4096, lr=1e-3, seed=0):
     plan = [(hp.sod(128, 128), 0.2, 70, 0.25), (hp.kh(1024, 1024), 0.0, 40, 0.02),
             (hp.sedov(1024, 1024), 0.0, 300, 0.005)]
     t0 = time.perf_counter()
+    gate = (0.35, 1.0)  # the default gate of the learned kernels (model.set_gate)
     for pr, tmax, steps, rate in plan:
         s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
         H.hydro_set_harvest(s.ctx, buf.data_ptr(), cap, rate, count.data_ptr())
+        H.hydro_set_harvest_gate(s.ctx, *gate)
         s.advance(steps, tmax)
         s.status()
         s.close()
     n = min(int(count.item()), cap)
     data = buf[:n]
+    torch.cuda.synchronize()
+    t_h = time.perf_counter()
+    gated = strong_mask(data)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    strong_set, weak_set = data[gated], data[~gated]
+    k = min(weak_set.shape[0], max(strong_set.shape[0], 1))
+    weak_pick = weak_set[torch.randperm(weak_set.shape[0], device="cuda", generator=g)[:k]]
+    train_set = torch.cat([strong_set, weak_pick])
+    train_set = train_set[torch.randperm(train_set.shape[0], device="cuda", generator=g)].contiguous()
     t1 = time.perf_counter()
     m = Model(seed=seed)
-    loss = m.train(data, steps=train_steps, batch=batch, lr=lr, seed=seed + 1)
+    loss = m.train(train_set, steps=train_steps, batch=batch, lr=lr, seed=seed + 1)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     # iterations per face at the FP32 tolerance, acoustic vs learned start: on a held-out problem family
@@ -305,14 +318,12 @@ def harvest_and_train(train_steps=4000, batch=4096, lr=1e-3, seed=0):
     held = buf2[:min(int(count2.item()), cap2)]
 
     def strong(d):
-        pmax, pmin = torch.maximum(d[:, 2], d[:, 5]), torch.minimum(d[:, 2], d[:, 5])
-        du = d[:, 1] - d[:, 4]
-        return d[(pmax >= math.exp(0.7) * pmin) | (du ** 4 * d[:, 0] * d[:, 3] >= d[:, 2] * d[:, 5])].contiguous()
+        return d[strong_mask(d)].contiguous()
 
     iters = {}
+    rnd = data[~gated][:2_000_000].contiguous()  # the randomly kept faces (gated ones are counted apart)
     for name, d in (("held_out_quad_all", held), ("held_out_quad_strong", strong(held)),
-                    ("training_set_all", data[:2_000_000].contiguous()),
-                    ("training_set_strong", strong(data[:2_000_000]))):
+                    ("training_runs_random", rnd), ("training_runs_strong", strong_set.contiguous())):
         row = {"faces": int(d.shape[0])}
         if d.shape[0]:
             for learned in (False, True):
@@ -320,8 +331,18 @@ def harvest_and_train(train_steps=4000, batch=4096, lr=1e-3, seed=0):
                 row["learned" if learned else "acoustic"] = mean
                 row["nonconverged_" + ("learned" if learned else "acoustic")] = nonconv
         iters[name] = row
-    return m, {"samples": n, "harvest_s": t1 - t0, "train_steps": train_steps, "batch": batch, "train_s": t2 - t1,
+    return m, {"samples": n, "gated_samples": int(strong_set.shape[0]), "training_set": int(train_set.shape[0]),
+               "harvest_s": t_h - t0, "curation_s": t1 - t_h, "train_steps": train_steps, "batch": batch, "train_s": t2 - t1,
                "final_minibatch_loss": loss, "iterations_per_face": iters}
+
+
+def strong_mask(d):
+    """Harvested faces past the default gate of the learned kernels: |ln(pL/pR)|/2 >= 0.35 or
+    |uL - uR| / c_ref >= 1 (columns rho_L, u_L, p_L, rho_R, u_R, p_R)."""
+    import torch
+    pmax, pmin = torch.maximum(d[:, 2], d[:, 5]), torch.minimum(d[:, 2], d[:, 5])
+    du = d[:, 1] - d[:, 4]
+    return (pmax >= math.exp(0.7) * pmin) | (du ** 4 * d[:, 0] * d[:, 3] >= d[:, 2] * d[:, 5])
 
 
 def time_learned(model, steps=20, warmup=3):

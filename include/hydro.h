@@ -235,6 +235,13 @@ hydro_status hydro_set_riemann_model(hydro_ctx* ctx, const hydro_mlp* m);
 hydro_status hydro_set_harvest(hydro_ctx* ctx, void* d_buf, unsigned long long capacity, double rate,
                                unsigned long long* d_count);
 
+/* Also record every face past the learned proposal's gate (|ln(p_L/p_R)|/2 >= gate_dp or
+ * |u_L - u_R| / c_ref >= gate_du, see hydro_mlp_set_gate), whatever its hash, so that the rare faces the
+ * network is used on are not thinned out with the rest.  gate_dp <= 0 and gate_du <= 0 switch it off
+ * (the default).  Returns HYDRO_EINVAL for a half-set gate (one of them <= 0) or values beyond
+ * gate_dp = 40, gate_du = 1e9.  No paper counterpart (training-data selection). */
+hydro_status hydro_set_harvest_gate(hydro_ctx* ctx, double gate_dp, double gate_du);
+
 /* ---- Ensembles of independent problems (uneven grids, own time steps) ----------------------------
  * Not in the paper, which runs one problem at a time; this batches many independent copies of the §2
  * driver loop.  Each member has its own parameters (all members share one precision) and two caller-owned

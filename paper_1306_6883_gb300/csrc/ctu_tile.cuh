@@ -87,7 +87,8 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
   cnt.iters += it;
   cnt.nonconv += ok ? 0 : 1;
   if constexpr (MODE == FACE_HARVEST) {
-    if (hash32(key ^ hook.hseed) < hook.hthresh) {
+    if (hash32(key ^ hook.hseed) < hook.hthresh ||
+        (hook.hgate_ratio > 0.f && strong_face(a, b, hook.hgate_ratio, hook.hgate_u4))) {
       const unsigned long long k = atomicAdd(hook.hcount, 1ull);
       if (k < hook.hcap) {
         float* d = hook.hbuf + 8 * k;

@@ -3,6 +3,7 @@
 // get the time step, evolve one step.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -375,6 +376,19 @@ hydro_status hydro_set_harvest(hydro_ctx* c, void* d_buf, unsigned long long cap
   c->hook.hcap = capacity;
   c->hook.hthresh = rate >= 1.0 ? 0xFFFFFFFFu : (unsigned int)(rate * 4294967296.0);
   c->harvest = 1;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_set_harvest_gate(hydro_ctx* c, double gate_dp, double gate_du) {
+  if (!c) return HYDRO_EINVAL;
+  if (gate_dp <= 0.0 && gate_du <= 0.0) {
+    c->hook.hgate_ratio = 0.f;
+    c->hook.hgate_u4 = 0.f;
+    return HYDRO_OK;
+  }
+  if (!(gate_dp > 0.0) || !(gate_du > 0.0) || gate_dp > 40.0 || gate_du > 1e9) return HYDRO_EINVAL;
+  c->hook.hgate_ratio = (float)exp(2.0 * gate_dp);
+  c->hook.hgate_u4 = (float)(gate_du * gate_du * gate_du * gate_du);
   return HYDRO_OK;
 }
 

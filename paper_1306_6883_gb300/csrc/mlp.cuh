@@ -41,6 +41,8 @@ struct FaceHook {
   unsigned long long hcap;
   unsigned int hthresh;  // a face is sampled when its hash is below this
   unsigned int hseed;
+  // faces past this gate (as MlpBlob::gate_ratio / gate_u4) are recorded whatever their hash; 0 = off
+  float hgate_ratio, hgate_u4;
   const MlpBlob* mlp;    // learned proposal weights (device), or null
 };
 
@@ -151,15 +153,17 @@ static __device__ __noinline__ float mlp_warp_forward(const float x[6], const Ml
   return mt == 0 ? (half == 0 ? v00 : v01) : (half == 0 ? v10 : v11);
 }
 
+// The strong-face test of the gate: max(pL,pR) >= ratio min(pL,pR) or (uL-uR)^4 rho_L rho_R >= u4 p_L p_R
+// (no transcendental functions).
+__device__ __forceinline__ bool strong_face(const float a[4], const float b[4], float ratio, float u4) {
+  const float du = a[1] - b[1], du2 = du * du;
+  return fmaxf(a[3], b[3]) >= ratio * fminf(a[3], b[3]) || du2 * du2 * (a[0] * b[0]) >= u4 * (a[3] * b[3]);
+}
+
 // Starting pressure proposed for the face of every lane (0 = use the acoustic guess); warp-collective.
 __device__ __forceinline__ float learned_guess(const float a[4], const float b[4], bool active,
                                                const MlpBlob* __restrict__ w) {
-  bool strong = false;
-  if (active) {  // the gate needs no transcendental functions
-    const float du = a[1] - b[1], du2 = du * du;
-    strong = fmaxf(a[3], b[3]) >= w->gate_ratio * fminf(a[3], b[3]) ||
-             du2 * du2 * (a[0] * b[0]) >= w->gate_u4 * (a[3] * b[3]);
-  }
+  const bool strong = active && strong_face(a, b, w->gate_ratio, w->gate_u4);
   if (!__any_sync(0xffffffffu, strong)) return 0.f;
   float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float pref = 0.f;

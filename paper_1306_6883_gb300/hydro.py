@@ -80,6 +80,7 @@ SIGNATURES = {
     "hydro_mlp_last_error": (ctypes.c_char_p, [_VP]),
     "hydro_set_riemann_model": (ctypes.c_int, [_VP, _VP]),
     "hydro_set_harvest": (ctypes.c_int, [_VP, _VP, ctypes.c_ulonglong, ctypes.c_double, _VP]),
+    "hydro_set_harvest_gate": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double]),
     "hydro_batch_create": (ctypes.c_int, [ctypes.c_int, _PP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP,
                                           ctypes.POINTER(_VP)]),
     "hydro_batch_destroy": (None, [_VP]),
@@ -369,3 +370,7 @@ def hydro_set_riemann_model(ctx, m):
 def hydro_set_harvest(ctx, d_buf_ptr, capacity, rate, d_count_ptr):
     _check(load().hydro_set_harvest(ctx, _VP(d_buf_ptr) if d_buf_ptr else None, int(capacity), float(rate),
                                     _VP(d_count_ptr) if d_count_ptr else None), ctx, "hydro_set_harvest")
+
+
+def hydro_set_harvest_gate(ctx, gate_dp, gate_du):
+    _check(load().hydro_set_harvest_gate(ctx, float(gate_dp), float(gate_du)), ctx, "hydro_set_harvest_gate")
