@@ -128,6 +128,39 @@ def test_harvest_records_valid_riemann_problems(torch):
     s.close()
 
 
+def test_harvest_gate_keeps_every_strong_face(torch):
+    # with a negligible random rate, the gated harvest records exactly the faces past the gate: every
+    # record is a strong face, and a run with the gate records more of them than the random rate alone
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Harvest, Solver, params_for
+    counts = {}
+    for gated in (False, True):
+        pr = hp.sod(64, 64)
+        s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
+        hv = Harvest(s, capacity=200000, rate=1e-9)
+        if gated:
+            H.hydro_set_harvest_gate(s.ctx, 0.35, 1.0)
+        s.advance(5)
+        s.status()
+        smp = hv.samples().cpu().numpy().astype(np.float32)
+        counts[gated] = smp.shape[0]
+        if gated:
+            pl, pr_, du = smp[:, 2], smp[:, 5], smp[:, 1] - smp[:, 4]
+            ratio, u4 = np.float32(np.exp(0.7)), np.float32(1.0)
+            strong = (np.maximum(pl, pr_) >= ratio * np.minimum(pl, pr_)) | \
+                     ((du * du) * (du * du) * (smp[:, 0] * smp[:, 3]) >= u4 * (pl * pr_))
+            assert smp.shape[0] > 0 and np.all(strong)
+        s.close()
+    assert counts[True] > counts[False]
+    with pytest.raises(H.HydroError):
+        pr = hp.sod(16, 16)
+        s = Solver(params_for(pr, H.HYDRO_FP32), pr.U)
+        try:
+            H.hydro_set_harvest_gate(s.ctx, 0.35, 0.0)  # half-set gate
+        finally:
+            s.close()
+
+
 def _step(pr, learned_model=None, nsteps=1):
     from paper_1306_6883_gb300 import hydro as H
     from paper_1306_6883_gb300.solver import Solver, params_for
