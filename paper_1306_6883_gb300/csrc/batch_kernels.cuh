@@ -117,8 +117,9 @@ template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(const BatchMember* __restrict__ mem,
                                                        const int4* __restrict__ tiles, int ntiles,
                                                        unsigned int* __restrict__ queue, int parity,
-                                                       DevScratch* __restrict__ agg) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                       DevScratch* __restrict__ agg,
+                                                       const CUtensorMap* __restrict__ tmaps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int cur;
   TileCounters cnt;
   while (true) {
@@ -132,7 +133,9 @@ __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(con
     s.load(m.P);
     StepFactors<R> f;
     f.load(m.scr->sc);
-    ctu_tile<R, TX, TY, NT>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z, smem_raw, cnt);
+    const CUtensorMap* tm = (tmaps != nullptr && m.tma) ? tmaps + 2 * t.x + parity : nullptr;
+    ctu_tile<R, TX, TY, NT>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z, smem_raw, cnt,
+                            FaceHook{}, nullptr, nullptr, tm);
     __syncthreads();  // the tile's last shared-memory reads finish before the next tile's loads
   }
   if (cnt.nonconv) cnt.flags |= STATUS_NONCONV;
@@ -167,7 +170,8 @@ struct BatchStep {
     return cudaSuccess;
   }
   static cudaError_t launch(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
-                            DevScratch* agg, cudaStream_t stream, int* grid_out) {
+                            DevScratch* agg, cudaStream_t stream, int* grid_out,
+                            const CUtensorMap* tmaps = nullptr) {
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
@@ -181,7 +185,7 @@ struct BatchStep {
     e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), stream);
     if (e != cudaSuccess) return e;
     batch_step_kernel<R, TX, TY, NT><<<grid, NT, TileLayout<R, TX, TY>::bytes, stream>>>(mem, tiles, ntiles, queue,
-                                                                                         parity, agg);
+                                                                                         parity, agg, tmaps);
     return cudaGetLastError();
   }
 };

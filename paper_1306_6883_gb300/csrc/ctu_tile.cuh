@@ -154,6 +154,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   if (tma_tile) {
     __shared__ unsigned long long tma_bar;
     const unsigned int bar = smem_addr(&tma_bar);
+    // a block that runs several tiles (persistent kernel) has read and written this shared memory through
+    // the generic proxy; order those accesses before the copy's async-proxy writes
+    fence_proxy_async_smem();
+    __syncthreads();
     if (tid == 0) {
       mbar_init(bar, 1);
       mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
@@ -166,6 +170,8 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       // (the shared memory must not be released under it) and leave this tile
       cnt.flags |= STATUS_TIMEOUT;
       mbar_wait(bar, 0);
+      __syncthreads();
+      if (tid == 0) mbar_inval(bar);
       return;
     }
     for (int e = tid; e < QX * QY; e += NT) {
@@ -187,6 +193,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       sq[3 * QP * QY + d] = p;
     }
     __syncthreads();
+    if (tid == 0) mbar_inval(bar);  // every thread has passed the wait; the next tile initialises it again
   } else {
     // all of a thread's loads are issued before any conversion, so their latencies overlap
     constexpr int NLD = (QX * QY + NT - 1) / NT;

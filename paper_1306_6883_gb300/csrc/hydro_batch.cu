@@ -50,6 +50,7 @@ struct hydro_batch {
   int4* d_dt = nullptr;
   int ndt = 0;
   std::vector<SizeClass> classes;
+  CUtensorMap* d_tmaps = nullptr; // FP32: two TMA descriptors per member (its buffers, its class's tile box)
   int parity = 0;                 // members' current state is U[parity]
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> executable graph
   char err[512] = {0};
@@ -76,6 +77,17 @@ static cudaError_t build_tiles(hydro_batch* b, SizeClass& c, int shape) {
   e = cudaMemcpy(c.d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
   c.ntiles = (int)tiles.size();
   c.shape = shape;
+  // TMA descriptors of the class's members for this tile box (members without them load cell by cell)
+  if (e == cudaSuccess && b->d_tmaps) {
+    for (int m : c.members) {
+      CUtensorMap maps[2];
+      BatchMember& bm = b->hmem[m];
+      bm.tma = hydro::make_state_tensor_map(&maps[0], bm.P, b->precision, bm.U[0], tx, ty) &&
+               hydro::make_state_tensor_map(&maps[1], bm.P, b->precision, bm.U[1], tx, ty);
+      if (bm.tma && e == cudaSuccess) e = cudaMemcpy(b->d_tmaps + 2 * m, maps, sizeof maps, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(b->d_mem + m, &bm, sizeof bm, cudaMemcpyHostToDevice);
+    }
+  }
   return e;
 }
 
@@ -91,7 +103,7 @@ static cudaError_t enqueue_step(hydro_batch* b, int parity, cudaStream_t s) {
   for (auto& c : b->classes) {
     if (e != cudaSuccess) break;
     e = hydro::batch_step(b->precision, c.shape, b->d_mem, c.d_tiles, c.ntiles, c.d_queue, parity, b->d_agg, s,
-                          nullptr);
+                          nullptr, b->d_tmaps);
   }
   return e;
 }
@@ -160,6 +172,7 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
   b->nfill = (int)fill.size();
   b->ndt = (int)dtab.size();
   e = cudaMemcpy(b->d_mem, b->hmem.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && prec == HYDRO_FP32) e = cudaMalloc((void**)&b->d_tmaps, sizeof(CUtensorMap) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_fill, sizeof(int2) * std::max(b->nfill, 1));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_fill, fill.data(), sizeof(int2) * b->nfill, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_dt, sizeof(int4) * std::max(b->ndt, 1));
@@ -194,6 +207,7 @@ void hydro_batch_destroy(hydro_batch* b) {
   if (b->d_partials) cudaFree(b->d_partials);
   if (b->d_fill) cudaFree(b->d_fill);
   if (b->d_dt) cudaFree(b->d_dt);
+  if (b->d_tmaps) cudaFree(b->d_tmaps);
   delete b;
 }
 
@@ -217,7 +231,7 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes) 
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
         if (r == 1) cudaEventRecord(e0, b->stream);
         e = hydro::batch_step(b->precision, sh, b->d_mem, c.d_tiles, c.ntiles, c.d_queue, b->parity, b->d_agg,
-                              b->stream, nullptr);
+                              b->stream, nullptr, b->d_tmaps);
       }
       cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);

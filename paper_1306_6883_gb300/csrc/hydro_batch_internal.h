@@ -1,5 +1,6 @@
 // Internal interface of the batched (ensemble) kernels (not installed).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "hydro_device.cuh"
@@ -11,6 +12,7 @@ struct BatchMember {
   KParams P;
   void* U[2];        // the member's two state buffers; parity p reads U[p] and writes U[1 - p]
   DevScratch* scr;   // the member's own dt, step factors, time and status
+  int tma;           // 1: the member's tiles load by TMA from the tensor maps 2*member + parity
 };
 
 constexpr int BATCH_DT_CELLS = 2048;  // cells reduced by one block of the batched dt kernel
@@ -28,8 +30,11 @@ cudaError_t batch_fill(int precision, const BatchMember* mem, const int2* tab, i
 cudaError_t batch_dt(int precision, const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
                      cudaStream_t stream);
 // tiles[k] = (member, tile x, tile y, 0) for tile shape `shape` (FP64 always uses 16 x 16)
+// tmaps (FP32, may be NULL): device array of two TMA descriptors per member (one per state buffer) with the
+// box of `shape`, used for members whose tma flag is set
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
-                       unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out);
+                       unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out,
+                       const CUtensorMap* tmaps = nullptr);
 // set the kernel attributes of every shape (call once before any stream capture)
 cudaError_t batch_prepare(int precision);
 

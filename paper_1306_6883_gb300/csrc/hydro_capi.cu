@@ -59,29 +59,36 @@ static encode_tiled_fn tensor_map_encoder() {
   return fn;
 }
 
-// Describe each FP32 state buffer as a 3-D tensor (x over the padded width, y over the padded height, the 4
-// conserved components) with the step kernel's (TX+8) x (TY+8) x 4 tile box.  TMA wants 16-byte aligned
-// bases and strides (the buffers are 256-byte aligned and rows are padded to 128 bytes) and 16-byte aligned
-// x coordinates: tile boxes start at x = ng - 4 + k * TX, so ng must be a multiple of 4.  Returns 0 (tiles
-// then load cell by cell) when any condition or the encoder is missing.
-static int make_tensor_maps(hydro_ctx* c) {
-  if (c->p.precision != HYDRO_FP32 || c->p.ng % 4 != 0) return 0;
-  if ((hydro::f32_tile_x() * sizeof(float)) % 16 != 0) return 0;
+namespace hydro {
+
+// Describe one FP32 state buffer as a 3-D tensor (x over the padded width, y over the padded height, the 4
+// conserved components) with a (tile_x + 8) x (tile_y + 8) x 4 box.  TMA wants 16-byte aligned bases and
+// strides (buffers are 256-byte aligned and rows padded to 128 bytes) and 16-byte aligned x coordinates:
+// tile boxes start at x = ng - 4 + k * tile_x, so ng - 4 and tile_x must be multiples of 4.  Returns 0
+// (tiles then load cell by cell) when a condition or the encoder is missing.
+int make_state_tensor_map(CUtensorMap* map, const KParams& k, int precision, void* base, int tile_x, int tile_y) {
+  if (precision != HYDRO_FP32 || (k.ng - 4) % 4 != 0 || tile_x % 4 != 0) return 0;
   encode_tiled_fn enc = tensor_map_encoder();
   if (!enc) return 0;
-  const cuuint64_t row = (cuuint64_t)c->kp.pitch * sizeof(float);
-  const cuuint64_t dims[3] = {(cuuint64_t)c->kp.NX, (cuuint64_t)c->kp.NY, 4};
-  const cuuint64_t strides[2] = {row, row * (cuuint64_t)c->kp.NY};
-  const cuuint32_t box[3] = {(cuuint32_t)hydro::f32_tile_x() + 8, (cuuint32_t)hydro::f32_tile_y() + 8, 4};
+  const cuuint64_t row = (cuuint64_t)k.pitch * sizeof(float);
+  const cuuint64_t dims[3] = {(cuuint64_t)k.NX, (cuuint64_t)k.NY, 4};
+  const cuuint64_t strides[2] = {row, row * (cuuint64_t)k.NY};
+  const cuuint32_t box[3] = {(cuuint32_t)tile_x + 8, (cuuint32_t)tile_y + 8, 4};
   const cuuint32_t estr[3] = {1, 1, 1};
-  if (row % 16 != 0 || box[0] * sizeof(float) % 16 != 0) return 0;
-  for (int b = 0; b < 2; ++b) {
-    if ((uintptr_t)c->state[b] % 16 != 0) return 0;
-    if (enc(&c->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->state[b], dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  if (row % 16 != 0 || (uintptr_t)base % 16 != 0 || box[0] > 256 || box[1] > 256) return 0;
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+}  // namespace hydro
+
+// Tensor maps of the context's two buffers for the single-problem FP32 tile.
+static int make_tensor_maps(hydro_ctx* c) {
+  for (int b = 0; b < 2; ++b)
+    if (!hydro::make_state_tensor_map(&c->tmap[b], c->kp, c->p.precision, c->state[b], hydro::f32_tile_x(),
+                                      hydro::f32_tile_y()))
       return 0;
-  }
   return 1;
 }
 

@@ -69,6 +69,10 @@ void fill_kparams(const hydro_params* p, KParams* k);
 cudaError_t upload_rows(const void* host_dev, void* dst, size_t row_bytes, size_t dst_pitch_bytes, int rows,
                         cudaStream_t stream);
 
+// TMA descriptor of one FP32 state buffer with the (tile_x + 8) x (tile_y + 8) x 4 box of a tile (host);
+// 0 when the precision, alignment or driver does not allow one.
+int make_state_tensor_map(CUtensorMap* map, const KParams& k, int precision, void* base, int tile_x, int tile_y);
+
 // Scratch initialisation (min accumulator = +inf, counters 0).
 cudaError_t init_scratch(DevScratch* scr, cudaStream_t stream);
 

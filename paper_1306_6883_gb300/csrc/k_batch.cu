@@ -31,14 +31,19 @@ const TileShape kTileShapes[] = {
 const int kNumTileShapes = sizeof(kTileShapes) / sizeof(kTileShapes[0]);
 
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
-                       unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out) {
+                       unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out,
+                       const CUtensorMap* tmaps) {
   if (precision == 0)  // the FP64 path keeps one shape (its cost is the FP64 pipe, not the tile)
     return batch_step_f64(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
   switch (shape) {
-    case 0: return BatchStep<float, 32, 16, 384>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
-    case 1: return BatchStep<float, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
-    case 2: return BatchStep<float, 32, 8, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
-    case 3: return BatchStep<float, 32, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+    case 0: return BatchStep<float, 32, 16, 384>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
+                                                              tmaps);
+    case 1: return BatchStep<float, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
+                                                              tmaps);
+    case 2: return BatchStep<float, 32, 8, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
+                                                              tmaps);
+    case 3: return BatchStep<float, 32, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
+                                                              tmaps);
     default: return cudaErrorInvalidValue;
   }
 }

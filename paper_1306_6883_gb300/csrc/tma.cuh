@@ -29,6 +29,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned int bar, unsigned
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(unsigned int bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Bounded wait for the phase with the given parity to complete; true if it did.
 __device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity) {
   for (unsigned int k = 0; k < TMA_WAIT_POLLS; ++k) {
