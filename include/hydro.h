@@ -299,6 +299,13 @@ const char* hydro_build_info(void);
  * counterpart: how the data reaches shared memory does not change what a step computes. */
 int hydro_tma_enabled(const hydro_ctx* ctx);
 
+/* Failure-path test of the bounded device-side wait (no paper counterpart).  drop = 1: the step kernels
+ * issue no TMA tile copy, so each such tile's mbarrier waits for bytes that never arrive; the wait gives up
+ * after `polls` polls (1000 if 0), the tile is left unwritten and the status word records a timeout
+ * (HYDRO_ETIMEOUT from hydro_sync_status).  Nothing is in flight when a tile gives up, and the context
+ * stays usable.  drop = 0 restores normal operation.  Returns HYDRO_EINVAL for other values of drop. */
+hydro_status hydro_test_drop_tile_copies(hydro_ctx* ctx, int drop, unsigned int polls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -158,18 +158,19 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     // the generic proxy; order those accesses before the copy's async-proxy writes
     fence_proxy_async_smem();
     __syncthreads();
+    const unsigned int polls = P.tma_polls ? P.tma_polls : TMA_WAIT_POLLS;
     if (tid == 0) {
       mbar_init(bar, 1);
       mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
-      tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
+      if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
     }
     __syncthreads();
-    const bool landed = mbar_wait(bar, 0);
+    const bool landed = mbar_wait(bar, 0, polls);
     if (__syncthreads_or(!landed)) {
       // the copy did not complete within the poll budget: report it, give it one more budget to land
       // (the shared memory must not be released under it) and leave this tile
       cnt.flags |= STATUS_TIMEOUT;
-      mbar_wait(bar, 0);
+      mbar_wait(bar, 0, polls);
       __syncthreads();
       if (tid == 0) mbar_inval(bar);
       return;

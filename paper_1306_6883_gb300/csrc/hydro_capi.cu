@@ -504,4 +504,12 @@ const char* hydro_build_info(void) {
 
 int hydro_tma_enabled(const hydro_ctx* c) { return c ? c->tma_ok : 0; }
 
+hydro_status hydro_test_drop_tile_copies(hydro_ctx* c, int drop, unsigned int polls) {
+  if (!c || (drop != 0 && drop != 1)) return HYDRO_EINVAL;
+  c->kp.tma_test_drop = drop;
+  c->kp.tma_polls = drop ? (polls ? polls : 1000u) : 0u;
+  c->fused_valid = 0;
+  return HYDRO_OK;
+}
+
 }  // extern "C"

@@ -30,6 +30,10 @@ struct KParams {
   double small_dens, small_pres;
   // float copies (filled on the host) so the FP32 kernels never convert from double
   float gamma_f, gm1_f, igm1_f, g1_f, small_dens_f, small_pres_f, tol_f, cvisc_f, dx_f, dy_f, idx_f, idy_f;
+  // failure-path test of the bounded TMA wait (0, 0 in normal operation): tma_test_drop = 1 issues no tile
+  // copy (the tile's mbarrier then waits for bytes that never come); tma_polls != 0 replaces the poll budget
+  int tma_test_drop;
+  unsigned int tma_polls;
 };
 
 // Time-step dependent factors of one CTU step, computed once in double (host, or the last block of

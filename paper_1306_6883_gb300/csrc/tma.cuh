@@ -38,9 +38,9 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Bounded wait for the phase with the given parity to complete; true if it did.
-__device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity) {
-  for (unsigned int k = 0; k < TMA_WAIT_POLLS; ++k) {
+// Bounded wait (polls polls) for the phase with the given parity to complete; true if it did.
+__device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity, unsigned int polls) {
+  for (unsigned int k = 0; k < polls; ++k) {
     unsigned int done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"

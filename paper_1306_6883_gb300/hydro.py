@@ -97,6 +97,7 @@ SIGNATURES = {
     "hydro_last_error": (ctypes.c_char_p, [_VP]),
     "hydro_build_info": (ctypes.c_char_p, []),
     "hydro_tma_enabled": (ctypes.c_int, [_VP]),
+    "hydro_test_drop_tile_copies": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint]),
 }
 
 
@@ -227,6 +228,10 @@ def hydro_build_info():
 
 def hydro_tma_enabled(ctx):
     return bool(load().hydro_tma_enabled(ctx))
+
+
+def hydro_test_drop_tile_copies(ctx, drop, polls=0):
+    _check(load().hydro_test_drop_tile_copies(ctx, int(drop), int(polls)), ctx, "hydro_test_drop_tile_copies")
 
 
 # ---------------------------------------------------------------------------------------------------- ensembles

@@ -407,6 +407,32 @@ def test_riemann_nonconvergence_is_reported():
     s.close()
 
 
+def test_a_lost_tile_copy_times_out_and_the_context_recovers():
+    # the bounded wait on a tile's TMA copy: with the copies withheld (nothing in flight) every TMA tile gives
+    # up after its poll budget and the host reads HYDRO_ETIMEOUT; with the copies restored the same context
+    # steps exactly like a fresh one
+    H, Solver, params_for = _mods()
+    pr = hp.kh(256, 256, seed=5)
+    s = Solver(params_for(pr, 1), pr.U)
+    assert H.hydro_tma_enabled(s.ctx)
+    H.hydro_test_drop_tile_copies(s.ctx, 1, 200)
+    s.step_fused()
+    st, _ = s.status(raise_on_error=False)
+    assert st == H.HYDRO_ETIMEOUT
+    H.hydro_test_drop_tile_copies(s.ctx, 0)
+    s.set_state(pr.U)
+    s.advance(3)
+    st, _ = s.status(raise_on_error=False)
+    assert st == H.HYDRO_OK
+    ref = Solver(params_for(pr, 1), pr.U)
+    ref.advance(3)
+    np.testing.assert_array_equal(_interior(s.state_numpy()), _interior(ref.state_numpy()))
+    s.close()
+    ref.close()
+    with pytest.raises(H.HydroError):
+        H.hydro_test_drop_tile_copies(None, 1, 10)
+
+
 @pytest.mark.parametrize("precision,ng,expect", [(1, 4, True), (0, 4, False), (1, 6, False)])
 def test_tile_loads_use_tma_where_they_can(precision, ng, expect):
     # FP32 contexts whose tile boxes start on 16-byte boundaries (ng a multiple of 4) load interior tiles by
