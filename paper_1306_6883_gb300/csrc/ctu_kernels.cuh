@@ -110,8 +110,23 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   f.load(*sc_cur);
   TileCounters cnt;
   R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
-  ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
-                                            nullptr, &cmin, use_tma ? &tmap : nullptr);
+  if (sc_cur->dt == 0.0) {
+    // a step of length zero (the run has reached tmax) leaves the state as it is: copy the tile's interior
+    // cells and take their CFL constraint as a step would (the next dt is then clamped to 0 again)
+    const size_t plane = (size_t)P.NY * P.pitch;
+    for (int e = threadIdx.x; e < TX * TY; e += NT) {
+      const int gi = P.ng + blockIdx.x * TX + e % TX, gj = P.ng + blockIdx.y * TY + e / TX;
+      if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
+      const size_t o = (size_t)gj * P.pitch + gi;
+      R u[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Uout[o + k * plane] = u[k] = Uin[o + k * plane];
+      cfl_value(s, u[0], u[1], u[2], u[3], cmin, cnt.flags);
+    }
+  } else {
+    ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt,
+                                              FaceHook{}, nullptr, &cmin, use_tma ? &tmap : nullptr);
+  }
   flush_counters<NT>(cnt, scr);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
