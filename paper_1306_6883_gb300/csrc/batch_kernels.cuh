@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(con
     StepFactors<R> f;
     f.load(m.scr->sc);
     const CUtensorMap* tm = (tmaps != nullptr && m.tma) ? tmaps + 2 * t.x + parity : nullptr;
-    ctu_tile<R, TX, TY, NT>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z, smem_raw, cnt,
+    ctu_tile<R, TX, TY, NT, FACE_PLAIN, false, true>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y,
+                                                     t.z, smem_raw, cnt,
                             FaceHook{}, nullptr, nullptr, tm);
     __syncthreads();  // the tile's last shared-memory reads finish before the next tile's loads
   }

@@ -104,8 +104,10 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
 // state, so consecutive calls by the same block need one __syncthreads() between them.  MODE selects
 // the face-solve variant (face_solve); wsm is the network's weights for FACE_LEARNED.  FUSED: ghost cells
 // come from the boundary-condition map of the interior (no ghost fill needed) and the CFL constraint of
-// every new cell is folded into *cfl_min (no separate dt pass needed).
-template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false>
+// every new cell is folded into *cfl_min (no separate dt pass needed).  PERSIST: the block runs several
+// tiles in turn (a TMA tile load then first orders the previous tile's shared-memory accesses before it).
+// tmap: TMA descriptor of Uin for FP32 tile loads (NULL: cell by cell).
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false, bool PERSIST = false>
 __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
                                          const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
                                          unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
@@ -154,10 +156,12 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   if (tma_tile) {
     __shared__ unsigned long long tma_bar;
     const unsigned int bar = smem_addr(&tma_bar);
-    // a block that runs several tiles (persistent kernel) has read and written this shared memory through
-    // the generic proxy; order those accesses before the copy's async-proxy writes
-    fence_proxy_async_smem();
-    __syncthreads();
+    if constexpr (PERSIST) {
+      // a block that runs several tiles has read and written this shared memory through the generic
+      // proxy; order those accesses before the copy's async-proxy writes
+      fence_proxy_async_smem();
+      __syncthreads();
+    }
     const unsigned int polls = P.tma_polls ? P.tma_polls : TMA_WAIT_POLLS;
     if (tid == 0) {
       mbar_init(bar, 1);

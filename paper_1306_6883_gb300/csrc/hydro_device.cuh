@@ -496,11 +496,20 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     const float ST = ust - sgn * M<float>::sq(g * pst * irst);  // fan tail u* -+ c*
     const bool take_o = shock ? sgn * S >= 0.0f : sgn * SH >= 0.0f;
     const bool take_star = shock ? !take_o : sgn * ST <= 0.0f;
-    const float frac = SH * rcpa(SH - ST);  // inside the fan only (selected away elsewhere)
-    fr = take_o ? ro : take_star ? rst : ro + frac * (rst - ro);
-    fu = take_o ? uo : take_star ? ust : uo + frac * (ust - uo);
-    fp = take_o ? po : take_star ? pst : po + frac * (pst - po);
+    fr = take_o ? ro : rst;
+    fu = take_o ? uo : ust;
+    fp = take_o ? po : pst;
     fv = vo;
+    // transonic fans are rare: the interpolation runs only in warps that have one
+    const bool in_fan = !take_o && !take_star;
+    if (__any_sync(__activemask(), in_fan)) {
+      const float frac = SH * rcpa(SH - ST);
+      if (in_fan) {
+        fr = ro + frac * (rst - ro);
+        fu = uo + frac * (ust - uo);
+        fp = po + frac * (pst - po);
+      }
+    }
   }
   face_flux(s, fr, fu, fv, fp, F);
   if (pstar_out) *pstar_out = pst;
