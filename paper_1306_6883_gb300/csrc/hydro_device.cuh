@@ -433,9 +433,8 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float xl = g * pl * rl, xr = g * pr * rr;
   const float icl = rsqa(xl), icr = rsqa(xr);  // 1/C_K
   const float cl = xl * icl, cr = xr * icr;
-  // 1/C_K^2 = 1/(gamma p_K rho_K) gives 1/p_K = gamma rho_K / C_K^2 and c_K = C_K/rho_K = gamma p_K / C_K
-  // without further reciprocals
-  const float ipl = g * rl * icl * icl, ipr = g * rr * icr * icr;
+  // one MUFU reciprocal each costs fewer issue slots than forming 1/p_K from 1/C_K^2 = 1/(gamma p_K rho_K)
+  const float ipl = rcpa(pl), ipr = rcpa(pr);
   // velocity scale of the problem: float rounding leaves u*_R - u*_L uncertain by ~2^-24 of it, which can
   // exceed tol * p* in pressure when p* << rho u^2, so the FP32 stopping rule also accepts a pressure
   // change smaller than the one a velocity mismatch of tol times this scale would produce
@@ -487,7 +486,7 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
     const float wo = left ? wl : wr;
     const float ico = left ? icl : icr;
     const float iwo = (left ? tl : tr) * ico;
-    const float iro = g * po * ico * ico;             // 1/rho_o
+    const float iro = rcpa(ro);                       // 1/rho_o
     const float irst = iro - (pst - po) * iwo * iwo;  // 1/rho*, Hugoniot
     const float rst = rcpa(irst);
     const bool shock = pst > po;
