@@ -3,7 +3,7 @@
 //
 // A CTA computes TX x TY interior cells.  It stages the (TX+8) x (TY+8) primitive tile (4-cell halo) in
 // shared memory and runs every stage of the step on it without sending any intermediate to global memory:
-//   0. load U, convert to primitives                        (Eqs. 11-12)
+//   0. load U (FP32 tiles inside the valid array: one TMA bulk tensor copy), convert to primitives (Eqs. 11-12)
 //   1. flattening coefficient xi on (TX+2) x (TY+2) cells    (§3.2, Colella 1990)
 //   2. limited slopes and characteristic tracing, x and y     (§3.1 limiter; Eq. 13)
 //   3. Riemann solves on the traced (hat) states at all faces the transverse terms need
