@@ -37,8 +37,12 @@ sys.path.insert(0, ROOT)
 FLOPS_BASE = 973.0
 FLOPS_PER_ITER = 40.0
 SOLVES_PER_ZONE = 4.008
-# measured ALU peaks on this machine's GB300 (FMA = 2 flops; 152 SMs): FP32 70.6 TFLOP/s, FP64 1.16 TFLOP/s
-ALU_PEAK_TFLOPS = {"fp32": 70.6, "fp64": 1.16}
+# ALU peaks from the unit counts and the maximum SM clock (FMA = 2 flops): FP32 152 SMs x 128 lanes x 2 x
+# 2070 MHz = 80.55 TFLOP/s; FP64 the part's 1.25 TFLOP/s.  (FMA-chain microbenchmarks on the same GPUs reach
+# 73.4 and 1.16 TFLOP/s.)
+ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64": 1.25}
+ALU_PEAK_SOURCE = {"fp32": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts x max SM clock)",
+                   "fp64": "GB300 FP64 rate 1.25 TFLOP/s"}
 
 
 # DRAM bytes (read + write) of one launch of the FP32 fused step kernel on the KH 1024^2 workload, from an
@@ -466,7 +470,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "ctu_step_fused_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"measured {args.precision} FMA-chain throughput on all 152 SMs",
+                     "peak_source": ALU_PEAK_SOURCE[args.precision],
                      "flops_per_zone": flops_zone, "kernel_ms": kern_ms,
                      "hbm_gbs": bytes_zone * zones / (kern_ms * 1e-3) / 1e9, "hbm_frac_of_measured": None,
                      "traffic": None, "traffic_note": None},
