@@ -228,6 +228,33 @@ def time_e2e(pr, precision, steps, warmup):
     return {"seconds": el, "h2d": nbytes, "d2h": nbytes}
 
 
+def fp32_error(pr, steps=50):
+    """Error of the FP32 path against the FP64 path after `steps` fused steps from the same initial state:
+    L1 and max of |U32 - U64| per field, relative to the field's L1 norm and maximum.  The FP64 path rounds
+    exactly like the oracle (bit-identical runs are a test of the suite), so this is the FP32 error against
+    the oracle."""
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Solver, params_for
+
+    out = {}
+    for prec in (H.HYDRO_FP64, H.HYDRO_FP32):
+        s = Solver(params_for(pr, prec), pr.U)
+        s.advance(steps)
+        ng = pr.ng
+        out[prec] = (s.state_numpy()[:, ng:-ng, ng:-ng].astype(np.float64), s.time())
+        s.status()
+        s.close()
+    a, (t32, _) = out[H.HYDRO_FP32]
+    b, (t64, _) = out[H.HYDRO_FP64]
+    d = np.abs(a - b).reshape(4, -1)
+    ref = np.abs(b).reshape(4, -1)
+    names = ("rho", "rho_u", "rho_v", "E")
+    return {"steps": steps, "against": "FP64 GPU path (bit-identical to the oracle)",
+            "l1_rel": dict(zip(names, (d.sum(1) / ref.sum(1)).tolist())),
+            "max_rel": dict(zip(names, (d.max(1) / ref.max(1)).tolist())),
+            "t_rel": abs(t32 - t64) / t64}
+
+
 def time_ensemble(steps=100, warmup=3, n=256, seed=0):
     """The 256-member ensemble of four-quadrant problems on {64,128,256,512}^2 grids (seeded), FP32, each
     member with its own CFL dt; tile shapes autotuned per size class; `steps` steps captured in one CUDA
@@ -426,6 +453,7 @@ def run_ours(args, world, rank, local):
     other = "fp64" if args.precision == "fp32" else "fp32"
     var = time_device_path(pr, other, max(args.steps // 4, 10), args.warmup, flush)
     e2e = time_e2e(pr, args.precision, max(args.steps // 4, 10), args.warmup)
+    accuracy = fp32_error(pr) if args.precision == "fp32" else None
     ens = time_ensemble() if args.precision == "fp32" else None
     learned = None
     if args.precision == "fp32":
@@ -483,6 +511,7 @@ def run_ours(args, world, rank, local):
                              "speedup_of_" + args.precision: value / world / var_value if args.precision == "fp32"
                              else var_value / (value / world)}},
         "riemann_iters_per_solve": main["iters_per_solve"],
+        "fp32_error": accuracy,
         "ensemble": ens,
         "learned_proposal": learned,
     }
