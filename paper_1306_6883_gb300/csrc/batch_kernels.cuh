@@ -5,6 +5,8 @@
 #pragma once
 #include <float.h>
 
+#include <atomic>
+
 #include "ctu_tile.cuh"
 #include "hydro_batch_internal.h"
 
@@ -157,17 +159,22 @@ __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(con
 
 template <typename R, int TX, int TY, int NT>
 struct BatchStep {
-  static int blocks_per_sm;  // occupancy of this instantiation, set by prepare()
+  // per device (function attributes and occupancy belong to the device's context): set by prepare()
+  static std::atomic<int> blocks_per_sm[64];
   static cudaError_t prepare() {
-    if (blocks_per_sm > 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (blocks_per_sm[dev].load(std::memory_order_relaxed) > 0) return cudaSuccess;
     const size_t smem = TileLayout<R, TX, TY>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<R, TX, TY, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(batch_step_kernel<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<R, TX, TY, NT>, NT, smem);
     if (e != cudaSuccess) return e;
-    blocks_per_sm = b > 0 ? b : 1;
+    blocks_per_sm[dev].store(b > 0 ? b : 1, std::memory_order_relaxed);
     return cudaSuccess;
   }
   static cudaError_t launch(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
@@ -179,7 +186,7 @@ struct BatchStep {
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    int grid = nsm * blocks_per_sm;
+    int grid = nsm * blocks_per_sm[dev].load(std::memory_order_relaxed);
     if (grid > ntiles) grid = ntiles;
     if (grid_out) *grid_out = grid;
     if (grid <= 0) return cudaSuccess;
@@ -191,6 +198,6 @@ struct BatchStep {
   }
 };
 template <typename R, int TX, int TY, int NT>
-int BatchStep<R, TX, TY, NT>::blocks_per_sm = 0;
+std::atomic<int> BatchStep<R, TX, TY, NT>::blocks_per_sm[64] = {};
 
 }  // namespace hydro

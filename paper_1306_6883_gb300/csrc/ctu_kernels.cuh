@@ -4,6 +4,8 @@
 #pragma once
 #include <float.h>
 
+#include <atomic>
+
 #include "ctu_tile.cuh"
 #include "hydro_kernels.h"
 
@@ -76,18 +78,28 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_kernel(KParams P
   flush_counters<NT>(cnt, scr);
 }
 
+// Raises a kernel's dynamic shared-memory limit once per device (function attributes belong to the device's
+// context); later calls on the same device only test a bit.  Devices beyond 63 set it on every call.
+template <typename K>
+cudaError_t smem_attr_once(K kernel, size_t smem, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_relaxed);
+  return e;
+}
+
 template <typename R, int TX, int TY, int NT, int MODE>
 cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
                             const StepScalars* sc_dev, DevScratch* scr, const FaceHook& hook, const CUtensorMap* tmap,
                             cudaStream_t stream) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
-  static bool attr_set = false;  // per instantiation; the attribute is per function, not per device
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ctu_step_kernel<R, TX, TY, NT, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  cudaError_t e = smem_attr_once(ctu_step_kernel<R, TX, TY, NT, MODE>, smem, attr_done);
+  if (e != cudaSuccess) return e;
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   ctu_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr, hook,
                                                                     tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0);
@@ -169,13 +181,9 @@ cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const
                                   StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
                                   cudaStream_t stream) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ctu_step_fused_kernel<R, TX, TY, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  cudaError_t e = smem_attr_once(ctu_step_fused_kernel<R, TX, TY, NT>, smem, attr_done);
+  if (e != cudaSuccess) return e;
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
                                                                    tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0);

@@ -46,16 +46,14 @@ typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static encode_tiled_fn tensor_map_encoder() {
-  static encode_tiled_fn fn = nullptr;
-  static bool looked = false;
-  if (!looked) {
-    looked = true;
+  static const encode_tiled_fn fn = [] {  // looked up once (thread-safe static initialisation)
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (encode_tiled_fn)f;
-  }
+      return (encode_tiled_fn)f;
+    return (encode_tiled_fn) nullptr;
+  }();
   return fn;
 }
 

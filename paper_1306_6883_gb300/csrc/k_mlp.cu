@@ -5,6 +5,7 @@
 // launches: mlp_grad_kernel (each block takes 64 samples through forward and backward passes in shared
 // memory and writes its partial gradient), then mlp_reduce_kernel (sums the block partials in block order
 // -- deterministic -- and applies Adam, or just stores the gradient).  All arithmetic FP32.
+#include <atomic>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -370,12 +371,17 @@ static cudaError_t repack(hydro_mlp* m) {
 
 static cudaError_t grad_launch(hydro_mlp* m, const float* samples, unsigned long long n, unsigned long long seed,
                                int blocks, float inv_count) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(hydro::mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(hydro::MlpSmem));
+  // the attribute belongs to the device's context: set it once per device
+  static std::atomic<unsigned long long> attr_done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (!bit || !(attr_done.load(std::memory_order_relaxed) & bit)) {
+    e = cudaFuncSetAttribute(hydro::mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(hydro::MlpSmem));
     if (e != cudaSuccess) return e;
-    attr = true;
+    if (bit) attr_done.fetch_or(bit, std::memory_order_relaxed);
   }
   hydro::mlp_grad_kernel<<<blocks, hydro::MLP_THREADS, sizeof(hydro::MlpSmem), m->stream>>>(m->theta, samples, n, seed,
                                                                                            inv_count, m->partial);
