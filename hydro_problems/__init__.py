@@ -20,13 +20,15 @@ class Problem:
     nx: int
     ny: int
     U: np.ndarray                    # (4, ny+2ng, nx+2ng) float64, interior set, ghosts zero
-    bc: tuple                        # (xlo, xhi, ylo, yhi), each "outflow" or "periodic"
+    bc: tuple                        # (xlo, xhi, ylo, yhi): "outflow", "periodic", "reflect" or
+                                     # "hydrostatic" (y sides)
     gamma: float = 1.4
     cfl: float = 0.8
     tmax: float = 0.2
     domain: tuple = (0.0, 1.0, 0.0, 1.0)
     ng: int = NG
     extra: dict = field(default_factory=dict)
+    grav: float = 0.0                # constant gravitational acceleration along y
 
 
 def _centres(nx, ny, domain=(0.0, 1.0, 0.0, 1.0)):
@@ -61,6 +63,25 @@ def sod(nx=128, ny=128, direction="x", gamma=1.4):
     bc = ("outflow", "outflow", "periodic", "periodic") if direction == "x" else \
         ("periodic", "periodic", "outflow", "outflow")
     return Problem("sod_" + direction, nx, ny, _pack(rho, z, z, p, gamma), bc, gamma=gamma, cfl=0.8, tmax=0.2)
+
+
+def rt(nx=128, ny=384, rho1=1.0, rho2=2.0, grav=-1.0, p0=5.0, amp=0.01, sigma=0.1, gamma=1.4, lx=1.0, ly=3.0):
+    """Single-mode Rayleigh-Taylor instability (paper §3.2, Rayleigh-Taylor set-up and Fig. 4): rho = rho1
+    below y_c = ly/2 and rho2 above (2:1 ratio); pressure in hydrostatic equilibrium for constant g,
+    p = p0 + rho1 g y below y_c, p0 + rho1 g y_c + rho2 g (y - y_c) above (evaluated at cell centres);
+    v = amp cos(2 pi x / lx) exp(-(y - y_c)^2 / sigma^2), u = 0.  Periodic in x, hydrostatic boundaries
+    in y, gravity along -y.  The paper ran 128 x 384 zones at CFL 0.8; it does not state p0, amp, sigma or
+    the domain, which are this generator's choices (p0 keeps the pressure positive over the column)."""
+    domain = (0.0, lx, 0.0, ly)
+    X, Y = _centres(nx, ny, domain)
+    yc = 0.5 * ly
+    below = Y < yc
+    rho = np.where(below, rho1, rho2)
+    p = np.where(below, p0 + rho1 * grav * Y, p0 + rho1 * grav * yc + rho2 * grav * (Y - yc))
+    v = amp * np.cos(2.0 * np.pi * X / lx) * np.exp(-((Y - yc) ** 2) / sigma ** 2)
+    u = np.zeros_like(rho)
+    return Problem("rt", nx, ny, _pack(rho, u, v, p, gamma), ("periodic", "periodic", "hydrostatic", "hydrostatic"),
+                   gamma=gamma, cfl=0.8, tmax=3.0, domain=domain, grav=grav)
 
 
 def kh(nx=1024, ny=1024, seed=0, gamma=1.4):

@@ -24,7 +24,7 @@ class OracleParams(ctypes.Structure):
         ("bc_xlo", ctypes.c_int), ("bc_xhi", ctypes.c_int), ("bc_ylo", ctypes.c_int), ("bc_yhi", ctypes.c_int),
         ("limiter", ctypes.c_int), ("use_flattening", ctypes.c_int), ("cvisc", ctypes.c_double),
         ("riemann_maxiter", ctypes.c_int), ("riemann_tol", ctypes.c_double),
-        ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double),
+        ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double), ("grav", ctypes.c_double),
     ]
 
 
@@ -64,11 +64,11 @@ def lib():
 
 def params(nx, ny, *, ng=4, xmin=0.0, xmax=1.0, ymin=0.0, ymax=1.0, gamma=1.4, cfl=0.8,
            bc=("outflow", "outflow", "outflow", "outflow"), limiter=2, use_flattening=1, cvisc=0.1,
-           riemann_maxiter=32, riemann_tol=1e-14, small_dens=1e-10, small_pres=1e-20):
-    code = {"outflow": 0, "periodic": 1}
+           riemann_maxiter=32, riemann_tol=1e-14, small_dens=1e-10, small_pres=1e-20, grav=0.0):
+    code = {"outflow": 0, "periodic": 1, "reflect": 2, "hydrostatic": 3}
     return OracleParams(nx, ny, ng, xmin, xmax, ymin, ymax, gamma, cfl,
                         code[bc[0]], code[bc[1]], code[bc[2]], code[bc[3]],
-                        limiter, use_flattening, cvisc, riemann_maxiter, riemann_tol, small_dens, small_pres)
+                        limiter, use_flattening, cvisc, riemann_maxiter, riemann_tol, small_dens, small_pres, grav)
 
 
 def _ptr(a):

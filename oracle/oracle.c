@@ -44,6 +44,8 @@ static int params_ok(const oracle_params* p) {
   if (!(p->xmax > p->xmin) || !(p->ymax > p->ymin)) return 0;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return 0;
   if ((p->bc_xlo == 1) != (p->bc_xhi == 1) || (p->bc_ylo == 1) != (p->bc_yhi == 1)) return 0;
+  if (p->bc_xlo < 0 || p->bc_xlo > 2 || p->bc_xhi < 0 || p->bc_xhi > 2) return 0; /* hydrostatic: y only */
+  if (p->bc_ylo < 0 || p->bc_ylo > 3 || p->bc_yhi < 0 || p->bc_yhi > 3) return 0;
   if (p->bc_xlo == 1 && p->nx < p->ng) return 0;
   if (p->bc_ylo == 1 && p->ny < p->ng) return 0;
   if (p->limiter < 0 || p->limiter > 2) return 0;
@@ -280,23 +282,57 @@ int oracle_riemann(const oracle_params* p, const double qL[4], const double qR[4
 /* Ghost cells (§2 CellCenterData2d "filling ghost cells"; Fig. 1; zero-gradient copy as described for
  * the RT problem in §3.2.3): outflow copies the last valid cell, periodic wraps.  The x pass fills the
  * ghost columns of the interior rows, then the y pass fills whole ghost rows, so corners are defined. */
+/* Ghost cells (paper §2 and the RT set-up of §3.2): x pass over the interior rows, then y pass over the
+ * full padded width, so that corners are consistent.
+ *   outflow (0): copy of the nearest interior cell (zero gradient);
+ *   periodic (1): wrap;
+ *   reflecting (2): mirror image of the interior across the wall, normal momentum negated;
+ *   hydrostatic (3, y sides): density and both momenta copied from the row next to the wall; the pressure
+ *     of that row's cell integrated with dp/dy = rho g at constant rho into the ghost cells,
+ *     p = p_edge + rho g (y - y_edge), and the energy rebuilt from it (p/(gamma-1) + kinetic). */
 int oracle_fill_ghost(const oracle_params* p, double* U) {
   if (!params_ok(p) || !U) return 1;
   const int ng = p->ng, nx = p->nx, ny = p->ny, NX = nx + 2 * ng, NY = ny + 2 * ng;
+  const size_t plane = (size_t)NX * NY;
+  const double dy = (p->ymax - p->ymin) / ny;
   for (int k = 0; k < NVAR; ++k) {
-    double* a = U + (size_t)k * NX * NY;
+    double* a = U + (size_t)k * plane;
+    const double flip = (k == IMX) ? -1.0 : 1.0;
     for (int j = ng; j < ng + ny; ++j) {
       double* row = a + (size_t)j * NX;
-      for (int i = 0; i < ng; ++i) row[i] = (p->bc_xlo == 1) ? row[i + nx] : row[ng];
-      for (int i = ng + nx; i < NX; ++i) row[i] = (p->bc_xhi == 1) ? row[i - nx] : row[ng + nx - 1];
+      for (int i = 0; i < ng; ++i)
+        row[i] = p->bc_xlo == 1 ? row[i + nx] : p->bc_xlo == 2 ? flip * row[2 * ng - 1 - i] : row[ng];
+      for (int i = ng + nx; i < NX; ++i)
+        row[i] = p->bc_xhi == 1   ? row[i - nx]
+                 : p->bc_xhi == 2 ? flip * row[2 * (ng + nx) - 1 - i]
+                                  : row[ng + nx - 1];
     }
-    for (int j = 0; j < ng; ++j) {
-      int src = (p->bc_ylo == 1) ? j + ny : ng;
-      memcpy(a + (size_t)j * NX, a + (size_t)src * NX, sizeof(double) * NX);
-    }
-    for (int j = ng + ny; j < NY; ++j) {
-      int src = (p->bc_yhi == 1) ? j - ny : ng + ny - 1;
-      memcpy(a + (size_t)j * NX, a + (size_t)src * NX, sizeof(double) * NX);
+  }
+  for (int side = 0; side < 2; ++side) {
+    const int bc = side == 0 ? p->bc_ylo : p->bc_yhi;
+    const int edge = side == 0 ? ng : ng + ny - 1;
+    for (int j = (side == 0 ? 0 : ng + ny); j < (side == 0 ? ng : NY); ++j) {
+      const int src = bc == 1 ? (side == 0 ? j + ny : j - ny)
+                      : bc == 2 ? (side == 0 ? 2 * ng - 1 - j : 2 * (ng + ny) - 1 - j)
+                                : edge;
+      for (int i = 0; i < NX; ++i) {
+        const size_t d = (size_t)j * NX + i, s = (size_t)src * NX + i;
+        if (bc == 3) {
+          const double rho = U[s], mx = U[s + plane], my = U[s + 2 * plane];
+          const double ke = 0.5 * (mx * mx + my * my) / rho;
+          const double pe = (p->gamma - 1.0) * (U[s + 3 * plane] - ke);
+          const double pg = pe + rho * p->grav * ((double)(j - edge) * dy);
+          U[d] = rho;
+          U[d + plane] = mx;
+          U[d + 2 * plane] = my;
+          U[d + 3 * plane] = pg / (p->gamma - 1.0) + ke;
+        } else {
+          for (int k = 0; k < NVAR; ++k) {
+            const double flip = (bc == 2 && k == IMY) ? -1.0 : 1.0;
+            U[d + k * plane] = flip * U[s + k * plane];
+          }
+        }
+      }
     }
   }
   return 0;
@@ -458,8 +494,10 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
       }
 
   /* 4. characteristic tracing to the four half-step face states of each cell (Eq. 13) on cells
-   *    [3, NX-3) x [3, NY-3).  In y the normal velocity is v and the transverse one u. */
+   *    [3, NX-3) x [3, NY-3).  In y the normal velocity is v and the transverse one u.  With gravity
+   *    (the rho g source of §3.2's Euler equations) the half-step states of v gain dt g / 2. */
   const double sigx = dt / dx, sigy = dt / dy;
+  const double hdtg = 0.5 * dt * p->grav;
 #pragma omp parallel for
   for (int j = 3; j < NY - 3; ++j)
     for (int i = 3; i < NX - 3; ++i) {
@@ -467,6 +505,10 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
       double dx4[4] = {AT(dqx, 0, j, i), AT(dqx, 1, j, i), AT(dqx, 2, j, i), AT(dqx, 3, j, i)};
       double ql[4], qr[4];
       oracle_trace(p, sigx, qc, dx4, ql, qr);
+      if (p->grav != 0.0) { /* half-step gravity on v (transverse in x) */
+        ql[2] = ql[2] + hdtg;
+        qr[2] = qr[2] + hdtg;
+      }
       for (int k = 0; k < 4; ++k) {
         AT(qxl, k, j, i) = ql[k];
         AT(qxr, k, j, i) = qr[k];
@@ -474,6 +516,10 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
       double qn[4] = {qc[0], qc[2], qc[1], qc[3]};
       double dy4[4] = {AT(dqy, 0, j, i), AT(dqy, 2, j, i), AT(dqy, 1, j, i), AT(dqy, 3, j, i)};
       oracle_trace(p, sigy, qn, dy4, ql, qr);
+      if (p->grav != 0.0) { /* half-step gravity on v (normal in y) */
+        ql[1] = ql[1] + hdtg;
+        qr[1] = qr[1] + hdtg;
+      }
       /* back to (rho, u, v, p) order */
       double yl[4] = {ql[0], ql[2], ql[1], ql[3]}, yr[4] = {qr[0], qr[2], qr[1], qr[3]};
       for (int k = 0; k < 4; ++k) {
@@ -603,15 +649,22 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
       }
   }
 
-  /* 8. conservative update (Eq. 5) */
+  /* 8. conservative update (Eq. 5); with gravity, the time-centred sources of §3.2's Euler equations:
+   *    (rho v) += dt g (rho^n + rho^{n+1}) / 2, then (rho E) += dt g ((rho v)^n + (rho v)^{n+1}) / 2 */
   {
     const double sx = dt / dx, sy = dt / dy;
 #pragma omp parallel for
     for (int j = ng; j < ng + ny; ++j)
-      for (int i = ng; i < ng + nx; ++i)
+      for (int i = ng; i < ng + nx; ++i) {
+        const double rho_n = AT(U, 0, j, i), my_n = AT(U, 2, j, i);
         for (int k = 0; k < 4; ++k)
           AT(U, k, j, i) = AT(U, k, j, i) + (sx * (AT(fx, k, j, i) - AT(fx, k, j, i + 1)) +
                                              sy * (AT(fy, k, j, i) - AT(fy, k, j + 1, i)));
+        if (p->grav != 0.0) {
+          AT(U, 2, j, i) = AT(U, 2, j, i) + hdtg * (rho_n + AT(U, 0, j, i));
+          AT(U, 3, j, i) = AT(U, 3, j, i) + hdtg * (my_n + AT(U, 2, j, i));
+        }
+      }
   }
   (void)g;
   if (st) {

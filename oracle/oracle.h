@@ -23,13 +23,15 @@ typedef struct {
   int nx, ny, ng;
   double xmin, xmax, ymin, ymax;
   double gamma, cfl;
-  int bc_xlo, bc_xhi, bc_ylo, bc_yhi; /* 0 outflow (zero gradient), 1 periodic */
+  int bc_xlo, bc_xhi, bc_ylo, bc_yhi; /* 0 outflow (zero gradient), 1 periodic, 2 reflecting,
+                                          3 hydrostatic (y sides only) */
   int limiter;                         /* 0 piecewise constant, 1 MC, 2 fourth-order MC */
   int use_flattening;                  /* 0/1 */
   double cvisc;                        /* artificial-viscosity coefficient (0 disables) */
   int riemann_maxiter;
   double riemann_tol;
   double small_dens, small_pres;       /* floors applied to working copies only */
+  double grav;                         /* constant gravitational acceleration along y (0: none) */
 } oracle_params;
 
 typedef struct {

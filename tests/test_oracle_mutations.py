@@ -28,6 +28,16 @@ MUTATIONS = {
     "star density sign": [("double rst = 1.0 / (1.0 / ro - (pst - po) / (wo * wo));",
                            "double rst = 1.0 / (1.0 / ro + (pst - po) / (wo * wo));")],
     "energy flux": [("F[3] = un * (rhoE + pres);", "F[3] = un * (rhoE);")],
+    "gravity energy source not time-centred": [
+        ("AT(U, 3, j, i) = AT(U, 3, j, i) + hdtg * (my_n + AT(U, 2, j, i));",
+         "AT(U, 3, j, i) = AT(U, 3, j, i) + hdtg * (2.0 * my_n);")],
+    "gravity half-step of the y states dropped": [
+        ("        ql[1] = ql[1] + hdtg;\n        qr[1] = qr[1] + hdtg;", "")],
+    "reflecting wall keeps the normal momentum": [
+        ("const double flip = (k == IMX) ? -1.0 : 1.0;", "const double flip = 1.0;")],
+    "hydrostatic ghost pressure sign": [
+        ("const double pg = pe + rho * p->grav * ((double)(j - edge) * dy);",
+         "const double pg = pe - rho * p->grav * ((double)(j - edge) * dy);")],
     "artificial viscosity strength": [
         ("double av = p->cvisc * fmax(-div * dx, 0.0);", "double av = 10 * p->cvisc * fmax(-div * dx, 0.0);"),
         ("double av = p->cvisc * fmax(-div * dy, 0.0);", "double av = 10 * p->cvisc * fmax(-div * dy, 0.0);")],
@@ -51,7 +61,8 @@ def test_pins_catch_the_planted_mistake(name):
             src = src.replace(a, b)
         open(path, "w").write(src)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-                            "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py"],
+                            "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py",
+                            "tests/test_oracle_gravity.py"],
                            cwd=d, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
         assert "FAILED" in r.stdout
