@@ -43,7 +43,18 @@ typedef enum {
   HYDRO_ERANGE = 8       /* a size is beyond a fixed maximum of the call (see the call) */
 } hydro_status;
 
-typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1 } hydro_bc;
+/* Boundary conditions (paper §2 ghost cells; §3.2 Rayleigh-Taylor problem for the hydrostatic wall).
+ * OUTFLOW: zero gradient.  PERIODIC: wrap (both sides of an axis).  REFLECT: mirror image of the interior
+ * with the normal momentum negated.  HYDROSTATIC (y sides only): density and momenta copied from the row
+ * next to the wall, pressure integrated with dp/dy = rho g from that row's cell, energy rebuilt from it.
+ * REFLECT and HYDROSTATIC are filled by hydro_fill_ghost; hydro_step_fused and hydro_advance then run the
+ * fill / dt / step passes instead of one fused launch. */
+typedef enum {
+  HYDRO_BC_OUTFLOW = 0,
+  HYDRO_BC_PERIODIC = 1,
+  HYDRO_BC_REFLECT = 2,
+  HYDRO_BC_HYDROSTATIC = 3
+} hydro_bc;
 
 typedef enum {
   HYDRO_FP64 = 0, /* state and arithmetic in double */
@@ -69,6 +80,8 @@ typedef struct {
   int precision;                    /* hydro_precision */
   int use_learned_guess;            /* 1: start each Riemann iteration from a learned proposal (FP32 only;
                                        see hydro_set_riemann_model), default 0 */
+  double grav;                      /* constant gravitational acceleration along y (paper §3.2 Euler
+                                       equations' rho g and rho U.g sources), default 0 */
 } hydro_params;
 
 typedef struct hydro_ctx hydro_ctx;

@@ -40,12 +40,7 @@ __global__ void __launch_bounds__(256) batch_fill_kernel(const BatchMember* __re
     const int f = e - 2 * band - side;
     j = P.ng + f / P.ng; i = P.ng + P.nx + f % P.ng;
   }
-  const int si = map_index(i, P.ng, P.nx, P.bc[0], P.bc[1]);
-  const int sj = map_index(j, P.ng, P.ny, P.bc[2], P.bc[3]);
-  const size_t plane = (size_t)P.NY * P.pitch;
-  const size_t d = (size_t)j * P.pitch + i, s = (size_t)sj * P.pitch + si;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) U[d + k * plane] = U[s + k * plane];
+  fill_ghost_cell(P, U, i, j, (size_t)P.NY * P.pitch);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -103,7 +98,7 @@ __global__ void __launch_bounds__(256) batch_dt_kernel(const BatchMember* __rest
     const unsigned long long bits = atomicExch(&scr->dt_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
     const double dt = P.cfl * __longlong_as_double((long long)bits);
     scr->dt = dt;
-    scr->sc = make_step_scalars(dt, P.dx, P.dy);
+    scr->sc = make_step_scalars(dt, P.dx, P.dy, P.grav);
     if (advance) {
       scr->t = scr->t + dt;
       scr->nsteps = scr->nsteps + 1;

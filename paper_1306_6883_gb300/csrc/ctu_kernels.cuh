@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
       dt = dt < 0.0 ? 0.0 : dt;
     }
     scr->dt = dt;
-    *sc_next = make_step_scalars(dt, P.dx, P.dy);
+    *sc_next = make_step_scalars(dt, P.dx, P.dy, P.grav);
     scr->step_blocks_done = 0u;
   }
 }

@@ -51,12 +51,12 @@ struct TileCounters {
 // Time-step factors in the kernel's precision.
 template <typename R>
 struct StepFactors {
-  R sigx, sigy, hx, hy;
+  R sigx, sigy, hx, hy, hdtg;
   __device__ __forceinline__ void load(const StepScalars& sc) {
     if constexpr (is_f32<R>()) {
-      sigx = sc.sigx_f; sigy = sc.sigy_f; hx = sc.hx_f; hy = sc.hy_f;
+      sigx = sc.sigx_f; sigy = sc.sigy_f; hx = sc.hx_f; hy = sc.hy_f; hdtg = sc.hdtg_f;
     } else {
-      sigx = sc.sigx; sigy = sc.sigy; hx = sc.hx; hy = sc.hy;
+      sigx = sc.sigx; sigy = sc.sigy; hx = sc.hx; hy = sc.hy; hdtg = sc.hdtg;
     }
   }
 };
@@ -286,6 +286,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       }
       R ql[4], qrr[4];
       trace<R>(s, YD ? sigy : sigx, q, dq, ql, qrr);
+      if (P.use_grav) {  // half-step gravity (the rho g source, §3.2) on v: normal in y, transverse in x
+        constexpr int mg = YD ? 1 : 2;
+        ql[mg] = ql[mg] + f.hdtg;
+        qrr[mg] = qrr[mg] + f.hdtg;
+      }
       R* dl = YD ? syl : sxl;
       R* dr = YD ? syr : sxr;
 #pragma unroll
@@ -467,18 +472,29 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     const size_t o = (size_t)gj * P.pitch + gi;
     const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
     const int cy = ty * SX + tx + 1;    // final y flux of face ty (below the cell) lives in syl[cy]
-    R Un[4];
+    R Un[4], rho_n, my_n;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const R* fx = sxl + k * nC;
       const R* fy = syl + k * nC;
       const R d = ux * (fx[cx] - fx[cx + 1]) + uy * (fy[cy] - fy[cy + SX]);
+      R u0;
       if constexpr (L::SMEM_U)
-        Un[k] = sU[k * nC + cy + SX] + d;  // the cell's own U^n, s index (ty + 1) * SX + tx + 1
+        u0 = sU[k * nC + cy + SX];  // the cell's own U^n, s index (ty + 1) * SX + tx + 1
       else
-        Un[k] = __ldg(Uin + o + k * plane) + d;
-      Uout[o + k * plane] = Un[k];
+        u0 = __ldg(Uin + o + k * plane);
+      if (k == 0) rho_n = u0;
+      if (k == 2) my_n = u0;
+      Un[k] = u0 + d;
     }
+    if (P.use_grav) {
+      // time-centred gravity sources (§3.2): rho v gains dt g (rho^n + rho^{n+1}) / 2, then rho E gains
+      // dt g ((rho v)^n + (rho v)^{n+1}) / 2 with the updated momentum
+      Un[2] = Un[2] + f.hdtg * (rho_n + Un[0]);
+      Un[3] = Un[3] + f.hdtg * (my_n + Un[2]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Uout[o + k * plane] = Un[k];
     if constexpr (FUSED) {
       // the CFL constraint of the new state (Eq. 6), for the next step's time step
       cfl_value(s, Un[0], Un[1], Un[2], Un[3], *cfl_min, flags);

@@ -107,7 +107,15 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
   if (!(p->cfl > 0.0)) BAD("cfl must be > 0");
   const int bcs[4] = {p->bc_xlo, p->bc_xhi, p->bc_ylo, p->bc_yhi};
   for (int k = 0; k < 4; ++k)
-    if (bcs[k] != HYDRO_BC_OUTFLOW && bcs[k] != HYDRO_BC_PERIODIC) BAD("unknown boundary condition");
+    if (bcs[k] < HYDRO_BC_OUTFLOW || bcs[k] > HYDRO_BC_HYDROSTATIC) BAD("unknown boundary condition");
+  if (p->bc_xlo == HYDRO_BC_HYDROSTATIC || p->bc_xhi == HYDRO_BC_HYDROSTATIC)
+    BAD("hydrostatic boundaries are for the y sides (gravity acts along y)");
+  // a mirrored ghost cell's source must be an interior cell
+  if ((p->bc_xlo == HYDRO_BC_REFLECT || p->bc_xhi == HYDRO_BC_REFLECT) && p->nx < p->ng)
+    BAD("reflecting x walls need nx >= ng");
+  if ((p->bc_ylo == HYDRO_BC_REFLECT || p->bc_yhi == HYDRO_BC_REFLECT) && p->ny < p->ng)
+    BAD("reflecting y walls need ny >= ng");
+  if (!(p->grav > -1e30 && p->grav < 1e30)) BAD("grav must be finite");
   if ((p->bc_xlo == HYDRO_BC_PERIODIC) != (p->bc_xhi == HYDRO_BC_PERIODIC) ||
       (p->bc_ylo == HYDRO_BC_PERIODIC) != (p->bc_yhi == HYDRO_BC_PERIODIC))
     BAD("periodic boundaries must be paired");
@@ -170,6 +178,9 @@ void fill_kparams(const hydro_params* p, KParams* kp) {
   k.riemann_tol = p->riemann_tol;
   k.small_dens = p->small_dens;
   k.small_pres = p->small_pres;
+  k.grav = p->grav;
+  k.grav_f = (float)p->grav;
+  k.use_grav = p->grav != 0.0;
   k.gamma_f = (float)k.gamma;
   k.gm1_f = (float)k.gm1;
   k.igm1_f = (float)(1.0 / k.gm1);
@@ -210,6 +221,7 @@ hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision
   p->small_pres = 1e-20;
   p->precision = precision;
   p->use_learned_guess = 0;
+  p->grav = 0.0;
   return HYDRO_OK;
 }
 
@@ -332,7 +344,7 @@ static hydro_status check_model(hydro_ctx* c) {
 hydro_status hydro_step(hydro_ctx* c, double dt) {
   if (!c || !(dt > 0.0) || !(dt < 1e300)) return HYDRO_EINVAL;
   if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
-  cudaError_t e = launch_step(c, hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy), nullptr);
+  cudaError_t e = launch_step(c, hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy, c->kp.grav), nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "ctu_step");
   c->cur = 1 - c->cur;
   c->fused_valid = 0;
@@ -341,7 +353,11 @@ hydro_status hydro_step(hydro_ctx* c, double dt) {
 
 hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
   if (!c) return HYDRO_EINVAL;
-  if (c->p.use_learned_guess == 1 || c->harvest) {  // the optional face variants use the separate passes
+  // the optional face variants, and reflecting or hydrostatic sides (whose ghost cells are not plain copies
+  // of interior cells), use the separate passes: ghost fill, dt, step
+  const bool plain_bc = c->p.bc_xlo <= HYDRO_BC_PERIODIC && c->p.bc_xhi <= HYDRO_BC_PERIODIC &&
+                        c->p.bc_ylo <= HYDRO_BC_PERIODIC && c->p.bc_yhi <= HYDRO_BC_PERIODIC;
+  if (c->p.use_learned_guess == 1 || c->harvest || !plain_bc) {
     if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);

@@ -19,7 +19,7 @@ namespace hydro {
 struct KParams {
   int nx, ny, ng, pitch;  // interior size, ghost width, row pitch (elements)
   int NX, NY;             // padded extents nx + 2 ng, ny + 2 ng
-  int bc[4];              // xlo, xhi, ylo, yhi: 0 outflow, 1 periodic
+  int bc[4];              // xlo, xhi, ylo, yhi: 0 outflow, 1 periodic, 2 reflect, 3 hydrostatic
   double dx, dy;
   double gamma, gm1, g1;  // gamma, gamma - 1, (gamma + 1)/(2 gamma)
   double cfl;
@@ -34,26 +34,32 @@ struct KParams {
   // copy (the tile's mbarrier then waits for bytes that never come); tma_polls != 0 replaces the poll budget
   int tma_test_drop;
   unsigned int tma_polls;
+  double grav;  // gravitational acceleration along y
+  float grav_f;
+  int use_grav;  // grav != 0: the step applies the gravity terms
 };
 
 // Time-step dependent factors of one CTU step, computed once in double (host, or the last block of
 // the dt reduction) so the kernels do no double division: sig = dt/dx, h = dt/(2dx), as in Eqs. 3-5.
 struct StepScalars {
   double dt, sigx, sigy, hx, hy;
-  float sigx_f, sigy_f, hx_f, hy_f;
+  double hdtg;  // dt g / 2: half-step gravity of the traced v, and the factor of the time-centred sources
+  float sigx_f, sigy_f, hx_f, hy_f, hdtg_f;
 };
 
-__host__ __device__ inline StepScalars make_step_scalars(double dt, double dx, double dy) {
+__host__ __device__ inline StepScalars make_step_scalars(double dt, double dx, double dy, double grav) {
   StepScalars s;
   s.dt = dt;
   s.sigx = dt / dx;
   s.sigy = dt / dy;
   s.hx = 0.5 * dt / dx;
   s.hy = 0.5 * dt / dy;
+  s.hdtg = 0.5 * dt * grav;
   s.sigx_f = (float)s.sigx;
   s.sigy_f = (float)s.sigy;
   s.hx_f = (float)s.hx;
   s.hy_f = (float)s.hy;
+  s.hdtg_f = (float)s.hdtg;
   return s;
 }
 
@@ -156,12 +162,47 @@ __device__ __forceinline__ bool finite4(R a, R b, R c, R d) {
   return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
 }
 
-// Ghost-cell source index along one axis (paper §2, CellCenterData2d ghost filling; Fig. 1): outflow clamps
-// to the nearest interior index (zero gradient), periodic wraps.
+// Ghost-cell source index along one axis (paper §2, CellCenterData2d ghost filling; Fig. 1): outflow and
+// hydrostatic clamp to the nearest interior index, periodic wraps, reflect mirrors about the wall.
 __device__ __forceinline__ int map_index(int i, int ng, int n, int lo_bc, int hi_bc) {
-  if (i < ng) return lo_bc == 1 ? i + n : ng;
-  if (i >= ng + n) return hi_bc == 1 ? i - n : ng + n - 1;
+  if (i < ng) return lo_bc == 1 ? i + n : lo_bc == 2 ? 2 * ng - 1 - i : ng;
+  if (i >= ng + n) return hi_bc == 1 ? i - n : hi_bc == 2 ? 2 * (ng + n) - 1 - i : ng + n - 1;
   return i;
+}
+
+// Boundary condition that fills padded index i along one axis (-1 inside the domain).
+__device__ __forceinline__ int ghost_bc(int i, int ng, int n, int lo_bc, int hi_bc) {
+  return i < ng ? lo_bc : i >= ng + n ? hi_bc : -1;
+}
+
+// One ghost cell (i, j) of the padded state.  Its source is the interior cell (map_x(i), map_y(j)); a
+// reflecting side negates the momentum normal to it (mx across x walls, my across y walls).  A hydrostatic
+// y side keeps the edge row's density and momenta and integrates its pressure with dp/dy = rho g at constant
+// rho: p = p_edge + rho g (y - y_edge), E = p/(gamma - 1) + kinetic.  Every source is an interior cell, so
+// one pass fills edges and corners; a corner combines its x side's mapping with its y side's, as filling the
+// x sides of the interior rows and then the y bands over the full width does.  The hydrostatic energy is
+// computed in double with rounded operations only, in the order of the formula, for every state precision.
+template <typename R>
+__device__ __forceinline__ void fill_ghost_cell(const KParams& P, R* __restrict__ U, int i, int j, size_t plane) {
+  const int si = map_index(i, P.ng, P.nx, P.bc[0], P.bc[1]);
+  const int sj = map_index(j, P.ng, P.ny, P.bc[2], P.bc[3]);
+  const size_t d = (size_t)j * P.pitch + i, s = (size_t)sj * P.pitch + si;
+  R v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = U[s + k * plane];
+  if (ghost_bc(i, P.ng, P.nx, P.bc[0], P.bc[1]) == 2) v[1] = -v[1];
+  const int ybc = ghost_bc(j, P.ng, P.ny, P.bc[2], P.bc[3]);
+  if (ybc == 2) {
+    v[2] = -v[2];
+  } else if (ybc == 3) {
+    const double rho = (double)v[0], mx = (double)v[1], my = (double)v[2];
+    const double ke = __ddiv_rn(__dmul_rn(0.5, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))), rho);
+    const double pe = __dmul_rn(P.gm1, __dsub_rn((double)v[3], ke));
+    const double pg = __dadd_rn(pe, __dmul_rn(__dmul_rn(rho, P.grav), __dmul_rn((double)(j - sj), P.dy)));
+    v[3] = (R)__dadd_rn(__ddiv_rn(pg, P.gm1), ke);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) U[d + k * plane] = v[k];
 }
 
 // ---------------------------------------------------------------------------------------------------

@@ -8,7 +8,7 @@ namespace hydro {
 
 // ---------------------------------------------------------------------------------------------------
 // Ghost cells (paper §2, CellCenterData2d ghost filling; Fig. 1): ghost (i, j) takes interior cell
-// (map_x(i), map_y(j)); outflow clamps to the nearest interior index (zero gradient), periodic wraps.
+// (map_x(i), map_y(j)) through fill_ghost_cell (outflow, periodic, reflecting and hydrostatic sides).
 // All sources are interior cells, so one pass over the ghost frame fills edges and corners.
 template <typename R>
 __global__ void fill_ghost_kernel(KParams P, R* __restrict__ U) {
@@ -31,11 +31,7 @@ __global__ void fill_ghost_kernel(KParams P, R* __restrict__ U) {
       const int f = e - 2 * band - side;
       j = P.ng + f / P.ng; i = P.ng + P.nx + f % P.ng;
     }
-    const int si = map_index(i, P.ng, P.nx, P.bc[0], P.bc[1]);
-    const int sj = map_index(j, P.ng, P.ny, P.bc[2], P.bc[3]);
-    const size_t d = (size_t)j * P.pitch + i, s = (size_t)sj * P.pitch + si;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) U[d + k * plane] = U[s + k * plane];
+    fill_ghost_cell(P, U, i, j, plane);
   }
 }
 
@@ -116,7 +112,7 @@ __global__ void __launch_bounds__(DT_THREADS) cfl_dt_kernel(KParams P, const R* 
       dt = dt < 0.0 ? 0.0 : dt;
     }
     scr->dt = dt;
-    scr->sc = make_step_scalars(dt, P.dx, P.dy);
+    scr->sc = make_step_scalars(dt, P.dx, P.dy, P.grav);
     if (sc_out) *sc_out = scr->sc;
     if (advance) {
       scr->t = scr->t + dt;

@@ -15,7 +15,7 @@ STATUS_NAMES = ["HYDRO_OK", "HYDRO_EINVAL", "HYDRO_ENOMEM", "HYDRO_ECUDA", "HYDR
                 "HYDRO_ENONCONV", "HYDRO_ETIMEOUT", "HYDRO_ERANGE"]
 NOALLOC_MAX_ROWS = 16384
 HYDRO_FP64, HYDRO_FP32 = 0, 1
-BC = {"outflow": 0, "periodic": 1}
+BC = {"outflow": 0, "periodic": 1, "reflect": 2, "hydrostatic": 3}
 
 
 class HydroParams(ctypes.Structure):
@@ -28,6 +28,7 @@ class HydroParams(ctypes.Structure):
         ("riemann_maxiter", ctypes.c_int), ("riemann_tol", ctypes.c_double),
         ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double),
         ("precision", ctypes.c_int), ("use_learned_guess", ctypes.c_int),
+        ("grav", ctypes.c_double),
     ]
 
 

@@ -106,7 +106,8 @@ def params_for(problem, precision=H.HYDRO_FP64, **kw):
     """C-ABI parameters for a hydro_problems.Problem."""
     xmin, xmax, ymin, ymax = problem.domain
     return H.default_params(problem.nx, problem.ny, precision, bc=problem.bc, gamma=problem.gamma, cfl=problem.cfl,
-                            xmin=xmin, xmax=xmax, ymin=ymin, ymax=ymax, ng=problem.ng, **kw)
+                            xmin=xmin, xmax=xmax, ymin=ymin, ymax=ymax, ng=problem.ng,
+                            grav=getattr(problem, "grav", 0.0), **kw)
 
 
 class Ensemble:

@@ -45,7 +45,9 @@ def test_defaults_and_layout(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("ng", 3), ("gamma", 1.0), ("cfl", 0.0),
                                          ("limiter", 3), ("riemann_maxiter", 0), ("small_pres", 0.0),
-                                         ("precision", 2), ("bc_xlo", 1), ("use_learned_guess", 1)])
+                                         ("precision", 2), ("bc_xlo", 1), ("use_learned_guess", 1),
+                                         ("bc_xlo", 3), ("bc_xhi", 3), ("bc_yhi", 4), ("bc_ylo", -1),
+                                         ("grav", float("nan")), ("grav", float("inf"))])
 def test_invalid_parameters_are_rejected_before_any_allocation(lib, field, value):
     from paper_1306_6883_gb300 import hydro as H
     p = H.default_params(16, 16)
@@ -54,6 +56,16 @@ def test_invalid_parameters_are_rejected_before_any_allocation(lib, field, value
     ctx = ctypes.c_void_p()
     st = lib.hydro_init(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(512), None, ctypes.byref(ctx))
     assert st == H.HYDRO_EINVAL and not ctx.value
+
+
+@pytest.mark.parametrize("bc", [("reflect",) * 4, ("periodic", "periodic", "hydrostatic", "hydrostatic"),
+                                ("reflect", "outflow", "hydrostatic", "reflect")])
+def test_reflecting_and_hydrostatic_sides_are_accepted(lib, bc):
+    from paper_1306_6883_gb300 import hydro as H
+    p = H.default_params(16, 16, bc=bc, grav=-1.0)
+    assert H.state_pitch(p) > 0
+    p = H.default_params(3, 3, bc=bc)  # a mirrored ghost cell's source must lie inside the domain
+    assert H.state_pitch(p) == 0
 
 
 def test_null_and_misaligned_buffers_are_rejected(lib):

@@ -39,7 +39,7 @@ def _mods():
 def _oparams(pr, **kw):
     xmin, xmax, ymin, ymax = pr.domain
     return oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl, xmin=xmin, xmax=xmax, ymin=ymin,
-                         ymax=ymax, **kw)
+                         ymax=ymax, grav=pr.grav, **kw)
 
 
 def _field_err(got, ref):
