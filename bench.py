@@ -1,7 +1,7 @@
 """Throughput of the unsplit CTU step on a GB300 (zone-updates per second).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload kh1024|sedov4096|sedov8192] [--precision fp32|fp64]
+                    [--workload kh1024|sedov4096|sedov8192|rt1024] [--precision fp32|fp64]
 
 A step is one pass of the solver's driver loop (paper §2): ghost fill, CFL time step reduced on the
 device, one fused CTU step.  Default workload: the 1024 x 1024 periodic Kelvin-Helmholtz shear layer
@@ -79,6 +79,8 @@ def workload(name):
         return hp.sedov(4096, 4096), "sedov_4096x4096_outflow"
     if name == "sedov8192":
         return hp.sedov(8192, 8192, density_noise=0.01), "sedov_8192x8192_outflow_1pct_noise"
+    if name == "rt1024":
+        return hp.rt(1024, 3072), "rayleigh_taylor_1024x3072_gravity_hydrostatic"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -162,8 +164,9 @@ def max_over_ranks(x, world):
 
 # ---------------------------------------------------------------------------------------------------- our arm
 def time_device_path(pr, precision, steps, warmup, flush):
-    """Value: steps of the driver loop (ghost cells, CFL dt, CTU step) with the state resident in HBM, each
-    step one launch of the fused step kernel (hydro_step_fused)."""
+    """Value: steps of the driver loop (ghost cells, CFL dt, CTU step) with the state resident in HBM through
+    hydro_step_fused: one launch of the fused step kernel, or for reflecting / hydrostatic sides the three
+    launches fill, dt, step."""
     import torch
 
     from paper_1306_6883_gb300 import hydro as H
@@ -190,8 +193,9 @@ def time_device_path(pr, precision, steps, warmup, flush):
     s.close()
     solves = stats1[0] - stats0[0]
     iters = stats1[1] - stats0[1]
+    plain = all(b in ("outflow", "periodic") for b in pr.bc)
     return {"step_ms": step_ms, "kernel_ms": step_ms, "iters_per_solve": iters / max(solves, 1),
-            "t_sim": t_sim, "totals": tot, "launches_per_step": 1}
+            "t_sim": t_sim, "totals": tot, "launches_per_step": 1 if plain else 3}
 
 
 def time_e2e(pr, precision, steps, warmup):
@@ -455,6 +459,13 @@ def run_ours(args, world, rank, local):
     e2e = time_e2e(pr, args.precision, max(args.steps // 4, 10), args.warmup)
     accuracy = fp32_error(pr) if args.precision == "fp32" else None
     ens = time_ensemble() if args.precision == "fp32" else None
+    rt = None
+    if args.precision == "fp32":
+        prt, rtname = workload("rt1024")
+        r = time_device_path(prt, "fp32", 20, args.warmup, flush)
+        rt = {"workload": rtname, "steps": 20, "value": prt.nx * prt.ny * 20 / (sum(r["step_ms"]) / 1e3),
+              "ms_per_step": sum(r["step_ms"]) / 20, "launches_per_step": r["launches_per_step"],
+              "riemann_iters_per_solve": r["iters_per_solve"]}
     learned = None
     if args.precision == "fp32":
         model, training = harvest_and_train()
@@ -513,6 +524,7 @@ def run_ours(args, world, rank, local):
         "riemann_iters_per_solve": main["iters_per_solve"],
         "fp32_error": accuracy,
         "ensemble": ens,
+        "rayleigh_taylor": rt,
         "learned_proposal": learned,
     }
     line["roofline"]["hbm_frac_of_measured"] = line["roofline"]["hbm_gbs"] / hbm

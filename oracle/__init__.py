@@ -47,6 +47,7 @@ def lib():
         L.oracle_fill_ghost.argtypes = [P, _D]
         L.oracle_cfl_dt.argtypes = [P, _D, _D]
         L.oracle_step.argtypes = [P, _D, ctypes.c_double, ctypes.POINTER(OracleStats)]
+        L.oracle_step_split.argtypes = [P, _D, ctypes.c_double, ctypes.c_int, ctypes.POINTER(OracleStats)]
         L.oracle_conserved_totals.argtypes = [P, _D, _D]
         L.oracle_cons_to_prim.argtypes = [P, _D, _D]
         L.oracle_prim_to_cons.argtypes = [P, _D, _D]
@@ -96,6 +97,15 @@ def step(p, U, dt, stats=None):
     """One CTU step of length dt, in place on the interior of the ghost-filled state U."""
     st = stats if stats is not None else OracleStats()
     _check(lib().oracle_step(ctypes.byref(p), _ptr(U), float(dt), ctypes.byref(st)), "oracle_step")
+    return U
+
+
+def step_split(p, U, dt, first_dir, stats=None):
+    """One dimensionally split step (§3.1): sweep along first_dir (0 x, 1 y), ghost fill, sweep along the
+    other direction, in place on the ghost-filled state U."""
+    st = stats if stats is not None else OracleStats()
+    _check(lib().oracle_step_split(ctypes.byref(p), _ptr(U), float(dt), int(first_dir), ctypes.byref(st)),
+           "oracle_step_split")
     return U
 
 
@@ -158,8 +168,9 @@ def num_threads():
     return lib().oracle_num_threads()
 
 
-def advance(p, U, nsteps=None, tmax=None, stats=None):
-    """The paper's driver loop (§2): fill ghosts, get dt (clamped to reach tmax), step; returns (t, n)."""
+def advance(p, U, nsteps=None, tmax=None, stats=None, split=False):
+    """The paper's driver loop (§2): fill ghosts, get dt (clamped to reach tmax), step; returns (t, n).
+    split: dimensionally split steps, x first on even steps and y first on odd ones."""
     t, n = 0.0, 0
     while True:
         if nsteps is not None and n >= nsteps:
@@ -170,7 +181,10 @@ def advance(p, U, nsteps=None, tmax=None, stats=None):
         dt = cfl_dt(p, U)
         if tmax is not None and t + dt > tmax:
             dt = tmax - t
-        step(p, U, dt, stats)
+        if split:
+            step_split(p, U, dt, n % 2, stats)
+        else:
+            step(p, U, dt, stats)
         t += dt
         n += 1
     fill_ghost(p, U)

@@ -679,3 +679,136 @@ done:
   free(fxh); free(fyh); free(fx); free(fy);
   return err;
 }
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Dimensionally split variant (§3.1: the fluxes of a directional update are built without knowledge of
+ * the transverse flow, each directional update acts on the state left by the previous one, and the order
+ * of the directions alternates from step to step for second-order accuracy).  One sweep along dir
+ * (0: x, 1: y) applies the one-dimensional piecewise-linear Godunov method of §3.2 to every interior line:
+ *   1. primitives of the line's cells, in the face frame (rho, u_normal, u_transverse, p);
+ *   2. flattening along the line only: xi_m = min(chi_m, chi_{m-s}), s = sign(p_{m+1} - p_{m-1});
+ *   3. limited slopes along the line, times xi;
+ *   4. characteristic tracing (Eq. 13) to the two half-step face states of each cell, sigma = dt / h;
+ *   5. Riemann solves at the interior faces of the line;
+ *   6. artificial viscosity with the divergence along the line, (u_m - u_{m-1}) / h;
+ *   7. conservative update of the line's interior cells, U += sigma (F_{m-1/2} - F_{m+1/2}).
+ * The state must be ghost-filled on entry.  Lines are independent; each keeps its own work arrays. */
+static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_stats* st) {
+  const int ng = p->ng, nx = p->nx, ny = p->ny, NX = nx + 2 * ng, NY = ny + 2 * ng;
+  const size_t plane = (size_t)NX * NY;
+  const double h = dir == 0 ? (p->xmax - p->xmin) / nx : (p->ymax - p->ymin) / ny;
+  const int n = dir == 0 ? nx : ny;         /* interior cells along a line */
+  const int N = n + 2 * ng;                 /* cells along a line, ghosts included */
+  const int nlines = dir == 0 ? ny : nx;    /* interior lines */
+  const size_t sa = dir == 0 ? 1 : (size_t)NX;  /* stride along the line */
+  const size_t sl = dir == 0 ? (size_t)NX : 1;  /* stride between lines */
+  const int kn = dir == 0 ? 1 : 2, kt = dir == 0 ? 2 : 1;  /* normal and transverse momentum components */
+  const double sigma = dt / h;
+  long long n_solves = 0, n_iters = 0, n_nonconv = 0;
+  int max_iters = 0, err = 0;
+
+#pragma omp parallel for reduction(+ : n_solves, n_iters, n_nonconv) reduction(max : max_iters) reduction(| : err)
+  for (int l = 0; l < nlines; ++l) {
+    const size_t base = (size_t)(ng + l) * sl;  /* cell m of the line is base + m * sa */
+    double* w = calloc((size_t)N * 19 + 4 * ((size_t)N + 1), sizeof(double));
+    if (!w) {
+      err |= 2;
+      continue;
+    }
+    double* q = w;                /* [4][N] primitives, face frame */
+    double* chi = q + 4 * N;      /* [N] */
+    double* xi = chi + N;         /* [N] */
+    double* dq = xi + N;          /* [4][N] limited slopes */
+    double* ql = dq + 4 * N;      /* [4][N] left state at m+1/2 of cell m */
+    double* qr = ql + 4 * N;      /* [4][N] right state at m-1/2 of cell m */
+    double* G = qr + 4 * N;       /* [4][N+1] flux at face f (between cells f-1 and f), conserved order */
+#define C(k, m) U[(size_t)(k) * plane + base + (size_t)(m) * sa]
+    /* 1. primitives */
+    for (int m = 0; m < N; ++m) {
+      double Uc[4] = {C(0, m), C(1, m), C(2, m), C(3, m)}, qc[4];
+      oracle_cons_to_prim(p, Uc, qc);
+      q[0 * N + m] = qc[0];
+      q[1 * N + m] = qc[kn];
+      q[2 * N + m] = qc[kt];
+      q[3 * N + m] = qc[3];
+    }
+    /* 2. flattening along the line */
+    for (int m = 0; m < N; ++m) {
+      chi[m] = 1.0;
+      xi[m] = 1.0;
+    }
+    if (p->use_flattening) {
+      for (int m = 2; m < N - 2; ++m)
+        chi[m] = oracle_flatten_chi(q[3 * N + m - 2], q[3 * N + m - 1], q[3 * N + m + 1], q[3 * N + m + 2],
+                                    q[1 * N + m - 1], q[1 * N + m + 1], p->small_pres);
+      for (int m = 3; m < N - 3; ++m) {
+        int s = (q[3 * N + m + 1] - q[3 * N + m - 1]) >= 0.0 ? 1 : -1;
+        xi[m] = fmin(chi[m], chi[m - s]);
+      }
+    }
+    /* 3. slopes */
+    for (int k = 0; k < 4; ++k)
+      for (int m = 2; m < N - 2; ++m)
+        dq[k * N + m] = xi[m] * oracle_slope(p->limiter, q[k * N + m - 2], q[k * N + m - 1], q[k * N + m],
+                                             q[k * N + m + 1], q[k * N + m + 2]);
+    /* 4. tracing */
+    for (int m = 3; m < N - 3; ++m) {
+      double qc[4], d4[4], a[4], b[4];
+      for (int k = 0; k < 4; ++k) {
+        qc[k] = q[k * N + m];
+        d4[k] = dq[k * N + m];
+      }
+      oracle_trace(p, sigma, qc, d4, a, b);
+      for (int k = 0; k < 4; ++k) {
+        ql[k * N + m] = a[k];
+        qr[k * N + m] = b[k];
+      }
+    }
+    /* 5.-6. Riemann solves and artificial viscosity at the faces f in [ng, ng + n] */
+    for (int f = ng; f <= ng + n; ++f) {
+      double a[4], b[4], F[4];
+      for (int k = 0; k < 4; ++k) {
+        a[k] = ql[k * N + f - 1];
+        b[k] = qr[k * N + f];
+      }
+      int it;
+      int ok = oracle_riemann(p, a, b, 0.0, NULL, F, NULL, NULL, &it);
+      n_solves++;
+      n_iters += it;
+      if (!ok) n_nonconv++;
+      if (it > max_iters) max_iters = it;
+      double Gf[4];
+      Gf[0] = F[0];
+      Gf[kn] = F[1];
+      Gf[kt] = F[2];
+      Gf[3] = F[3];
+      if (p->cvisc > 0.0) {
+        double div = (q[1 * N + f] - q[1 * N + f - 1]) / h;
+        double av = p->cvisc * fmax(-div * h, 0.0);
+        for (int k = 0; k < 4; ++k) Gf[k] += av * (C(k, f - 1) - C(k, f));
+      }
+      for (int k = 0; k < 4; ++k) G[k * (N + 1) + f] = Gf[k];
+    }
+    /* 7. update */
+    for (int m = ng; m < ng + n; ++m)
+      for (int k = 0; k < 4; ++k) C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m] - G[k * (N + 1) + m + 1]);
+#undef C
+    free(w);
+  }
+  if (st) {
+    st->riemann_solves += n_solves;
+    st->riemann_iters += n_iters;
+    st->riemann_nonconv += n_nonconv;
+    if (max_iters > st->riemann_maxiters_seen) st->riemann_maxiters_seen = max_iters;
+  }
+  return err;
+}
+
+int oracle_step_split(const oracle_params* p, double* U, double dt, int first_dir, oracle_stats* st) {
+  if (!params_ok(p) || !U || !(dt >= 0.0) || (first_dir != 0 && first_dir != 1)) return 1;
+  if (p->grav != 0.0) return 1; /* the split variant is defined here without source terms */
+  int err = sweep(p, U, dt, first_dir, st);
+  if (!err) err = oracle_fill_ghost(p, U);
+  if (!err) err = sweep(p, U, dt, 1 - first_dir, st);
+  return err;
+}

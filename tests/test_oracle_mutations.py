@@ -41,6 +41,18 @@ MUTATIONS = {
     "artificial viscosity strength": [
         ("double av = p->cvisc * fmax(-div * dx, 0.0);", "double av = 10 * p->cvisc * fmax(-div * dx, 0.0);"),
         ("double av = p->cvisc * fmax(-div * dy, 0.0);", "double av = 10 * p->cvisc * fmax(-div * dy, 0.0);")],
+    "split: viscosity from the transverse velocity": [
+        ("double div = (q[1 * N + f] - q[1 * N + f - 1]) / h;", "double div = (q[2 * N + f] - q[2 * N + f - 1]) / h;")],
+    "split: y sweep keeps the x components": [
+        ("const int kn = dir == 0 ? 1 : 2, kt = dir == 0 ? 2 : 1;", "const int kn = 1, kt = 2;")],
+    "split: both sweeps use the x spacing": [
+        ("const double h = dir == 0 ? (p->xmax - p->xmin) / nx : (p->ymax - p->ymin) / ny;",
+         "const double h = (p->xmax - p->xmin) / nx;")],
+    "split: no ghost fill between the sweeps": [
+        ("  if (!err) err = oracle_fill_ghost(p, U);\n  if (!err) err = sweep", "  if (!err) err = sweep")],
+    "split: flux difference reversed": [
+        ("C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m] - G[k * (N + 1) + m + 1]);",
+         "C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m + 1] - G[k * (N + 1) + m]);")],
 }
 
 
@@ -62,7 +74,7 @@ def test_pins_catch_the_planted_mistake(name):
         open(path, "w").write(src)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
                             "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py",
-                            "tests/test_oracle_gravity.py"],
+                            "tests/test_oracle_gravity.py", "tests/test_oracle_split.py"],
                            cwd=d, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
         assert "FAILED" in r.stdout
