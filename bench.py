@@ -163,7 +163,7 @@ def max_over_ranks(x, world):
 
 
 # ---------------------------------------------------------------------------------------------------- our arm
-def time_device_path(pr, precision, steps, warmup, flush):
+def time_device_path(pr, precision, steps, warmup, flush, **kw):
     """Value: steps of the driver loop (ghost cells, CFL dt, CTU step) with the state resident in HBM through
     hydro_step_fused: one launch of the fused step kernel, or for reflecting / hydrostatic sides the three
     launches fill, dt, step."""
@@ -173,7 +173,7 @@ def time_device_path(pr, precision, steps, warmup, flush):
     from paper_1306_6883_gb300.solver import Solver, params_for
 
     prec = H.HYDRO_FP32 if precision == "fp32" else H.HYDRO_FP64
-    s = Solver(params_for(pr, prec), pr.U)
+    s = Solver(params_for(pr, prec, **kw), pr.U)
     stream = s.stream
     for _ in range(warmup):
         s.step_fused()
@@ -194,8 +194,9 @@ def time_device_path(pr, precision, steps, warmup, flush):
     solves = stats1[0] - stats0[0]
     iters = stats1[1] - stats0[1]
     plain = all(b in ("outflow", "periodic") for b in pr.bc)
+    launches = 5 if kw.get("split") else (1 if plain else 3)  # split: fill, dt, sweep, fill, sweep
     return {"step_ms": step_ms, "kernel_ms": step_ms, "iters_per_solve": iters / max(solves, 1),
-            "t_sim": t_sim, "totals": tot, "launches_per_step": 1 if plain else 3}
+            "t_sim": t_sim, "totals": tot, "launches_per_step": launches}
 
 
 def time_e2e(pr, precision, steps, warmup):
@@ -459,8 +460,13 @@ def run_ours(args, world, rank, local):
     e2e = time_e2e(pr, args.precision, max(args.steps // 4, 10), args.warmup)
     accuracy = fp32_error(pr) if args.precision == "fp32" else None
     ens = time_ensemble() if args.precision == "fp32" else None
-    rt = None
+    rt = split = None
     if args.precision == "fp32":
+        r = time_device_path(pr, "fp32", 20, args.warmup, flush, split=1)
+        split = {"workload": wname, "steps": 20, "value": zones * 20 / (sum(r["step_ms"]) / 1e3),
+                 "ms_per_step": sum(r["step_ms"]) / 20, "launches_per_step": r["launches_per_step"],
+                 "riemann_iters_per_solve": r["iters_per_solve"],
+                 "step": "dimensionally split: ghost fill, CFL dt, x (or y) sweep, ghost fill, y (or x) sweep"}
         prt, rtname = workload("rt1024")
         r = time_device_path(prt, "fp32", 20, args.warmup, flush)
         rt = {"workload": rtname, "steps": 20, "value": prt.nx * prt.ny * 20 / (sum(r["step_ms"]) / 1e3),
@@ -525,6 +531,7 @@ def run_ours(args, world, rank, local):
         "fp32_error": accuracy,
         "ensemble": ens,
         "rayleigh_taylor": rt,
+        "split_variant": split,
         "learned_proposal": learned,
     }
     line["roofline"]["hbm_frac_of_measured"] = line["roofline"]["hbm_gbs"] / hbm

@@ -82,6 +82,11 @@ typedef struct {
                                        see hydro_set_riemann_model), default 0 */
   double grav;                      /* constant gravitational acceleration along y (paper §3.2 Euler
                                        equations' rho g and rho U.g sources), default 0 */
+  int split;                        /* 0: unsplit CTU step (default).  1: dimensionally split step (paper
+                                       §3.1: a one-dimensional sweep along x and one along y, each acting on
+                                       the state the other left; the context's k-th step, counted from
+                                       hydro_init, sweeps x first when k is even).  Needs grav = 0 and
+                                       use_learned_guess = 0; single problems only (not hydro_batch_*). */
 } hydro_params;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -126,7 +131,9 @@ hydro_status hydro_cfl_dt(hydro_ctx* ctx, double* dt_out);
  * traced states, transverse flux-difference correction, final Riemann solves + artificial viscosity,
  * conservative update.  Writes the other buffer and swaps.  Asynchronous: problems found on the device
  * (non-finite or non-positive results, unconverged Riemann solves) are recorded in the context's status
- * word and reported by hydro_sync_status(). */
+ * word and reported by hydro_sync_status().  With split = 1 the step is the dimensionally split one (§3.1):
+ * a one-dimensional sweep into the other buffer, a ghost fill of it, and the other sweep back into the
+ * current buffer (three launches). */
 hydro_status hydro_step(hydro_ctx* ctx, double dt);
 
 /* CFL time step kept on the device: reduce the dt of hydro_cfl_dt into the context's device memory,
@@ -151,8 +158,8 @@ hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
  * and reduces the CFL time step of the state it writes (so no dt pass); its last block advances the
  * device time by this step's dt and keeps the next step's dt (clamped to reach tmax when tmax > 0).  The
  * first call after any other state change (hydro_step, hydro_step_device_dt, hydro_upload) computes this
- * step's dt with one extra reduction.  FP32 contexts with a learned model or a harvest fall back to the
- * three separate passes.  Asynchronous. */
+ * step's dt with one extra reduction.  FP32 contexts with a learned model or a harvest, reflecting or
+ * hydrostatic sides, and the split variant run the separate passes instead.  Asynchronous. */
 hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
 /* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */

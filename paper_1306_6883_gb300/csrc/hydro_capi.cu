@@ -37,6 +37,7 @@ struct hydro_ctx {
   // FP32: TMA descriptors of the two state buffers (tile loads by bulk tensor copy) when tma_ok
   CUtensorMap tmap[2];
   int tma_ok;
+  unsigned long long split_steps;  // split variant: steps taken (x sweep first on even counts)
   char err[512];
 };
 
@@ -132,6 +133,9 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
     BAD("FP32 floors must be normal float numbers (>= 1e-30)");
   if (p->use_learned_guess != 0 && p->use_learned_guess != 1) BAD("use_learned_guess must be 0 or 1");
   if (p->use_learned_guess == 1 && p->precision != HYDRO_FP32) BAD("the learned proposal is an FP32 path");
+  if (p->split != 0 && p->split != 1) BAD("split must be 0 or 1");
+  if (p->split == 1 && p->grav != 0.0) BAD("the split variant has no gravity source");
+  if (p->split == 1 && p->use_learned_guess != 0) BAD("the split variant has no learned proposal");
   return 1;
 #undef BAD
 }
@@ -222,6 +226,7 @@ hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision
   p->precision = precision;
   p->use_learned_guess = 0;
   p->grav = 0.0;
+  p->split = 0;
   return HYDRO_OK;
 }
 
@@ -333,6 +338,22 @@ static cudaError_t launch_step(hydro_ctx* c, const hydro::StepScalars& sc_host, 
                          c->stream, mode, &c->hook, c->tma_ok ? &c->tmap[c->cur] : nullptr);
 }
 
+// one dimensionally split step (paper §3.1) on the ghost-filled current state: sweep along the first
+// direction into the other buffer, fill that buffer's ghost cells, sweep along the second direction back into
+// the current buffer (which then holds the new state)
+static cudaError_t launch_split_step(hydro_ctx* c, const hydro::StepScalars& sc_host,
+                                     const hydro::StepScalars* sc_dev) {
+  const int first = (int)(c->split_steps & 1ull);
+  const int prec = c->p.precision;
+  void* a = c->state[c->cur];
+  void* b = c->state[1 - c->cur];
+  cudaError_t e = hydro::split_sweep(prec, c->kp, a, b, first, sc_host, sc_dev, c->scr, 0, c->stream);
+  if (e == cudaSuccess) e = hydro::fill_ghost(prec, c->kp, b, c->stream);
+  if (e == cudaSuccess) e = hydro::split_sweep(prec, c->kp, b, a, 1 - first, sc_host, sc_dev, c->scr, 1, c->stream);
+  if (e == cudaSuccess) ++c->split_steps;
+  return e;
+}
+
 static hydro_status check_model(hydro_ctx* c) {
   if (c->p.use_learned_guess == 1 && !c->mlp) {
     set_err(c, "use_learned_guess = 1 needs a model (hydro_set_riemann_model)");
@@ -344,10 +365,15 @@ static hydro_status check_model(hydro_ctx* c) {
 hydro_status hydro_step(hydro_ctx* c, double dt) {
   if (!c || !(dt > 0.0) || !(dt < 1e300)) return HYDRO_EINVAL;
   if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
-  cudaError_t e = launch_step(c, hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy, c->kp.grav), nullptr);
+  const hydro::StepScalars sc = hydro::make_step_scalars(dt, c->kp.dx, c->kp.dy, c->kp.grav);
+  c->fused_valid = 0;
+  if (c->p.split) {
+    cudaError_t e = launch_split_step(c, sc, nullptr);
+    return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "split_step");
+  }
+  cudaError_t e = launch_step(c, sc, nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "ctu_step");
   c->cur = 1 - c->cur;
-  c->fused_valid = 0;
   return HYDRO_OK;
 }
 
@@ -357,14 +383,18 @@ hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
   // of interior cells), use the separate passes: ghost fill, dt, step
   const bool plain_bc = c->p.bc_xlo <= HYDRO_BC_PERIODIC && c->p.bc_xhi <= HYDRO_BC_PERIODIC &&
                         c->p.bc_ylo <= HYDRO_BC_PERIODIC && c->p.bc_yhi <= HYDRO_BC_PERIODIC;
-  if (c->p.use_learned_guess == 1 || c->harvest || !plain_bc) {
+  if (c->p.use_learned_guess == 1 || c->harvest || !plain_bc || c->p.split) {
     if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
+    c->fused_valid = 0;
+    if (c->p.split) {  // the split step leaves the new state in the current buffer
+      if (e == cudaSuccess) e = launch_split_step(c, hydro::StepScalars{}, &c->scr->sc);
+      return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "advance");
+    }
     if (e == cudaSuccess) e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
     if (e != cudaSuccess) return cuda_fail(c, e, "advance");
     c->cur = 1 - c->cur;
-    c->fused_valid = 0;
     return HYDRO_OK;
   }
   cudaError_t e = cudaSuccess;
@@ -390,7 +420,7 @@ hydro_status hydro_set_harvest(hydro_ctx* c, void* d_buf, unsigned long long cap
     c->harvest = 0;
     return HYDRO_OK;
   }
-  if (c->p.precision != HYDRO_FP32 || !d_count || capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
+  if (c->p.precision != HYDRO_FP32 || c->p.split || !d_count || capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
     return HYDRO_EINVAL;
   c->hook.hbuf = (float*)d_buf;
   c->hook.hcount = d_count;
@@ -429,10 +459,14 @@ hydro_status hydro_cfl_dt_async(hydro_ctx* c, double tmax) {
 hydro_status hydro_step_device_dt(hydro_ctx* c) {
   if (!c) return HYDRO_EINVAL;
   if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  c->fused_valid = 0;
+  if (c->p.split) {
+    cudaError_t e = launch_split_step(c, hydro::StepScalars{}, &c->scr->sc);
+    return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "step_device_dt");
+  }
   cudaError_t e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
   if (e != cudaSuccess) return cuda_fail(c, e, "step_device_dt");
   c->cur = 1 - c->cur;
-  c->fused_valid = 0;
   return HYDRO_OK;
 }
 

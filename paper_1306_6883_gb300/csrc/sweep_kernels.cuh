@@ -1,0 +1,244 @@
+// Dimensionally split variant of the step (paper §3.1: the fluxes of a directional update are built without
+// the transverse flow, each directional update acts on the state the previous one left, and the order of the
+// directions alternates from step to step).  One sweep applies the one-dimensional piecewise-linear Godunov
+// method of §3.2 along x or y to every interior line of a ghost-filled state:
+//   0. primitives of the tile's cells, in the face frame (rho, u_normal, u_transverse, p);
+//   1. flattening along the line only, xi = min(chi_m, chi_{m-s});
+//   2. limited slopes along the line times xi, characteristic tracing (Eq. 13) with sigma = dt / h;
+//   3. Riemann solves at the faces, artificial viscosity from the divergence along the line;
+//   4. conservative update U += sigma (F_{m-1/2} - F_{m+1/2}).
+// A CTA takes NL lines of LN cells along the sweep (plus the 4 halo cells each side the flattening needs).
+// Shared memory is laid out so that the load enumeration is also the storage order: along-the-line
+// positions are fastest for x sweeps (rows), lines are fastest for y sweeps (columns), so both load
+// consecutive x addresses with consecutive threads.  Instantiated for FP32 in k_split.cu and for FP64 in
+// k_split_f64.cu, which is compiled without multiply-add contraction (each expression then rounds like the
+// plain C implementation of the method).
+#pragma once
+#include <atomic>
+
+#include "ctu_kernels.cuh"
+
+namespace hydro {
+
+template <typename R, int DIR, int LN, int NL>
+struct SweepLayout {
+  static constexpr int PQ = LN + 8;  // positions loaded along a line
+  static constexpr int PC = LN + 2;  // traced cells along a line: positions [3, LN + 5)
+  static constexpr int PF = LN + 1;  // faces along a line: positions [4, LN + 4]
+  static constexpr int nQ = PQ * NL, nC = PC * NL, nF = PF * NL;
+  // strides along the line and between lines, for the q arrays (Q) and the traced-cell arrays (C)
+  static constexpr int QA = DIR == 0 ? 1 : NL, QL = DIR == 0 ? PQ : 1;
+  static constexpr int CA = DIR == 0 ? 1 : NL, CL = DIR == 0 ? PC : 1;
+  static constexpr int FA = DIR == 0 ? 1 : NL, FL = DIR == 0 ? PF : 1;
+  // [4][nQ] primitives (stages 0-2), then [4][nF] fluxes (stages 3-4); [nC] xi; [nC] u_normal; [4][nC] x 2
+  // traced states
+  static constexpr int elems = 4 * nQ + 2 * nC + 8 * nC;
+  static constexpr size_t bytes = sizeof(R) * (size_t)elems;
+  static_assert(nF <= nQ, "the fluxes reuse the primitive area");
+};
+
+// item e of an enumeration over (position along, line) in storage order -> (along, line)
+template <int DIR, int PA, int NL>
+__device__ __forceinline__ void sweep_item(int e, int& a, int& l) {
+  if constexpr (DIR == 0) {
+    a = e % PA;
+    l = e / PA;
+  } else {
+    l = e % NL;
+    a = e / NL;
+  }
+}
+
+template <typename R, int DIR, int LN, int NL, int NT>
+__global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
+                                                   StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
+                                                   DevScratch* __restrict__ scr, int check_state) {
+  using L = SweepLayout<R, DIR, LN, NL>;
+  constexpr int PQ = L::PQ, PC = L::PC, PF = L::PF, nQ = L::nQ, nC = L::nC, nF = L::nF;
+  constexpr int kn = DIR == 0 ? 1 : 2, kt = DIR == 0 ? 2 : 1;  // normal / transverse momentum components
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  R* sq = reinterpret_cast<R*>(smem_raw);  // [4][nQ] primitives, face frame
+  R* sG = sq;                               // [4][nF] fluxes (conserved order), after stage 2
+  R* sxi = sq + 4 * nQ;                     // [nC]
+  R* sun = sxi + nC;                        // [nC] normal velocity of the traced cells
+  R* sl = sun + nC;                         // [4][nC] left state at m+1/2 of cell m
+  R* sr = sl + 4 * nC;                      // [4][nC] right state at m-1/2
+
+  SP<R> s;
+  s.load(P);
+  const StepScalars& sc = sc_dev ? *sc_dev : sc_host;
+  R sigma;
+  if constexpr (is_f32<R>())
+    sigma = DIR == 0 ? sc.sigx_f : sc.sigy_f;
+  else
+    sigma = DIR == 0 ? sc.sigx : sc.sigy;
+  const R h = DIR == 0 ? s.dx : s.dy;
+  const int n = DIR == 0 ? P.nx : P.ny;      // interior cells along a line
+  const int nlines = DIR == 0 ? P.ny : P.nx;
+  const int bt = DIR == 0 ? blockIdx.x : blockIdx.y;  // tile along the sweep
+  const int bl = DIR == 0 ? blockIdx.y : blockIdx.x;  // group of lines
+  const int a0 = P.ng + bt * LN;                      // padded index of the tile's first cell along the sweep
+  const int l0 = P.ng + bl * NL;                      // padded index of its first line
+  const size_t plane = (size_t)P.NY * P.pitch;
+  const int tid = threadIdx.x;
+  auto offset = [&](int a, int l) -> size_t {  // padded (along, line) -> array offset, clamped into the array
+    int i = DIR == 0 ? a : l, j = DIR == 0 ? l : a;
+    i = i < 0 ? 0 : (i >= P.NX ? P.NX - 1 : i);
+    j = j < 0 ? 0 : (j >= P.NY ? P.NY - 1 : j);
+    return (size_t)j * P.pitch + i;
+  };
+
+  // ---- 0. primitives of positions [0, LN + 8) of every line
+  for (int e = tid; e < nQ; e += NT) {
+    int a, l;
+    sweep_item<DIR, PQ, NL>(e, a, l);
+    const size_t o = offset(a0 - 4 + a, l0 + l);
+    R q[4];
+    cons_to_prim(s, __ldg(Uin + o), __ldg(Uin + o + plane), __ldg(Uin + o + 2 * plane), __ldg(Uin + o + 3 * plane),
+                 q[0], q[1], q[2], q[3]);
+    sq[e] = q[0];
+    sq[nQ + e] = q[kn];
+    sq[2 * nQ + e] = q[kt];
+    sq[3 * nQ + e] = q[3];
+  }
+  __syncthreads();
+
+  // ---- 1.-2. flattening, slopes and tracing of the cells at positions [3, LN + 5)
+  for (int e = tid; e < nC; e += NT) {
+    int c, l;
+    sweep_item<DIR, PC, NL>(e, c, l);
+    const int b = (c + 3) * L::QA + l * L::QL;  // the cell's index in the q arrays
+    constexpr int st = L::QA;
+    const R* qp = sq + 3 * nQ;
+    const R* qn = sq + nQ;
+    R xi = (R)1;
+    if (s.flatten) {
+      auto chi = [&](int m) {
+        return flatten_chi<R>(qp[b + (m - 2) * st], qp[b + (m - 1) * st], qp[b + (m + 1) * st], qp[b + (m + 2) * st],
+                              qn[b + (m - 1) * st], qn[b + (m + 1) * st], s.small_pres);
+      };
+      const int sgn = (qp[b + st] - qp[b - st]) >= (R)0 ? 1 : -1;
+      xi = M<R>::mn(chi(0), chi(-sgn));
+    }
+    sxi[e] = xi;
+    sun[e] = qn[b];
+    R q[4], dq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const R* a = sq + k * nQ + b;
+      q[k] = a[0];
+      dq[k] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+    }
+    R ql[4], qr[4];
+    trace<R>(s, sigma, q, dq, ql, qr);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sl[k * nC + e] = ql[k];
+      sr[k * nC + e] = qr[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. Riemann solves + artificial viscosity at faces [0, LN] of each line (face f between traced
+  //         cells f and f + 1, i.e. padded positions a0 + f - 1 and a0 + f)
+  TileCounters cnt;
+  for (int e = tid; e < nF; e += NT) {
+    int f, l;
+    sweep_item<DIR, PF, NL>(e, f, l);
+    const int fa = a0 + f;  // padded index of the cell right of the face
+    const bool valid = l0 + l < P.ng + nlines && fa <= P.ng + n;
+    const int cL = f * L::CA + l * L::CL, cR = cL + L::CA;
+    R a[4], bq[4], F[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = sl[k * nC + cL];
+      bq[k] = sr[k * nC + cR];
+    }
+    int it;
+    bool ok;
+    R pst;
+    riemann(s, a, bq, (R)0, F, it, ok, &pst);
+    if (valid && (f < LN || fa == P.ng + n)) {  // a face shared by two tiles counts once
+      cnt.solves++;
+      cnt.iters += it;
+      cnt.nonconv += ok ? 0 : 1;
+    }
+    R G[4];
+    G[0] = F[0];
+    G[kn] = F[1];
+    G[kt] = F[2];
+    G[3] = F[3];
+    if (s.cvisc > (R)0 && valid) {
+      R av;
+      if constexpr (is_f32<R>()) {
+        av = s.cvisc * M<R>::mx(sun[cL] - sun[cR], (R)0);
+      } else {
+        const R div = (sun[cR] - sun[cL]) / h;
+        av = s.cvisc * M<R>::mx(-div * h, (R)0);
+      }
+      const size_t oL = offset(fa - 1, l0 + l), oR = offset(fa, l0 + l);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) G[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+    }
+    const int g = f * L::FA + l * L::FL;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sG[k * nF + g] = G[k];
+  }
+  __syncthreads();
+
+  // ---- 4. conservative update of the tile's interior cells
+  constexpr int nU = LN * NL;
+  for (int e = tid; e < nU; e += NT) {
+    int u, l;
+    sweep_item<DIR, LN, NL>(e, u, l);
+    if (l0 + l >= P.ng + nlines || a0 + u >= P.ng + n) continue;
+    const size_t o = offset(a0 + u, l0 + l);
+    const int g = u * L::FA + l * L::FL;
+    R Un[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Un[k] = __ldg(Uin + o + k * plane) + sigma * (sG[k * nF + g] - sG[k * nF + g + L::FA]);
+      Uout[o + k * plane] = Un[k];
+    }
+    if (check_state) {
+      if (!finite4(Un[0], Un[1], Un[2], Un[3])) {
+        cnt.flags |= STATUS_NONFINITE;
+      } else {
+        const R ke = M<R>::dv((R)0.5 * (Un[1] * Un[1] + Un[2] * Un[2]), Un[0]);
+        if (!(Un[0] > (R)0) || !(Un[3] - ke > (R)0)) cnt.flags |= STATUS_NEGATIVE;
+      }
+    }
+  }
+  flush_counters<NT>(cnt, scr);
+}
+
+// Launch of one sweep with the tile shape of the precision (set once per device: dynamic shared memory).
+template <typename R, int DIR, int LN, int NL, int NT>
+struct Sweep {
+  static std::atomic<unsigned long long> attr_set;
+  static cudaError_t launch(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
+                            const StepScalars* sc_dev, DevScratch* scr, int check_state, cudaStream_t stream) {
+    using L = SweepLayout<R, DIR, LN, NL>;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    const unsigned long long bit = 1ull << dev;
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+      e = cudaFuncSetAttribute(sweep_kernel<R, DIR, LN, NL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)L::bytes);
+      if (e != cudaSuccess) return e;
+      attr_set.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    const int along = DIR == 0 ? P.nx : P.ny, lines = DIR == 0 ? P.ny : P.nx;
+    const int ta = (along + LN - 1) / LN, tl = (lines + NL - 1) / NL;
+    const dim3 grid(DIR == 0 ? ta : tl, DIR == 0 ? tl : ta);
+    sweep_kernel<R, DIR, LN, NL, NT><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
+                                                                     check_state);
+    return cudaGetLastError();
+  }
+};
+template <typename R, int DIR, int LN, int NL, int NT>
+std::atomic<unsigned long long> Sweep<R, DIR, LN, NL, NT>::attr_set{0};
+
+}  // namespace hydro

@@ -28,7 +28,7 @@ class HydroParams(ctypes.Structure):
         ("riemann_maxiter", ctypes.c_int), ("riemann_tol", ctypes.c_double),
         ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double),
         ("precision", ctypes.c_int), ("use_learned_guess", ctypes.c_int),
-        ("grav", ctypes.c_double),
+        ("grav", ctypes.c_double), ("split", ctypes.c_int),
     ]
 
 

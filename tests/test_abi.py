@@ -47,7 +47,8 @@ def test_defaults_and_layout(lib):
                                          ("limiter", 3), ("riemann_maxiter", 0), ("small_pres", 0.0),
                                          ("precision", 2), ("bc_xlo", 1), ("use_learned_guess", 1),
                                          ("bc_xlo", 3), ("bc_xhi", 3), ("bc_yhi", 4), ("bc_ylo", -1),
-                                         ("grav", float("nan")), ("grav", float("inf"))])
+                                         ("grav", float("nan")), ("grav", float("inf")), ("split", 2),
+                                         ("split", -1)])
 def test_invalid_parameters_are_rejected_before_any_allocation(lib, field, value):
     from paper_1306_6883_gb300 import hydro as H
     p = H.default_params(16, 16)
@@ -83,3 +84,13 @@ def test_null_and_misaligned_buffers_are_rejected(lib):
 def test_oracle_library_builds_and_loads():
     import oracle
     assert oracle.num_threads() >= 1
+
+
+@pytest.mark.parametrize("extra", [dict(grav=-1.0), dict(use_learned_guess=1, precision=1)])
+def test_split_variant_rejects_what_it_does_not_implement(lib, extra):
+    from paper_1306_6883_gb300 import hydro as H
+    p = H.default_params(16, 16, split=1)
+    assert H.state_pitch(p) > 0
+    for k, v in extra.items():
+        setattr(p, k, v)
+    assert H.state_pitch(p) == 0
