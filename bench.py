@@ -194,7 +194,7 @@ def time_device_path(pr, precision, steps, warmup, flush, **kw):
     solves = stats1[0] - stats0[0]
     iters = stats1[1] - stats0[1]
     plain = all(b in ("outflow", "periodic") for b in pr.bc)
-    launches = 5 if kw.get("split") else (1 if plain else 3)  # split: fill, dt, sweep, fill, sweep
+    launches = 2 if kw.get("split") else (1 if plain else 3)  # split: x (y) sweep, y (x) sweep + dt
     return {"step_ms": step_ms, "kernel_ms": step_ms, "iters_per_solve": iters / max(solves, 1),
             "t_sim": t_sim, "totals": tot, "launches_per_step": launches}
 
@@ -466,7 +466,7 @@ def run_ours(args, world, rank, local):
         split = {"workload": wname, "steps": 20, "value": zones * 20 / (sum(r["step_ms"]) / 1e3),
                  "ms_per_step": sum(r["step_ms"]) / 20, "launches_per_step": r["launches_per_step"],
                  "riemann_iters_per_solve": r["iters_per_solve"],
-                 "step": "dimensionally split: ghost fill, CFL dt, x (or y) sweep, ghost fill, y (or x) sweep"}
+                 "step": "dimensionally split: x (or y) sweep, then y (or x) sweep folding in the next CFL dt"}
         prt, rtname = workload("rt1024")
         r = time_device_path(prt, "fp32", 20, args.warmup, flush)
         rt = {"workload": rtname, "steps": 20, "value": prt.nx * prt.ny * 20 / (sum(r["step_ms"]) / 1e3),

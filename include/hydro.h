@@ -132,8 +132,8 @@ hydro_status hydro_cfl_dt(hydro_ctx* ctx, double* dt_out);
  * conservative update.  Writes the other buffer and swaps.  Asynchronous: problems found on the device
  * (non-finite or non-positive results, unconverged Riemann solves) are recorded in the context's status
  * word and reported by hydro_sync_status().  With split = 1 the step is the dimensionally split one (§3.1):
- * a one-dimensional sweep into the other buffer, a ghost fill of it, and the other sweep back into the
- * current buffer (three launches). */
+ * a one-dimensional sweep into the other buffer and the other sweep back into the current buffer (two
+ * launches; cells outside the domain are read through the boundary map). */
 hydro_status hydro_step(hydro_ctx* ctx, double dt);
 
 /* CFL time step kept on the device: reduce the dt of hydro_cfl_dt into the context's device memory,
@@ -158,8 +158,9 @@ hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
  * and reduces the CFL time step of the state it writes (so no dt pass); its last block advances the
  * device time by this step's dt and keeps the next step's dt (clamped to reach tmax when tmax > 0).  The
  * first call after any other state change (hydro_step, hydro_step_device_dt, hydro_upload) computes this
- * step's dt with one extra reduction.  FP32 contexts with a learned model or a harvest, reflecting or
- * hydrostatic sides, and the split variant run the separate passes instead.  Asynchronous. */
+ * step's dt with one extra reduction.  With split = 1: the two sweeps of hydro_step, the second one
+ * reducing the next dt.  FP32 contexts with a learned model or a harvest, and reflecting or hydrostatic
+ * sides of the unsplit step, run the separate passes instead.  Asynchronous. */
 hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
 /* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */

@@ -1,10 +1,11 @@
 """Command-line driver, after the paper's single driver (§2: ./pyro.py solver problem infile):
 
     python -m paper_1306_6883_gb300 PROBLEM [--nx N] [--ny N] [--precision fp32|fp64]
-                                            [--steps K | --tmax T] [--seed S] [--dump FILE]
+                                            [--steps K | --tmax T] [--seed S] [--split] [--dump FILE]
 
-PROBLEM is one of sod, sod_y, kh, sedov, quad, pulse (seeded set-ups of hydro_problems).  Runs the
-device-resident loop (fill ghost cells, CFL dt, CTU step) and prints one JSON line with the simulated
+PROBLEM is one of sod, sod_y, kh, sedov, quad, pulse, rt (seeded set-ups of hydro_problems; rt is the
+Rayleigh-Taylor column with gravity, nx x 3nx by default).  Runs the device-resident loop (fill ghost
+cells, CFL dt, CTU step; --split: the dimensionally split step) and prints one JSON line with the simulated
 time, step count, wall time, conserved totals and the Riemann-solver counters.  --dump writes the final
 state (dense float64 array, shape (4, ny+8, nx+8)) with numpy.save.
 """
@@ -35,6 +36,8 @@ def make_problem(name, nx, ny, seed):
         return hp.quad(nx, ny, seed=seed)
     if name == "pulse":
         return hp.pulse(nx, ny)
+    if name == "rt":
+        return hp.rt(nx, ny)
     raise SystemExit(f"unknown problem {name}")
 
 
@@ -47,6 +50,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--tmax", type=float, default=None)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--split", action="store_true")
     ap.add_argument("--dump", default=None)
     a = ap.parse_args(argv)
 
@@ -57,9 +61,10 @@ def main(argv=None):
     from .solver import Solver, params_for
 
     build.build()
-    pr = make_problem(a.problem, a.nx, a.ny or a.nx, a.seed)
+    ny = a.ny or (3 * a.nx if a.problem == "rt" else a.nx)
+    pr = make_problem(a.problem, a.nx, ny, a.seed)
     prec = H.HYDRO_FP32 if a.precision == "fp32" else H.HYDRO_FP64
-    s = Solver(params_for(pr, prec), pr.U)
+    s = Solver(params_for(pr, prec, split=int(a.split)), pr.U)
     tmax = a.tmax if a.tmax is not None else (pr.tmax if np.isfinite(pr.tmax) and a.steps is None else 0.0)
     steps = a.steps if a.steps is not None else 10 ** 9
     torch.cuda.synchronize()
@@ -78,7 +83,8 @@ def main(argv=None):
     wall = time.perf_counter() - t0
     st, stats = s.status(raise_on_error=False)
     t, nsteps = s.time()
-    out = {"problem": a.problem, "nx": pr.nx, "ny": pr.ny, "precision": a.precision, "t": t, "steps": nsteps,
+    out = {"problem": a.problem, "nx": pr.nx, "ny": pr.ny, "precision": a.precision, "split": a.split, "t": t,
+           "steps": nsteps,
            "wall_s": wall, "zone_updates_per_s": pr.nx * pr.ny * nsteps / wall if wall > 0 else None,
            "totals": s.totals(), "status": H.STATUS_NAMES[st], "riemann_solves": stats[0],
            "riemann_iters": stats[1], "riemann_nonconverged": stats[2]}

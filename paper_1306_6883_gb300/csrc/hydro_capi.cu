@@ -338,18 +338,19 @@ static cudaError_t launch_step(hydro_ctx* c, const hydro::StepScalars& sc_host, 
                          c->stream, mode, &c->hook, c->tma_ok ? &c->tmap[c->cur] : nullptr);
 }
 
-// one dimensionally split step (paper §3.1) on the ghost-filled current state: sweep along the first
-// direction into the other buffer, fill that buffer's ghost cells, sweep along the second direction back into
-// the current buffer (which then holds the new state)
-static cudaError_t launch_split_step(hydro_ctx* c, const hydro::StepScalars& sc_host,
-                                     const hydro::StepScalars* sc_dev) {
+// one dimensionally split step (paper §3.1) on the current state: sweep along the first direction into the
+// other buffer, then along the second direction back into the current buffer (which then holds the new
+// state).  The sweeps read cells outside the domain through the boundary map, so no ghost fill is needed.
+// sc_next != NULL: the second sweep also reduces the next step's dt (the fused step).
+static cudaError_t launch_split_step(hydro_ctx* c, const hydro::StepScalars& sc_host, const hydro::StepScalars* sc_dev,
+                                     hydro::StepScalars* sc_next = nullptr, double tmax = 0.0) {
   const int first = (int)(c->split_steps & 1ull);
   const int prec = c->p.precision;
   void* a = c->state[c->cur];
   void* b = c->state[1 - c->cur];
-  cudaError_t e = hydro::split_sweep(prec, c->kp, a, b, first, sc_host, sc_dev, c->scr, 0, c->stream);
-  if (e == cudaSuccess) e = hydro::fill_ghost(prec, c->kp, b, c->stream);
-  if (e == cudaSuccess) e = hydro::split_sweep(prec, c->kp, b, a, 1 - first, sc_host, sc_dev, c->scr, 1, c->stream);
+  cudaError_t e = hydro::split_sweep(prec, c->kp, a, b, first, sc_host, sc_dev, c->scr, 0, nullptr, 0.0, c->stream);
+  if (e == cudaSuccess)
+    e = hydro::split_sweep(prec, c->kp, b, a, 1 - first, sc_host, sc_dev, c->scr, 1, sc_next, tmax, c->stream);
   if (e == cudaSuccess) ++c->split_steps;
   return e;
 }
@@ -383,15 +384,26 @@ hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
   // of interior cells), use the separate passes: ghost fill, dt, step
   const bool plain_bc = c->p.bc_xlo <= HYDRO_BC_PERIODIC && c->p.bc_xhi <= HYDRO_BC_PERIODIC &&
                         c->p.bc_ylo <= HYDRO_BC_PERIODIC && c->p.bc_yhi <= HYDRO_BC_PERIODIC;
-  if (c->p.use_learned_guess == 1 || c->harvest || !plain_bc || c->p.split) {
+  if (c->p.split) {
+    // two sweeps, the second folding in the next step's dt; the new state is in the current buffer
+    cudaError_t e = cudaSuccess;
+    if (!c->fused_valid)
+      e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 0, &c->scr->scf[c->fused_parity],
+                        c->stream);
+    if (e == cudaSuccess)
+      e = launch_split_step(c, hydro::StepScalars{}, &c->scr->scf[c->fused_parity],
+                            &c->scr->scf[1 - c->fused_parity], tmax);
+    if (e != cudaSuccess) return cuda_fail(c, e, "split_step_fused");
+    ++c->step_calls;
+    c->fused_parity = 1 - c->fused_parity;
+    c->fused_valid = 1;
+    return HYDRO_OK;
+  }
+  if (c->p.use_learned_guess == 1 || c->harvest || !plain_bc) {
     if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
     c->fused_valid = 0;
-    if (c->p.split) {  // the split step leaves the new state in the current buffer
-      if (e == cudaSuccess) e = launch_split_step(c, hydro::StepScalars{}, &c->scr->sc);
-      return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "advance");
-    }
     if (e == cudaSuccess) e = launch_step(c, hydro::StepScalars{}, &c->scr->sc);
     if (e != cudaSuccess) return cuda_fail(c, e, "advance");
     c->cur = 1 - c->cur;

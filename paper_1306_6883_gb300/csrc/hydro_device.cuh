@@ -175,19 +175,19 @@ __device__ __forceinline__ int ghost_bc(int i, int ng, int n, int lo_bc, int hi_
   return i < ng ? lo_bc : i >= ng + n ? hi_bc : -1;
 }
 
-// One ghost cell (i, j) of the padded state.  Its source is the interior cell (map_x(i), map_y(j)); a
-// reflecting side negates the momentum normal to it (mx across x walls, my across y walls).  A hydrostatic
-// y side keeps the edge row's density and momenta and integrates its pressure with dp/dy = rho g at constant
-// rho: p = p_edge + rho g (y - y_edge), E = p/(gamma - 1) + kinetic.  Every source is an interior cell, so
-// one pass fills edges and corners; a corner combines its x side's mapping with its y side's, as filling the
-// x sides of the interior rows and then the y bands over the full width does.  The hydrostatic energy is
-// computed in double with rounded operations only, in the order of the formula, for every state precision.
+// Value of the padded cell (i, j) as the ghost fill defines it (an interior cell: its stored value).  The
+// source is the interior cell (map_x(i), map_y(j)); a reflecting side negates the momentum normal to it (mx
+// across x walls, my across y walls).  A hydrostatic y side keeps the edge row's density and momenta and
+// integrates its pressure with dp/dy = rho g at constant rho: p = p_edge + rho g (y - y_edge),
+// E = p/(gamma - 1) + kinetic.  Every source is an interior cell, so one pass fills edges and corners; a
+// corner combines its x side's mapping with its y side's, as filling the x sides of the interior rows and
+// then the y bands over the full width does.  The hydrostatic energy is computed in double with rounded
+// operations only, in the order of the formula, for every state precision.
 template <typename R>
-__device__ __forceinline__ void fill_ghost_cell(const KParams& P, R* __restrict__ U, int i, int j, size_t plane) {
+__device__ __forceinline__ void bc_cell(const KParams& P, const R* U, int i, int j, size_t plane, R v[4]) {
   const int si = map_index(i, P.ng, P.nx, P.bc[0], P.bc[1]);
   const int sj = map_index(j, P.ng, P.ny, P.bc[2], P.bc[3]);
-  const size_t d = (size_t)j * P.pitch + i, s = (size_t)sj * P.pitch + si;
-  R v[4];
+  const size_t s = (size_t)sj * P.pitch + si;
 #pragma unroll
   for (int k = 0; k < 4; ++k) v[k] = U[s + k * plane];
   if (ghost_bc(i, P.ng, P.nx, P.bc[0], P.bc[1]) == 2) v[1] = -v[1];
@@ -201,6 +201,14 @@ __device__ __forceinline__ void fill_ghost_cell(const KParams& P, R* __restrict_
     const double pg = __dadd_rn(pe, __dmul_rn(__dmul_rn(rho, P.grav), __dmul_rn((double)(j - sj), P.dy)));
     v[3] = (R)__dadd_rn(__ddiv_rn(pg, P.gm1), ke);
   }
+}
+
+// Writes the ghost cell (i, j) with its boundary value (bc_cell).
+template <typename R>
+__device__ __forceinline__ void fill_ghost_cell(const KParams& P, R* __restrict__ U, int i, int j, size_t plane) {
+  R v[4];
+  bc_cell(P, U, i, j, plane, v);
+  const size_t d = (size_t)j * P.pitch + i;
 #pragma unroll
   for (int k = 0; k < 4; ++k) U[d + k * plane] = v[k];
 }

@@ -51,14 +51,18 @@ cudaError_t ctu_step_fused_f64(const KParams& P, const double* Uin, double* Uout
 cudaError_t ctu_step_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,
                          const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
 
-// One sweep of the dimensionally split variant (sweep_kernels.cuh) along dir (0: x, 1: y) of the ghost-filled
-// state Uin into Uout (interior cells only), with sigma = dt/dx or dt/dy from sc_dev if not NULL, else sc_host.
-// check_state: flag non-finite / non-positive cells of the result in the status word.
+// One sweep of the dimensionally split variant (sweep_kernels.cuh) along dir (0: x, 1: y) of the state Uin
+// into Uout (interior cells only; halo cells outside the domain are read through the boundary map, so Uin
+// needs no ghost fill), with sigma = dt/dx or dt/dy from sc_dev if not NULL, else sc_host.  check_state:
+// flag non-finite / non-positive cells of the result in the status word.  sc_next != NULL: the second sweep
+// of a fused step -- also reduce the CFL dt of the result; the last block advances the device time by this
+// step's dt and writes the next step's factors to sc_next (dt clamped to reach tmax when tmax > 0).
 cudaError_t split_sweep(int precision, const KParams& P, const void* Uin, void* Uout, int dir,
                         const StepScalars& sc_host, const StepScalars* sc_dev, DevScratch* scr, int check_state,
-                        cudaStream_t stream);
+                        StepScalars* sc_next, double tmax, cudaStream_t stream);
 cudaError_t split_sweep_f64(const KParams& P, const double* Uin, double* Uout, int dir, const StepScalars& sc_host,
-                            const StepScalars* sc_dev, DevScratch* scr, int check_state, cudaStream_t stream);
+                            const StepScalars* sc_dev, DevScratch* scr, int check_state, StepScalars* sc_next,
+                            double tmax, cudaStream_t stream);
 
 // Host copy of the device hash32 (mlp.cuh), for per-step sampling seeds.
 inline unsigned int host_hash32(unsigned int x) {

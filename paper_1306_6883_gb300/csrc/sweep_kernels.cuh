@@ -1,13 +1,17 @@
 // Dimensionally split variant of the step (paper §3.1: the fluxes of a directional update are built without
 // the transverse flow, each directional update acts on the state the previous one left, and the order of the
 // directions alternates from step to step).  One sweep applies the one-dimensional piecewise-linear Godunov
-// method of §3.2 along x or y to every interior line of a ghost-filled state:
+// method of §3.2 along x or y to every interior line of the state:
 //   0. primitives of the tile's cells, in the face frame (rho, u_normal, u_transverse, p);
 //   1. flattening along the line only, xi = min(chi_m, chi_{m-s});
 //   2. limited slopes along the line times xi, characteristic tracing (Eq. 13) with sigma = dt / h;
 //   3. Riemann solves at the faces, artificial viscosity from the divergence along the line;
 //   4. conservative update U += sigma (F_{m-1/2} - F_{m+1/2}).
 // A CTA takes NL lines of LN cells along the sweep (plus the 4 halo cells each side the flattening needs).
+// Halo cells outside the domain are read through the boundary conditions' map of the interior (bc_cell: the
+// values a ghost fill would write), so neither sweep needs a ghost-fill pass.  FUSED (the second sweep of a
+// step run by hydro_step_fused): the sweep also folds the CFL constraint of its new cells into a minimum,
+// and its last block advances the time and writes the next step's factors, as the fused unsplit step does.
 // Shared memory is laid out so that the load enumeration is also the storage order: along-the-line
 // positions are fastest for x sweeps (rows), lines are fastest for y sweeps (columns), so both load
 // consecutive x addresses with consecutive threads.  Instantiated for FP32 in k_split.cu and for FP64 in
@@ -49,10 +53,11 @@ __device__ __forceinline__ void sweep_item(int e, int& a, int& l) {
   }
 }
 
-template <typename R, int DIR, int LN, int NL, int NT>
+template <typename R, int DIR, int LN, int NL, int NT, bool FUSED>
 __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
                                                    StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
-                                                   DevScratch* __restrict__ scr, int check_state) {
+                                                   DevScratch* __restrict__ scr, int check_state,
+                                                   StepScalars* __restrict__ sc_next, double tmax) {
   using L = SweepLayout<R, DIR, LN, NL>;
   constexpr int PQ = L::PQ, PC = L::PC, PF = L::PF, nQ = L::nQ, nC = L::nC, nF = L::nF;
   constexpr int kn = DIR == 0 ? 1 : 2, kt = DIR == 0 ? 2 : 1;  // normal / transverse momentum components
@@ -81,25 +86,64 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
   const int l0 = P.ng + bl * NL;                      // padded index of its first line
   const size_t plane = (size_t)P.NY * P.pitch;
   const int tid = threadIdx.x;
-  auto offset = [&](int a, int l) -> size_t {  // padded (along, line) -> array offset, clamped into the array
-    int i = DIR == 0 ? a : l, j = DIR == 0 ? l : a;
-    i = i < 0 ? 0 : (i >= P.NX ? P.NX - 1 : i);
-    j = j < 0 ? 0 : (j >= P.NY ? P.NY - 1 : j);
+  // Lines past the domain (a ragged last group) and positions past the padded array (a ragged last tile)
+  // are clamped to cells that exist; what is computed from them is never stored or counted.
+  auto clamp_line = [&](int l) { return l < P.ng + nlines ? l : P.ng + nlines - 1; };
+  auto clamp_along = [&](int a) { return a < n + 2 * P.ng ? a : n + 2 * P.ng - 1; };
+  auto interior_offset = [&](int a, int l) -> size_t {
+    const int i = DIR == 0 ? a : l, j = DIR == 0 ? l : a;
     return (size_t)j * P.pitch + i;
   };
-
-  // ---- 0. primitives of positions [0, LN + 8) of every line
-  for (int e = tid; e < nQ; e += NT) {
-    int a, l;
-    sweep_item<DIR, PQ, NL>(e, a, l);
-    const size_t o = offset(a0 - 4 + a, l0 + l);
+  // cell (along a, line l) with ghost values from the boundary map
+  auto load_cell = [&](int a, int l, R v[4]) {
+    a = clamp_along(a);
+    l = clamp_line(l);
+    if (a >= P.ng && a < P.ng + n) {
+      const size_t o = interior_offset(a, l);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = __ldg(Uin + o + k * plane);
+    } else {
+      bc_cell(P, Uin, DIR == 0 ? a : l, DIR == 0 ? l : a, plane, v);
+    }
+  };
+  auto store_prim = [&](int e, const R U[4]) {
     R q[4];
-    cons_to_prim(s, __ldg(Uin + o), __ldg(Uin + o + plane), __ldg(Uin + o + 2 * plane), __ldg(Uin + o + 3 * plane),
-                 q[0], q[1], q[2], q[3]);
+    cons_to_prim(s, U[0], U[1], U[2], U[3], q[0], q[1], q[2], q[3]);
     sq[e] = q[0];
     sq[nQ + e] = q[kn];
     sq[2 * nQ + e] = q[kt];
     sq[3 * nQ + e] = q[3];
+  };
+
+  // ---- 0. primitives of positions [0, LN + 8) of every line
+  if (a0 - 4 >= P.ng && a0 + LN + 4 <= P.ng + n) {
+    // the tile's positions are all interior: every load of a thread is issued before any conversion
+    constexpr int NLD = (nQ + NT - 1) / NT;
+    R Ul[NLD][4];
+#pragma unroll
+    for (int it = 0; it < NLD; ++it) {
+      const int e = tid + it * NT;
+      if (e < nQ) {
+        int a, l;
+        sweep_item<DIR, PQ, NL>(e, a, l);
+        const size_t o = interior_offset(a0 - 4 + a, clamp_line(l0 + l));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NLD; ++it) {
+      const int e = tid + it * NT;
+      if (e < nQ) store_prim(e, Ul[it]);
+    }
+  } else {
+    for (int e = tid; e < nQ; e += NT) {
+      int a, l;
+      sweep_item<DIR, PQ, NL>(e, a, l);
+      R U[4];
+      load_cell(a0 - 4 + a, l0 + l, U);
+      store_prim(e, U);
+    }
   }
   __syncthreads();
 
@@ -176,9 +220,11 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
         const R div = (sun[cR] - sun[cL]) / h;
         av = s.cvisc * M<R>::mx(-div * h, (R)0);
       }
-      const size_t oL = offset(fa - 1, l0 + l), oR = offset(fa, l0 + l);
+      R UL[4], UR[4];
+      load_cell(fa - 1, l0 + l, UL);
+      load_cell(fa, l0 + l, UR);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) G[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+      for (int k = 0; k < 4; ++k) G[k] += av * (UL[k] - UR[k]);
     }
     const int g = f * L::FA + l * L::FL;
 #pragma unroll
@@ -188,11 +234,12 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
 
   // ---- 4. conservative update of the tile's interior cells
   constexpr int nU = LN * NL;
+  R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
   for (int e = tid; e < nU; e += NT) {
     int u, l;
     sweep_item<DIR, LN, NL>(e, u, l);
     if (l0 + l >= P.ng + nlines || a0 + u >= P.ng + n) continue;
-    const size_t o = offset(a0 + u, l0 + l);
+    const size_t o = interior_offset(a0 + u, l0 + l);
     const int g = u * L::FA + l * L::FL;
     R Un[4];
 #pragma unroll
@@ -200,7 +247,9 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
       Un[k] = __ldg(Uin + o + k * plane) + sigma * (sG[k * nF + g] - sG[k * nF + g + L::FA]);
       Uout[o + k * plane] = Un[k];
     }
-    if (check_state) {
+    if constexpr (FUSED) {
+      cfl_value(s, Un[0], Un[1], Un[2], Un[3], cmin, cnt.flags);  // the next step's constraint (Eq. 6)
+    } else if (check_state) {
       if (!finite4(Un[0], Un[1], Un[2], Un[3])) {
         cnt.flags |= STATUS_NONFINITE;
       } else {
@@ -210,35 +259,72 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
     }
   }
   flush_counters<NT>(cnt, scr);
+  if constexpr (FUSED) {
+    // block minimum of the CFL constraint; the last block to finish advances the time by this step's dt
+    // and writes the next step's factors (dt = cfl * min, clamped to reach tmax when tmax > 0)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const R o = __shfl_xor_sync(0xffffffffu, cmin, off);
+      cmin = o < cmin ? o : cmin;
+    }
+    __shared__ R wmin[NT / 32];
+    __shared__ bool last;
+    if ((tid & 31) == 0) wmin[tid >> 5] = cmin;
+    __syncthreads();
+    if (tid == 0) {
+      R b = wmin[0];
+      for (int k = 1; k < NT / 32; ++k) b = wmin[k] < b ? wmin[k] : b;
+      atomicMin(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong((double)b));
+      __threadfence();
+      last = atomicAdd(&scr->step_blocks_done, 1u) == gridDim.x * gridDim.y - 1u;
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+      __threadfence();
+      const unsigned long long bits =
+          atomicExch(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
+      const double t = scr->t + sc.dt;
+      scr->t = t;
+      scr->nsteps = scr->nsteps + 1;
+      double dt = P.cfl * __longlong_as_double((long long)bits);
+      if (tmax > 0.0) {
+        const double left = tmax - t;
+        dt = dt > left ? left : dt;
+        dt = dt < 0.0 ? 0.0 : dt;
+      }
+      scr->dt = dt;
+      *sc_next = make_step_scalars(dt, P.dx, P.dy, P.grav);
+      scr->step_blocks_done = 0u;
+    }
+  }
 }
 
-// Launch of one sweep with the tile shape of the precision (set once per device: dynamic shared memory).
+// Launch of one sweep with the tile shape of the precision (dynamic shared memory raised once per device).
+// sc_next == NULL: a plain sweep; otherwise the fused second sweep of a step (FUSED instantiation).
 template <typename R, int DIR, int LN, int NL, int NT>
 struct Sweep {
-  static std::atomic<unsigned long long> attr_set;
   static cudaError_t launch(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
-                            const StepScalars* sc_dev, DevScratch* scr, int check_state, cudaStream_t stream) {
+                            const StepScalars* sc_dev, DevScratch* scr, int check_state, StepScalars* sc_next,
+                            double tmax, cudaStream_t stream) {
     using L = SweepLayout<R, DIR, LN, NL>;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev >= 64) return cudaErrorInvalidDevice;
-    const unsigned long long bit = 1ull << dev;
-    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-      e = cudaFuncSetAttribute(sweep_kernel<R, DIR, LN, NL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)L::bytes);
-      if (e != cudaSuccess) return e;
-      attr_set.fetch_or(bit, std::memory_order_acq_rel);
-    }
+    static std::atomic<unsigned long long> done_plain{0}, done_fused{0};
     const int along = DIR == 0 ? P.nx : P.ny, lines = DIR == 0 ? P.ny : P.nx;
     const int ta = (along + LN - 1) / LN, tl = (lines + NL - 1) / NL;
     const dim3 grid(DIR == 0 ? ta : tl, DIR == 0 ? tl : ta);
-    sweep_kernel<R, DIR, LN, NL, NT><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
-                                                                     check_state);
+    cudaError_t e;
+    if (sc_next) {
+      e = smem_attr_once(sweep_kernel<R, DIR, LN, NL, NT, true>, L::bytes, done_fused);
+      if (e != cudaSuccess) return e;
+      sweep_kernel<R, DIR, LN, NL, NT, true><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
+                                                                             check_state, sc_next, tmax);
+    } else {
+      e = smem_attr_once(sweep_kernel<R, DIR, LN, NL, NT, false>, L::bytes, done_plain);
+      if (e != cudaSuccess) return e;
+      sweep_kernel<R, DIR, LN, NL, NT, false><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
+                                                                              check_state, nullptr, 0.0);
+    }
     return cudaGetLastError();
   }
 };
-template <typename R, int DIR, int LN, int NL, int NT>
-std::atomic<unsigned long long> Sweep<R, DIR, LN, NL, NT>::attr_set{0};
 
 }  // namespace hydro
