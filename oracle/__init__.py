@@ -25,6 +25,7 @@ class OracleParams(ctypes.Structure):
         ("limiter", ctypes.c_int), ("use_flattening", ctypes.c_int), ("cvisc", ctypes.c_double),
         ("riemann_maxiter", ctypes.c_int), ("riemann_tol", ctypes.c_double),
         ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double), ("grav", ctypes.c_double),
+        ("riemann_solver", ctypes.c_int),
     ]
 
 
@@ -58,6 +59,8 @@ def lib():
         L.oracle_trace.argtypes = [P, ctypes.c_double, _D, _D, _D, _D]
         L.oracle_riemann.argtypes = [P, _D, _D, ctypes.c_double, _D, _D, _D, _D, ctypes.POINTER(ctypes.c_int)]
         L.oracle_euler_flux.argtypes = [P, _D, _D]
+        L.oracle_hllc.argtypes = [P, _D, _D, _D, _D]
+        L.oracle_hllc_core.argtypes = [P, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D]
         L.oracle_num_threads.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -65,11 +68,14 @@ def lib():
 
 def params(nx, ny, *, ng=4, xmin=0.0, xmax=1.0, ymin=0.0, ymax=1.0, gamma=1.4, cfl=0.8,
            bc=("outflow", "outflow", "outflow", "outflow"), limiter=2, use_flattening=1, cvisc=0.1,
-           riemann_maxiter=32, riemann_tol=1e-14, small_dens=1e-10, small_pres=1e-20, grav=0.0):
+           riemann_maxiter=32, riemann_tol=1e-14, small_dens=1e-10, small_pres=1e-20, grav=0.0, riemann_solver=0):
+    """riemann_solver: 0 (or "two-shock") the two-shock iteration, 1 (or "hllc") HLLC."""
     code = {"outflow": 0, "periodic": 1, "reflect": 2, "hydrostatic": 3}
+    solver = {"two-shock": 0, "hllc": 1}.get(riemann_solver, riemann_solver)
     return OracleParams(nx, ny, ng, xmin, xmax, ymin, ymax, gamma, cfl,
                         code[bc[0]], code[bc[1]], code[bc[2]], code[bc[3]],
-                        limiter, use_flattening, cvisc, riemann_maxiter, riemann_tol, small_dens, small_pres, grav)
+                        limiter, use_flattening, cvisc, riemann_maxiter, riemann_tol, small_dens, small_pres, grav,
+                        solver)
 
 
 def _ptr(a):
@@ -162,6 +168,24 @@ def euler_flux(p, q):
     F = np.zeros(4)
     lib().oracle_euler_flux(ctypes.byref(p), _ptr(q), _ptr(F))
     return F
+
+
+def hllc(p, qL, qR):
+    """HLLC flux in the face frame with estimated wave speeds.  Returns (flux, (S_L, S*, S_R))."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    F, sp = np.zeros(4), np.zeros(3)
+    lib().oracle_hllc(ctypes.byref(p), _ptr(qL), _ptr(qR), _ptr(F), _ptr(sp))
+    return F, tuple(sp)
+
+
+def hllc_core(p, qL, qR, SL, SR):
+    """HLLC flux with the outer wave speeds given.  Returns (flux, S*)."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    F, sst = np.zeros(4), ctypes.c_double()
+    lib().oracle_hllc_core(ctypes.byref(p), _ptr(qL), _ptr(qR), float(SL), float(SR), _ptr(F), ctypes.byref(sst))
+    return F, sst.value
 
 
 def num_threads():

@@ -32,6 +32,7 @@ typedef struct {
   double riemann_tol;
   double small_dens, small_pres;       /* floors applied to working copies only */
   double grav;                         /* constant gravitational acceleration along y (0: none) */
+  int riemann_solver;                  /* 0 two-shock iteration, 1 HLLC */
 } oracle_params;
 
 typedef struct {
@@ -64,6 +65,12 @@ void oracle_trace(const oracle_params* p, double sigma, const double q[4], const
 int oracle_riemann(const oracle_params* p, const double qL[4], const double qR[4], double guess, double face[4],
                    double flux[4], double* pstar, double* ustar, int* iters);
 void oracle_euler_flux(const oracle_params* p, const double q[4], double F[4]);
+/* HLLC flux in the face frame (Toro 1997): oracle_hllc bounds the outer waves by the sound speeds of both
+ * sides (Davis) and returns (S_L, S*, S_R) in speeds when not NULL; oracle_hllc_core takes S_L and S_R as
+ * given and returns S* in *sstar when not NULL. */
+void oracle_hllc(const oracle_params* p, const double qL[4], const double qR[4], double flux[4], double speeds[3]);
+void oracle_hllc_core(const oracle_params* p, const double qL[4], const double qR[4], double SL, double SR,
+                      double flux[4], double* sstar);
 
 int oracle_num_threads(void);
 

@@ -50,6 +50,13 @@ MUTATIONS = {
          "const double h = (p->xmax - p->xmin) / nx;")],
     "split: no ghost fill between the sweeps": [
         ("  if (!err) err = oracle_fill_ghost(p, U);\n  if (!err) err = sweep", "  if (!err) err = sweep")],
+    "hllc: star energy term": [
+        ("f * (El / rl + (sst - ul) * (sst + pl / (rl * (SL - ul))))",
+         "f * (El / rl + (sst - ul) * (sst - pl / (rl * (SL - ul))))")],
+    "hllc: contact speed with the pressure jump reversed": [
+        ("double sst = (pr - pl + rl * ul", "double sst = (pl - pr + rl * ul")],
+    "hllc: left speed from the left state only": [
+        ("double SL = fmin(qL[1] - cl, qR[1] - cr);", "double SL = qL[1] - cl;")],
     "split: flux difference reversed": [
         ("C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m] - G[k * (N + 1) + m + 1]);",
          "C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m + 1] - G[k * (N + 1) + m]);")],
@@ -74,7 +81,8 @@ def test_pins_catch_the_planted_mistake(name):
         open(path, "w").write(src)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
                             "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py",
-                            "tests/test_oracle_gravity.py", "tests/test_oracle_split.py"],
+                            "tests/test_oracle_gravity.py", "tests/test_oracle_split.py",
+                            "tests/test_oracle_hllc.py"],
                            cwd=d, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
         assert "FAILED" in r.stdout
