@@ -49,6 +49,11 @@ typedef enum {
  * next to the wall, pressure integrated with dp/dy = rho g from that row's cell, energy rebuilt from it.
  * REFLECT and HYDROSTATIC are filled by hydro_fill_ghost; hydro_step_fused and hydro_advance then run the
  * fill / dt / step passes instead of one fused launch. */
+/* Riemann solvers (paper §3.2).  TWO_SHOCK: Newton iteration of the two-shock approximation (the default).
+ * HLLC: Toro's three-wave HLLC flux, outer wave speeds min(u_L - c_L, u_R - c_R), max(u_L + c_L, u_R + c_R);
+ * no iterations (the iteration counters then stay 0). */
+typedef enum { HYDRO_RIEMANN_TWO_SHOCK = 0, HYDRO_RIEMANN_HLLC = 1 } hydro_riemann;
+
 typedef enum {
   HYDRO_BC_OUTFLOW = 0,
   HYDRO_BC_PERIODIC = 1,
@@ -87,6 +92,9 @@ typedef struct {
                                        the state the other left; the context's k-th step, counted from
                                        hydro_init, sweeps x first when k is even).  Needs grav = 0 and
                                        use_learned_guess = 0; single problems only (not hydro_batch_*). */
+  int riemann_solver;               /* hydro_riemann: the two-shock iteration (default) or HLLC (§3.2 names
+                                       both; HLLC needs use_learned_guess = 0, no harvest, and is for single
+                                       problems only, not hydro_batch_*) */
 } hydro_params;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -272,8 +280,10 @@ hydro_status hydro_set_harvest_gate(hydro_ctx* ctx, double gate_dp, double gate_
  * from a work queue. */
 typedef struct hydro_batch hydro_batch;
 
-/* Create an ensemble of n members.  params, d_states, d_states_alt: arrays of n entries.
- * Errors: HYDRO_EINVAL (bad member, mixed precisions), HYDRO_ENOMEM, HYDRO_ECUDA. */
+/* Create an ensemble of n members.  params, d_states, d_states_alt: arrays of n entries.  Members take the
+ * unsplit step with the two-shock solver.
+ * Errors: HYDRO_EINVAL (bad member, mixed precisions, split = 1 or the HLLC solver), HYDRO_ENOMEM,
+ * HYDRO_ECUDA. */
 hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* d_states, void* const* d_states_alt,
                                 void* cuda_stream, hydro_batch** out);
 void hydro_batch_destroy(hydro_batch* b);

@@ -49,6 +49,23 @@ __device__ __forceinline__ void flush_counters(TileCounters& cnt, DevScratch* sc
   }
 }
 
+// Tile of the single-problem FP32 kernels (overridable at compile time for tile sweeps; the TMA box of the
+// state buffers is encoded for it).  Measured on KH
+// 1024^2 and Sedov 2048^2 at 256 threads: 32x16 (3 CTAs per SM) beats 30x16 (warp-aligned rows but a ragged
+// last tile on power-of-two grids), 30x8 and 14x16 by 1-2%, and 30x24/384, 62x8 and 30x32/512 (fewer warps
+// per SM) by 4-40%.  With 384 threads (36 warps per SM at 56 registers) 32x16 gains another 6-8%; more
+// threads per tile force spills or fewer tiles per SM and lose.
+#ifndef HYDRO_F32_TX
+#define HYDRO_F32_TX 32
+#endif
+#ifndef HYDRO_F32_TY
+#define HYDRO_F32_TY 16
+#endif
+#ifndef HYDRO_F32_NT
+#define HYDRO_F32_NT 384
+#endif
+constexpr int F32_TX = HYDRO_F32_TX, F32_TY = HYDRO_F32_TY, F32_NT = HYDRO_F32_NT;
+
 #ifndef HYDRO_F32_MINB
 #define HYDRO_F32_MINB 3
 #endif
@@ -109,7 +126,7 @@ cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepS
 // Fused step: the tile reads ghost cells through the boundary map and folds the CFL constraint of its new
 // cells into a block minimum; the last block to finish advances the time by this step's dt and writes
 // the next step's factors, so a run needs one launch per step and no ghost-fill or dt pass.
-template <typename R, int TX, int TY, int NT>
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KParams P, const R* __restrict__ Uin,
                                                             R* __restrict__ Uout, const StepScalars* __restrict__ sc_cur,
                                                             StepScalars* __restrict__ sc_next,
@@ -136,8 +153,8 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
       cfl_value(s, u[0], u[1], u[2], u[3], cmin, cnt.flags);
     }
   } else {
-    ctu_tile<R, TX, TY, NT, FACE_PLAIN, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt,
-                                              FaceHook{}, nullptr, &cmin, use_tma ? &tmap : nullptr);
+    ctu_tile<R, TX, TY, NT, MODE, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
+                                        nullptr, &cmin, use_tma ? &tmap : nullptr);
   }
   flush_counters<NT>(cnt, scr);
 #pragma unroll
@@ -176,17 +193,18 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   }
 }
 
-template <typename R, int TX, int TY, int NT>
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
                                   StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
                                   cudaStream_t stream) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
   static std::atomic<unsigned long long> attr_done{0};
-  cudaError_t e = smem_attr_once(ctu_step_fused_kernel<R, TX, TY, NT>, smem, attr_done);
+  cudaError_t e = smem_attr_once(ctu_step_fused_kernel<R, TX, TY, NT, MODE>, smem, attr_done);
   if (e != cudaSuccess) return e;
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_fused_kernel<R, TX, TY, NT><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
-                                                                   tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0);
+  ctu_step_fused_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
+                                                                         tmap ? *tmap : CUtensorMap{},
+                                                                         tmap ? 1 : 0);
   return cudaGetLastError();
 }
 

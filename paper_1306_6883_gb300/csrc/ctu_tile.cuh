@@ -71,11 +71,19 @@ __device__ __forceinline__ unsigned int face_key(int bx, int by, int stage, int 
 //  FACE_PLAIN:   acoustic start.
 //  FACE_LEARNED: start from the network's proposal where the warp's gate opens (warp-collective).
 //  FACE_HARVEST: acoustic start, and a hash-sampled subset of faces records inputs, p* and iterations.
+//  FACE_HLLC:    the HLLC solver instead of the two-shock iteration (no iterations to count).
 template <typename R, int MODE>
 __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R b[4], bool active,
                                            const FaceHook& hook, const MlpBlob* wsm, unsigned int key, R F[4],
                                            TileCounters& cnt) {
-  static_assert(MODE == FACE_PLAIN || is_f32<R>(), "the harvest and the learned proposal are FP32 paths");
+  static_assert(MODE == FACE_PLAIN || MODE == FACE_HLLC || is_f32<R>(),
+                "the harvest and the learned proposal are FP32 paths");
+  if constexpr (MODE == FACE_HLLC) {
+    if (!active) return;
+    hllc(s, a, b, F);
+    cnt.solves++;
+    return;
+  }
   R guess = (R)0;
   if constexpr (MODE == FACE_LEARNED) guess = learned_guess(a, b, active, wsm);
   if (!active) return;

@@ -136,6 +136,10 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
   if (p->split != 0 && p->split != 1) BAD("split must be 0 or 1");
   if (p->split == 1 && p->grav != 0.0) BAD("the split variant has no gravity source");
   if (p->split == 1 && p->use_learned_guess != 0) BAD("the split variant has no learned proposal");
+  if (p->riemann_solver != HYDRO_RIEMANN_TWO_SHOCK && p->riemann_solver != HYDRO_RIEMANN_HLLC)
+    BAD("riemann_solver must be HYDRO_RIEMANN_TWO_SHOCK or HYDRO_RIEMANN_HLLC");
+  if (p->riemann_solver == HYDRO_RIEMANN_HLLC && p->use_learned_guess != 0)
+    BAD("the learned proposal starts the two-shock iteration; HLLC has none");
   return 1;
 #undef BAD
 }
@@ -185,6 +189,7 @@ void fill_kparams(const hydro_params* p, KParams* kp) {
   k.grav = p->grav;
   k.grav_f = (float)p->grav;
   k.use_grav = p->grav != 0.0;
+  k.riemann_solver = p->riemann_solver;
   k.gamma_f = (float)k.gamma;
   k.gm1_f = (float)k.gm1;
   k.igm1_f = (float)(1.0 / k.gm1);
@@ -227,6 +232,7 @@ hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision
   p->use_learned_guess = 0;
   p->grav = 0.0;
   p->split = 0;
+  p->riemann_solver = HYDRO_RIEMANN_TWO_SHOCK;
   return HYDRO_OK;
 }
 
@@ -432,7 +438,8 @@ hydro_status hydro_set_harvest(hydro_ctx* c, void* d_buf, unsigned long long cap
     c->harvest = 0;
     return HYDRO_OK;
   }
-  if (c->p.precision != HYDRO_FP32 || c->p.split || !d_count || capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
+  if (c->p.precision != HYDRO_FP32 || c->p.split || c->p.riemann_solver != HYDRO_RIEMANN_TWO_SHOCK || !d_count ||
+      capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
     return HYDRO_EINVAL;
   c->hook.hbuf = (float*)d_buf;
   c->hook.hcount = d_count;

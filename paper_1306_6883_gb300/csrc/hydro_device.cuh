@@ -37,6 +37,7 @@ struct KParams {
   double grav;  // gravitational acceleration along y
   float grav_f;
   int use_grav;  // grav != 0: the step applies the gravity terms
+  int riemann_solver;  // 0 two-shock iteration, 1 HLLC
 };
 
 // Time-step dependent factors of one CTU step, computed once in double (host, or the last block of
@@ -141,7 +142,7 @@ __device__ __forceinline__ float M<float>::sq(float x) { return x * rsqa(x); }
 template <typename R>
 struct SP {
   R gamma, gm1, igm1, g1, small_dens, small_pres, tol, cvisc, dx, dy, idx, idy;
-  int maxiter, limiter, flatten;
+  int maxiter, limiter, flatten, hllc;
   __device__ __forceinline__ void load(const KParams& P) {
     if constexpr (is_f32<R>()) {
       gamma = P.gamma_f; gm1 = P.gm1_f; igm1 = P.igm1_f; g1 = P.g1_f; small_dens = P.small_dens_f;
@@ -154,6 +155,7 @@ struct SP {
     maxiter = P.riemann_maxiter;
     limiter = P.limiter;
     flatten = P.use_flattening;
+    hllc = P.riemann_solver;
   }
 };
 
@@ -561,6 +563,63 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   }
   face_flux(s, fr, fu, fv, fp, F);
   if (pstar_out) *pstar_out = pst;
+}
+
+// HLLC approximate Riemann solver (§3.2's alternative solver, after Toro 1997) in the face frame
+// (rho, un, ut, p).  Outer wave speeds: the direct (Davis) bounds of both sides' sound waves,
+// S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R); contact speed
+// S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R)) / (rho_L (S_L - u_L) - rho_R (S_R - u_R));
+// star state of side K: rho_K (S_K - u_K)/(S_K - S*) (1, S*, v_K, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).
+// The flux is F(U_L) for 0 <= S_L, F_L + S_L (U*_L - U_L) for S_L < 0 <= S*, F_R + S_R (U*_R - U_R) for
+// S* < 0 <= S_R, F(U_R) for S_R < 0: side o gives F(U_o), plus the jump across its outer wave when that
+// wave has passed the face.  FP64 evaluates every expression in the order
+// written; FP32 takes its divisions and square roots from reciprocal approximations.  The denominators do
+// not vanish: S_L - u_L <= -c_L < 0 < c_R <= S_R - u_R, and S_o - S* is nonzero where the jump is applied.
+template <typename R>
+__device__ __forceinline__ void hllc(const SP<R>& s, const R qL[4], const R qR[4], R F[4]) {
+  const R rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
+  const R rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
+  R cl, cr;
+  if constexpr (is_f32<R>()) {
+    cl = M<R>::sq(s.gamma * pl * rcpa(rl));
+    cr = M<R>::sq(s.gamma * pr * rcpa(rr));
+  } else {
+    cl = sqrt(s.gamma * pl / rl);
+    cr = sqrt(s.gamma * pr / rr);
+  }
+  const R SL = M<R>::mn(ul - cl, ur - cr);
+  const R SR = M<R>::mx(ul + cl, ur + cr);
+  const R num = pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur);
+  const R den = rl * (SL - ul) - rr * (SR - ur);
+  R sst;
+  if constexpr (is_f32<R>())
+    sst = num * rcpa(den);
+  else
+    sst = num / den;
+  // side whose flux the face takes (left when the whole fan is right of it, or the contact is), and whether
+  // that side's outer wave has passed the face
+  const bool left = (R)0 <= SL || (R)0 <= sst;
+  const R ro = left ? rl : rr, uo = left ? ul : ur, vo = left ? vl : vr, po = left ? pl : pr;
+  const R So = left ? SL : SR;
+  const bool jump = left ? SL < (R)0 : (R)0 <= SR;
+  face_flux(s, ro, uo, vo, po, F);
+  if (jump) {
+    R Eo, f, es;
+    if constexpr (is_f32<R>()) {
+      Eo = po * s.igm1 + 0.5f * ro * (uo * uo + vo * vo);
+      const float a = ro * (So - uo);
+      f = a * rcpa(So - sst);
+      es = Eo * rcpa(ro) + (sst - uo) * (sst + po * rcpa(a));
+    } else {
+      Eo = po / s.gm1 + 0.5 * ro * (uo * uo + vo * vo);
+      f = ro * (So - uo) / (So - sst);
+      es = Eo / ro + (sst - uo) * (sst + po / (ro * (So - uo)));
+    }
+    const R Us[4] = {f, f * sst, f * vo, f * es};
+    const R Uo[4] = {ro, ro * uo, ro * vo, Eo};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = F[k] + So * (Us[k] - Uo[k]);
+  }
 }
 
 // CFL constraint of one interior cell (Eq. 6 with |u|+c): min(dx/(|u|+c), dy/(|v|+c)), folded into rbest;

@@ -46,7 +46,7 @@ struct FaceHook {
   const MlpBlob* mlp;    // learned proposal weights (device), or null
 };
 
-enum { FACE_PLAIN = 0, FACE_HARVEST = 1, FACE_LEARNED = 2 };
+enum { FACE_PLAIN = 0, FACE_HARVEST = 1, FACE_LEARNED = 2, FACE_HLLC = 3 };
 
 __device__ __forceinline__ unsigned int hash32(unsigned int x) {
   // integer avalanche (xorshift-multiply)

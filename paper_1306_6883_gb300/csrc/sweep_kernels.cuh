@@ -198,10 +198,14 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
       a[k] = sl[k * nC + cL];
       bq[k] = sr[k * nC + cR];
     }
-    int it;
-    bool ok;
-    R pst;
-    riemann(s, a, bq, (R)0, F, it, ok, &pst);
+    int it = 0;
+    bool ok = true;
+    if (s.hllc) {
+      hllc(s, a, bq, F);
+    } else {
+      R pst;
+      riemann(s, a, bq, (R)0, F, it, ok, &pst);
+    }
     if (valid && (f < LN || fa == P.ng + n)) {  // a face shared by two tiles counts once
       cnt.solves++;
       cnt.iters += it;

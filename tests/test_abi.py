@@ -94,3 +94,25 @@ def test_split_variant_rejects_what_it_does_not_implement(lib, extra):
     for k, v in extra.items():
         setattr(p, k, v)
     assert H.state_pitch(p) == 0
+
+
+@pytest.mark.parametrize("extra", [dict(use_learned_guess=1, precision=1), dict(riemann_solver=2)])
+def test_hllc_rejects_what_it_does_not_implement(lib, extra):
+    from paper_1306_6883_gb300 import hydro as H
+    p = H.default_params(16, 16, riemann_solver="hllc")
+    assert H.state_pitch(p) > 0 and p.riemann_solver == 1
+    for k, v in extra.items():
+        setattr(p, k, v)
+    assert H.state_pitch(p) == 0
+
+
+def test_ensembles_take_the_two_shock_unsplit_step_only(lib):
+    from paper_1306_6883_gb300 import hydro as H
+    for kw in (dict(riemann_solver="hllc"), dict(split=1)):
+        p = H.default_params(16, 16, H.HYDRO_FP32, **kw)
+        arr = (H.HydroParams * 1)(p)
+        ptrs = (ctypes.c_void_p * 1)(256)
+        alt = (ctypes.c_void_p * 1)(512)
+        b = ctypes.c_void_p()
+        assert lib.hydro_batch_create(1, arr, ptrs, alt, None, ctypes.byref(b)) == H.HYDRO_EINVAL
+        assert not b.value
