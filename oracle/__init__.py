@@ -25,7 +25,7 @@ class OracleParams(ctypes.Structure):
         ("limiter", ctypes.c_int), ("use_flattening", ctypes.c_int), ("cvisc", ctypes.c_double),
         ("riemann_maxiter", ctypes.c_int), ("riemann_tol", ctypes.c_double),
         ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double), ("grav", ctypes.c_double),
-        ("riemann_solver", ctypes.c_int),
+        ("riemann_solver", ctypes.c_int), ("reconstruction", ctypes.c_int),
     ]
 
 
@@ -59,6 +59,8 @@ def lib():
         L.oracle_trace.argtypes = [P, ctypes.c_double, _D, _D, _D, _D]
         L.oracle_riemann.argtypes = [P, _D, _D, ctypes.c_double, _D, _D, _D, _D, ctypes.POINTER(ctypes.c_int)]
         L.oracle_euler_flux.argtypes = [P, _D, _D]
+        L.oracle_ppm_edges.argtypes = [_D, ctypes.c_double, _D]
+        L.oracle_trace_ppm.argtypes = [P, ctypes.c_double, _D, _D, _D, _D, _D]
         L.oracle_hllc.argtypes = [P, _D, _D, _D, _D]
         L.oracle_hllc_core.argtypes = [P, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D]
         L.oracle_num_threads.restype = ctypes.c_int
@@ -68,14 +70,17 @@ def lib():
 
 def params(nx, ny, *, ng=4, xmin=0.0, xmax=1.0, ymin=0.0, ymax=1.0, gamma=1.4, cfl=0.8,
            bc=("outflow", "outflow", "outflow", "outflow"), limiter=2, use_flattening=1, cvisc=0.1,
-           riemann_maxiter=32, riemann_tol=1e-14, small_dens=1e-10, small_pres=1e-20, grav=0.0, riemann_solver=0):
-    """riemann_solver: 0 (or "two-shock") the two-shock iteration, 1 (or "hllc") HLLC."""
+           riemann_maxiter=32, riemann_tol=1e-14, small_dens=1e-10, small_pres=1e-20, grav=0.0, riemann_solver=0,
+           reconstruction=0):
+    """riemann_solver: 0 (or "two-shock") the two-shock iteration, 1 (or "hllc") HLLC.
+    reconstruction: 0 (or "plm") piecewise linear, 1 (or "ppm") piecewise parabolic."""
     code = {"outflow": 0, "periodic": 1, "reflect": 2, "hydrostatic": 3}
     solver = {"two-shock": 0, "hllc": 1}.get(riemann_solver, riemann_solver)
+    recon = {"plm": 0, "ppm": 1}.get(reconstruction, reconstruction)
     return OracleParams(nx, ny, ng, xmin, xmax, ymin, ymax, gamma, cfl,
                         code[bc[0]], code[bc[1]], code[bc[2]], code[bc[3]],
                         limiter, use_flattening, cvisc, riemann_maxiter, riemann_tol, small_dens, small_pres, grav,
-                        solver)
+                        solver, recon)
 
 
 def _ptr(a):
@@ -168,6 +173,22 @@ def euler_flux(p, q):
     F = np.zeros(4)
     lib().oracle_euler_flux(ctypes.byref(p), _ptr(q), _ptr(F))
     return F
+
+
+def ppm_edges(a5, xi=1.0):
+    """PPM edge values (aL, aR) of the middle cell of five cell averages."""
+    a5 = np.ascontiguousarray(a5, dtype=np.float64)
+    e = np.zeros(2)
+    lib().oracle_ppm_edges(_ptr(a5), float(xi), _ptr(e))
+    return e[0], e[1]
+
+
+def trace_ppm(p, sigma, q, aL, aR):
+    """PPM traced states (left at i+1/2, right at i-1/2) of one cell in the face frame."""
+    q, aL, aR = (np.ascontiguousarray(x, dtype=np.float64) for x in (q, aL, aR))
+    ql, qr = np.zeros(4), np.zeros(4)
+    lib().oracle_trace_ppm(ctypes.byref(p), float(sigma), _ptr(q), _ptr(aL), _ptr(aR), _ptr(ql), _ptr(qr))
+    return ql, qr
 
 
 def hllc(p, qL, qR):

@@ -51,6 +51,7 @@ static int params_ok(const oracle_params* p) {
   if (p->limiter < 0 || p->limiter > 2) return 0;
   if (p->riemann_maxiter < 1 || !(p->riemann_tol > 0.0)) return 0;
   if (p->riemann_solver != 0 && p->riemann_solver != 1) return 0;
+  if (p->reconstruction != 0 && p->reconstruction != 1) return 0;
   if (!(p->small_dens > 0.0) || !(p->small_pres > 0.0) || p->cvisc < 0.0) return 0;
   return 1;
 }
@@ -176,6 +177,127 @@ void oracle_trace(const oracle_params* p, double sigma, const double q[4], const
   if (qR[0] < p->small_dens) qR[0] = p->small_dens;
   if (qL[3] < p->small_pres) qL[3] = p->small_pres;
   if (qR[3] < p->small_pres) qR[3] = p->small_pres;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Piecewise-parabolic reconstruction, the upgrade of the piecewise-linear one the paper points to (§3.2:
+ * PPM of Colella & Woodward 1984, tracing as discussed by Miller & Colella 2002).  Edge values of cell i
+ * from the cell averages a = (a_{i-2}, ..., a_{i+2}) of one primitive variable along one direction:
+ *   interface value a_{i+1/2} = a_i + (a_{i+1} - a_i)/2 - (da_{i+1} - da_i)/6 with da the MC-limited slopes
+ *     (for unlimited slopes the fourth-order 7/12 (a_i + a_{i+1}) - 1/12 (a_{i-1} + a_{i+2}));
+ *   aL = a_{i-1/2}, aR = a_{i+1/2}, then the monotonicity constraints: at a local extremum,
+ *     (aR - a_i)(a_i - aL) <= 0, the profile is flat, aL = aR = a_i; otherwise if the parabola's extremum
+ *     falls inside the cell, (aR - aL)(a_i - (aL + aR)/2) > (aR - aL)^2 / 6 moves it to the left edge,
+ *     aL = 3 a_i - 2 aR, and -(aR - aL)^2 / 6 > (aR - aL)(a_i - (aL + aR)/2) to the right one, aR = 3 a_i - 2 aL;
+ *   flattening blends the edges with the cell average: aL = xi aL + (1 - xi) a_i, likewise aR.
+ * edges[0] = aL, edges[1] = aR. */
+void oracle_ppm_edges(const double a[5], double xi, double edges[2]) {
+  double dm = mc_slope(a[0], a[1], a[2]);
+  double d0 = mc_slope(a[1], a[2], a[3]);
+  double dp = mc_slope(a[2], a[3], a[4]);
+  double c = a[2];
+  double l = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) / 6.0;
+  double r = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) / 6.0;
+  if ((r - c) * (c - l) <= 0.0) {
+    l = c;
+    r = c;
+  } else {
+    double da = r - l, mid = c - 0.5 * (l + r);
+    if (da * mid > da * da / 6.0)
+      l = 3.0 * c - 2.0 * r;
+    else if (-(da * da) / 6.0 > da * mid)
+      r = 3.0 * c - 2.0 * l;
+  }
+  edges[0] = xi * l + (1.0 - xi) * c;
+  edges[1] = xi * r + (1.0 - xi) * c;
+}
+
+/* PPM characteristic tracing (Eq. 13 with parabolic profiles).  In the cell, a(x) = aL + x (da + a6 (1 - x))
+ * for x in [0, 1] with da = aR - aL, a6 = 6 (a_i - (aL + aR)/2).  The average over the fraction s of the cell
+ * next to the right edge is Ip(s) = aR - (s/2)(da - (1 - 2s/3) a6), next to the left edge
+ * Im(s) = aL + (s/2)(da + (1 - 2s/3) a6).  A wave of speed lam reaches the right face from the region of
+ * width s = sigma lam (sigma = dt/dx) in a step.  Left state at i+1/2: reference ref = Ip(max(sigma lam4, 0))
+ * (the fastest right-moving wave; the edge value if none moves right), then for each wave with lam_nu >= 0
+ * subtract its part of ref - Ip(sigma lam_nu): qL = ref - sum_nu (l_nu . (ref - Ip(sigma lam_nu))) r_nu.
+ * Right state at i-1/2 likewise with Im, ref = Im(max(-sigma lam1, 0)) and the waves with lam_nu <= 0.
+ * Eigenvectors and floors as in oracle_trace.  With a linear profile (a6 = 0, aR - aL = dq) this is
+ * oracle_trace with the slope dq. */
+void oracle_trace_ppm(const oracle_params* p, double sigma, const double q[4], const double aL[4], const double aR[4],
+                      double qL[4], double qR[4]) {
+  double rho = q[0], un = q[1], pres = q[3];
+  double c = sqrt(p->gamma * pres / rho);
+  double lam[4] = {un - c, un, un, un + c};
+  double l[4][4] = {{0.0, -0.5 * rho / c, 0.0, 0.5 / (c * c)},
+                    {1.0, 0.0, 0.0, -1.0 / (c * c)},
+                    {0.0, 0.0, 1.0, 0.0},
+                    {0.0, 0.5 * rho / c, 0.0, 0.5 / (c * c)}};
+  double r[4][4] = {{1.0, -c / rho, 0.0, c * c}, {1.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 1.0, 0.0}, {1.0, c / rho, 0.0, c * c}};
+  double da[4], a6[4];
+  for (int m = 0; m < 4; ++m) {
+    da[m] = aR[m] - aL[m];
+    a6[m] = 6.0 * (q[m] - 0.5 * (aL[m] + aR[m]));
+  }
+  /* left state at i+1/2 */
+  {
+    double s4 = sigma * lam[3] > 0.0 ? sigma * lam[3] : 0.0;
+    double ref[4], out[4];
+    for (int m = 0; m < 4; ++m) {
+      ref[m] = aR[m] - 0.5 * s4 * (da[m] - (1.0 - (2.0 / 3.0) * s4) * a6[m]);
+      out[m] = ref[m];
+    }
+    for (int nu = 0; nu < 4; ++nu) {
+      if (!(lam[nu] >= 0.0)) continue;
+      double sn = sigma * lam[nu];
+      double beta = 0.0;
+      for (int m = 0; m < 4; ++m) {
+        double ip = aR[m] - 0.5 * sn * (da[m] - (1.0 - (2.0 / 3.0) * sn) * a6[m]);
+        beta += l[nu][m] * (ref[m] - ip);
+      }
+      for (int m = 0; m < 4; ++m) out[m] -= beta * r[nu][m];
+    }
+    for (int m = 0; m < 4; ++m) qL[m] = out[m];
+  }
+  /* right state at i-1/2 */
+  {
+    double s1 = -sigma * lam[0] > 0.0 ? -sigma * lam[0] : 0.0;
+    double ref[4], out[4];
+    for (int m = 0; m < 4; ++m) {
+      ref[m] = aL[m] + 0.5 * s1 * (da[m] + (1.0 - (2.0 / 3.0) * s1) * a6[m]);
+      out[m] = ref[m];
+    }
+    for (int nu = 0; nu < 4; ++nu) {
+      if (!(lam[nu] <= 0.0)) continue;
+      double sn = -sigma * lam[nu];
+      double beta = 0.0;
+      for (int m = 0; m < 4; ++m) {
+        double im = aL[m] + 0.5 * sn * (da[m] + (1.0 - (2.0 / 3.0) * sn) * a6[m]);
+        beta += l[nu][m] * (ref[m] - im);
+      }
+      for (int m = 0; m < 4; ++m) out[m] -= beta * r[nu][m];
+    }
+    for (int m = 0; m < 4; ++m) qR[m] = out[m];
+  }
+  if (qL[0] < p->small_dens) qL[0] = p->small_dens;
+  if (qR[0] < p->small_dens) qR[0] = p->small_dens;
+  if (qL[3] < p->small_pres) qL[3] = p->small_pres;
+  if (qR[3] < p->small_pres) qR[3] = p->small_pres;
+}
+
+/* Traced states of one cell along one direction, in the face frame, from the selected reconstruction:
+ * piecewise linear (the limited slope dq) or piecewise parabolic (edges from the five cells a5[k][0..4]). */
+static void trace_cell(const oracle_params* p, double sigma, const double q[4], const double dq[4],
+                       const double a5[4][5], double xi, double qL[4], double qR[4]) {
+  if (p->reconstruction == 1) {
+    double aL[4], aR[4], e[2];
+    for (int k = 0; k < 4; ++k) {
+      oracle_ppm_edges(a5[k], xi, e);
+      aL[k] = e[0];
+      aR[k] = e[1];
+    }
+    oracle_trace_ppm(p, sigma, q, aL, aR, qL, qR);
+  } else {
+    oracle_trace(p, sigma, q, dq, qL, qR);
+  }
 }
 
 /* ------------------------------------------------------------------------------------------------ */
@@ -574,8 +696,16 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
     for (int i = 3; i < NX - 3; ++i) {
       double qc[4] = {AT(q, 0, j, i), AT(q, 1, j, i), AT(q, 2, j, i), AT(q, 3, j, i)};
       double dx4[4] = {AT(dqx, 0, j, i), AT(dqx, 1, j, i), AT(dqx, 2, j, i), AT(dqx, 3, j, i)};
+      double a5[4][5], b5[4][5]; /* the five cells along x and along y (face frame), for PPM */
+      for (int m = 0; m < 5; ++m) {
+        for (int k = 0; k < 4; ++k) a5[k][m] = AT(q, k, j, i - 2 + m);
+        b5[0][m] = AT(q, 0, j - 2 + m, i);
+        b5[1][m] = AT(q, 2, j - 2 + m, i);
+        b5[2][m] = AT(q, 1, j - 2 + m, i);
+        b5[3][m] = AT(q, 3, j - 2 + m, i);
+      }
       double ql[4], qr[4];
-      oracle_trace(p, sigx, qc, dx4, ql, qr);
+      trace_cell(p, sigx, qc, dx4, (const double(*)[5])a5, AT(xi, 0, j, i), ql, qr);
       if (p->grav != 0.0) { /* half-step gravity on v (transverse in x) */
         ql[2] = ql[2] + hdtg;
         qr[2] = qr[2] + hdtg;
@@ -586,7 +716,7 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
       }
       double qn[4] = {qc[0], qc[2], qc[1], qc[3]};
       double dy4[4] = {AT(dqy, 0, j, i), AT(dqy, 2, j, i), AT(dqy, 1, j, i), AT(dqy, 3, j, i)};
-      oracle_trace(p, sigy, qn, dy4, ql, qr);
+      trace_cell(p, sigy, qn, dy4, (const double(*)[5])b5, AT(xi, 0, j, i), ql, qr);
       if (p->grav != 0.0) { /* half-step gravity on v (normal in y) */
         ql[1] = ql[1] + hdtg;
         qr[1] = qr[1] + hdtg;
@@ -824,12 +954,13 @@ static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_s
                                              q[k * N + m + 1], q[k * N + m + 2]);
     /* 4. tracing */
     for (int m = 3; m < N - 3; ++m) {
-      double qc[4], d4[4], a[4], b[4];
+      double qc[4], d4[4], a[4], b[4], a5[4][5];
       for (int k = 0; k < 4; ++k) {
         qc[k] = q[k * N + m];
         d4[k] = dq[k * N + m];
+        for (int t = 0; t < 5; ++t) a5[k][t] = q[k * N + m - 2 + t];
       }
-      oracle_trace(p, sigma, qc, d4, a, b);
+      trace_cell(p, sigma, qc, d4, (const double(*)[5])a5, xi[m], a, b);
       for (int k = 0; k < 4; ++k) {
         ql[k * N + m] = a[k];
         qr[k * N + m] = b[k];

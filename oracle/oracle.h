@@ -33,6 +33,7 @@ typedef struct {
   double small_dens, small_pres;       /* floors applied to working copies only */
   double grav;                         /* constant gravitational acceleration along y (0: none) */
   int riemann_solver;                  /* 0 two-shock iteration, 1 HLLC */
+  int reconstruction;                  /* 0 piecewise linear (limiter applies), 1 piecewise parabolic */
 } oracle_params;
 
 typedef struct {
@@ -59,6 +60,12 @@ double oracle_slope(int limiter, double qm2, double qm1, double q0, double qp1, 
 double oracle_flatten_chi(double pm2, double pm1, double pp1, double pp2, double um1, double up1, double small_pres);
 void oracle_trace(const oracle_params* p, double sigma, const double q[4], const double dq[4], double qL[4],
                   double qR[4]);
+/* PPM: edge values (aL, aR) of the middle cell of a[0..4] after the monotonicity constraints and the
+ * flattening blend xi; tracing of the parabolic profiles (aL, aR, and the cell average q) of the four
+ * face-frame variables. */
+void oracle_ppm_edges(const double a[5], double xi, double edges[2]);
+void oracle_trace_ppm(const oracle_params* p, double sigma, const double q[4], const double aL[4], const double aR[4],
+                      double qL[4], double qR[4]);
 /* two-shock Riemann problem in the face frame: q = (rho, u_normal, u_transverse, p).
  * guess <= 0 selects the acoustic (linearised) initial guess.  Outputs the face state and the flux
  * (mass, normal momentum, transverse momentum, energy), the converged p* and u*, and the iteration count. */

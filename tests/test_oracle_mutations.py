@@ -57,6 +57,16 @@ MUTATIONS = {
         ("double sst = (pr - pl + rl * ul", "double sst = (pl - pr + rl * ul")],
     "hllc: left speed from the left state only": [
         ("double SL = fmin(qL[1] - cl, qR[1] - cr);", "double SL = qL[1] - cl;")],
+    "ppm: interface correction sign": [
+        ("double r = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) / 6.0;",
+         "double r = a[2] + 0.5 * (a[3] - a[2]) + (dp - d0) / 6.0;")],
+    "ppm: overshoot moved to the wrong edge": [("      l = 3.0 * c - 2.0 * r;", "      r = 3.0 * c - 2.0 * l;")],
+    "ppm: curvature term of the right-edge average": [
+        ("double ip = aR[m] - 0.5 * sn * (da[m] - (1.0 - (2.0 / 3.0) * sn) * a6[m]);",
+         "double ip = aR[m] - 0.5 * sn * (da[m] + (1.0 - (2.0 / 3.0) * sn) * a6[m]);")],
+    "ppm: reference state from the slowest wave": [
+        ("double s4 = sigma * lam[3] > 0.0 ? sigma * lam[3] : 0.0;",
+         "double s4 = sigma * lam[1] > 0.0 ? sigma * lam[1] : 0.0;")],
     "split: flux difference reversed": [
         ("C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m] - G[k * (N + 1) + m + 1]);",
          "C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m + 1] - G[k * (N + 1) + m]);")],
@@ -82,7 +92,7 @@ def test_pins_catch_the_planted_mistake(name):
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
                             "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py",
                             "tests/test_oracle_gravity.py", "tests/test_oracle_split.py",
-                            "tests/test_oracle_hllc.py"],
+                            "tests/test_oracle_hllc.py", "tests/test_oracle_ppm.py"],
                            cwd=d, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
         assert "FAILED" in r.stdout
