@@ -146,16 +146,24 @@ double oracle_flatten_chi(double pm2, double pm1, double pp1, double pp2, double
  * speed, q + (1 - sigma lam4) dq / 2, and add (sigma/2)(lam4 - lam_nu) beta_nu r_nu for each wave with
  * lam_nu >= 0 (moving toward that face).  Right state at the i-1/2 face: q - (1 + sigma lam1) dq / 2 plus
  * (sigma/2)(lam1 - lam_nu) beta_nu r_nu for each wave with lam_nu <= 0.  beta_nu = l_nu . dq. */
+static void eigenvectors(double rho, double c, double l[4][4], double r[4][4]) {
+  const double L[4][4] = {{0.0, -0.5 * rho / c, 0.0, 0.5 / (c * c)},
+                          {1.0, 0.0, 0.0, -1.0 / (c * c)},
+                          {0.0, 0.0, 1.0, 0.0},
+                          {0.0, 0.5 * rho / c, 0.0, 0.5 / (c * c)}};
+  const double R[4][4] = {{1.0, -c / rho, 0.0, c * c}, {1.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 1.0, 0.0},
+                          {1.0, c / rho, 0.0, c * c}};
+  memcpy(l, L, sizeof L);
+  memcpy(r, R, sizeof R);
+}
+
 void oracle_trace(const oracle_params* p, double sigma, const double q[4], const double dq[4], double qL[4],
                   double qR[4]) {
   double rho = q[0], un = q[1], pres = q[3];
   double c = sqrt(p->gamma * pres / rho);
   double lam[4] = {un - c, un, un, un + c};
-  double l[4][4] = {{0.0, -0.5 * rho / c, 0.0, 0.5 / (c * c)},
-                    {1.0, 0.0, 0.0, -1.0 / (c * c)},
-                    {0.0, 0.0, 1.0, 0.0},
-                    {0.0, 0.5 * rho / c, 0.0, 0.5 / (c * c)}};
-  double r[4][4] = {{1.0, -c / rho, 0.0, c * c}, {1.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 1.0, 0.0}, {1.0, c / rho, 0.0, c * c}};
+  double l[4][4], r[4][4];
+  eigenvectors(rho, c, l, r);
   double beta[4];
   for (int nu = 0; nu < 4; ++nu) {
     double s = 0.0;
@@ -227,11 +235,8 @@ void oracle_trace_ppm(const oracle_params* p, double sigma, const double q[4], c
   double rho = q[0], un = q[1], pres = q[3];
   double c = sqrt(p->gamma * pres / rho);
   double lam[4] = {un - c, un, un, un + c};
-  double l[4][4] = {{0.0, -0.5 * rho / c, 0.0, 0.5 / (c * c)},
-                    {1.0, 0.0, 0.0, -1.0 / (c * c)},
-                    {0.0, 0.0, 1.0, 0.0},
-                    {0.0, 0.5 * rho / c, 0.0, 0.5 / (c * c)}};
-  double r[4][4] = {{1.0, -c / rho, 0.0, c * c}, {1.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 1.0, 0.0}, {1.0, c / rho, 0.0, c * c}};
+  double l[4][4], r[4][4];
+  eigenvectors(rho, c, l, r);
   double da[4], a6[4];
   for (int m = 0; m < 4; ++m) {
     da[m] = aR[m] - aL[m];
