@@ -460,8 +460,13 @@ def run_ours(args, world, rank, local):
     e2e = time_e2e(pr, args.precision, max(args.steps // 4, 10), args.warmup)
     accuracy = fp32_error(pr) if args.precision == "fp32" else None
     ens = time_ensemble() if args.precision == "fp32" else None
-    rt = split = hllc = None
+    rt = split = hllc = ppm = None
     if args.precision == "fp32":
+        r = time_device_path(pr, "fp32", 20, args.warmup, flush, reconstruction=1)
+        ppm = {"workload": wname, "steps": 20, "value": zones * 20 / (sum(r["step_ms"]) / 1e3),
+               "ms_per_step": sum(r["step_ms"]) / 20, "launches_per_step": r["launches_per_step"],
+               "riemann_iters_per_solve": r["iters_per_solve"],
+               "step": "the fused unsplit step with piecewise-parabolic reconstruction"}
         r = time_device_path(pr, "fp32", 20, args.warmup, flush, riemann_solver=1)
         hllc = {"workload": wname, "steps": 20, "value": zones * 20 / (sum(r["step_ms"]) / 1e3),
                 "ms_per_step": sum(r["step_ms"]) / 20, "launches_per_step": r["launches_per_step"],
@@ -537,6 +542,7 @@ def run_ours(args, world, rank, local):
         "rayleigh_taylor": rt,
         "split_variant": split,
         "hllc_variant": hllc,
+        "ppm_variant": ppm,
         "learned_proposal": learned,
     }
     line["roofline"]["hbm_frac_of_measured"] = line["roofline"]["hbm_gbs"] / hbm

@@ -54,6 +54,12 @@ typedef enum {
  * no iterations (the iteration counters then stay 0). */
 typedef enum { HYDRO_RIEMANN_TWO_SHOCK = 0, HYDRO_RIEMANN_HLLC = 1 } hydro_riemann;
 
+/* Reconstruction of the interface states (paper §3.2).  PLM: limited linear profiles (the paper's method).
+ * PPM: Colella & Woodward's parabolic profiles (MC-limited interface values, monotonicity constraints,
+ * flattening toward the cell average) traced along the characteristics, the fastest wave's average as the
+ * reference state. */
+typedef enum { HYDRO_RECON_PLM = 0, HYDRO_RECON_PPM = 1 } hydro_recon;
+
 typedef enum {
   HYDRO_BC_OUTFLOW = 0,
   HYDRO_BC_PERIODIC = 1,
@@ -95,6 +101,9 @@ typedef struct {
   int riemann_solver;               /* hydro_riemann: the two-shock iteration (default) or HLLC (§3.2 names
                                        both; HLLC needs use_learned_guess = 0, no harvest, and is for single
                                        problems only, not hydro_batch_*) */
+  int reconstruction;               /* hydro_recon: piecewise linear (default; `limiter` applies) or
+                                       piecewise parabolic (the PPM upgrade §3.2 points to; `limiter` is
+                                       unused; same restrictions as HLLC) */
 } hydro_params;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -281,8 +290,8 @@ hydro_status hydro_set_harvest_gate(hydro_ctx* ctx, double gate_dp, double gate_
 typedef struct hydro_batch hydro_batch;
 
 /* Create an ensemble of n members.  params, d_states, d_states_alt: arrays of n entries.  Members take the
- * unsplit step with the two-shock solver.
- * Errors: HYDRO_EINVAL (bad member, mixed precisions, split = 1 or the HLLC solver), HYDRO_ENOMEM,
+ * unsplit piecewise-linear step with the two-shock solver.
+ * Errors: HYDRO_EINVAL (bad member, mixed precisions, split = 1, the HLLC solver or PPM), HYDRO_ENOMEM,
  * HYDRO_ECUDA. */
 hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* d_states, void* const* d_states_alt,
                                 void* cuda_stream, hydro_batch** out);

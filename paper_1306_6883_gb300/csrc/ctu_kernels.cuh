@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_kernel(KParams P
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // the network's weights are read from global memory (L1/L2-resident) only by warps whose gate opens,
   // which is rare in smooth flow, so no CTA pays to stage them
-  const MlpBlob* wsm = MODE == FACE_LEARNED ? hook.mlp : nullptr;
+  const MlpBlob* wsm = face_kind(MODE) == FACE_LEARNED ? hook.mlp : nullptr;
   SP<R> s;
   s.load(P);
   StepFactors<R> f;

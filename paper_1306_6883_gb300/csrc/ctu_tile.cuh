@@ -76,16 +76,17 @@ template <typename R, int MODE>
 __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R b[4], bool active,
                                            const FaceHook& hook, const MlpBlob* wsm, unsigned int key, R F[4],
                                            TileCounters& cnt) {
-  static_assert(MODE == FACE_PLAIN || MODE == FACE_HLLC || is_f32<R>(),
+  constexpr int K = face_kind(MODE);
+  static_assert(K == FACE_PLAIN || K == FACE_HLLC || is_f32<R>(),
                 "the harvest and the learned proposal are FP32 paths");
-  if constexpr (MODE == FACE_HLLC) {
+  if constexpr (K == FACE_HLLC) {
     if (!active) return;
     hllc(s, a, b, F);
     cnt.solves++;
     return;
   }
   R guess = (R)0;
-  if constexpr (MODE == FACE_LEARNED) guess = learned_guess(a, b, active, wsm);
+  if constexpr (K == FACE_LEARNED) guess = learned_guess(a, b, active, wsm);
   if (!active) return;
   int it;
   bool ok;
@@ -94,7 +95,7 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
   cnt.solves++;
   cnt.iters += it;
   cnt.nonconv += ok ? 0 : 1;
-  if constexpr (MODE == FACE_HARVEST) {
+  if constexpr (K == FACE_HARVEST) {
     if (hash32(key ^ hook.hseed) < hook.hthresh ||
         (hook.hgate_ratio > 0.f && strong_face(a, b, hook.hgate_ratio, hook.hgate_u4))) {
       const unsigned long long k = atomicAdd(hook.hcount, 1ull);
@@ -110,7 +111,8 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
 // One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
 // smem_raw must hold TileLayout<R, TX, TY>::bytes.  Starts and ends with a block-wide barrier-free
 // state, so consecutive calls by the same block need one __syncthreads() between them.  MODE selects
-// the face-solve variant (face_solve); wsm is the network's weights for FACE_LEARNED.  FUSED: ghost cells
+// the face-solve variant (face_solve) and, with RECON_PPM, piecewise-parabolic reconstruction in stage 2;
+// wsm is the network's weights for FACE_LEARNED.  FUSED: ghost cells
 // come from the boundary-condition map of the interior (no ghost fill needed) and the CFL constraint of
 // every new cell is folded into *cfl_min (no separate dt pass needed).  PERSIST: the block runs several
 // tiles in turn (a TMA tile load then first orders the previous tile's shared-memory accesses before it).
@@ -284,16 +286,28 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       constexpr int k1 = YD ? 2 : 1, k2 = YD ? 1 : 2;
       const int b = (c / SX + 3) * QP + c % SX + 3;
       const R xi = sxi[c];
-      R q[4], dq[4];
+      R q[4], ql[4], qrr[4];
+      if constexpr ((MODE & RECON_PPM) != 0) {
+        R eL[4], eR[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
-        const R* a = sq + k * QP * QY + b;
-        q[m] = a[0];
-        dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+        for (int m = 0; m < 4; ++m) {
+          const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
+          const R* a = sq + k * QP * QY + b;
+          q[m] = a[0];
+          ppm_edges<R>(a[-2 * st], a[-st], a[0], a[st], a[2 * st], xi, eL[m], eR[m]);
+        }
+        trace_ppm<R>(s, YD ? sigy : sigx, q, eL, eR, ql, qrr);
+      } else {
+        R dq[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
+          const R* a = sq + k * QP * QY + b;
+          q[m] = a[0];
+          dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+        }
+        trace<R>(s, YD ? sigy : sigx, q, dq, ql, qrr);
       }
-      R ql[4], qrr[4];
-      trace<R>(s, YD ? sigy : sigx, q, dq, ql, qrr);
       if (P.use_grav) {  // half-step gravity (the rho g source, §3.2) on v: normal in y, transverse in x
         constexpr int mg = YD ? 1 : 2;
         ql[mg] = ql[mg] + f.hdtg;

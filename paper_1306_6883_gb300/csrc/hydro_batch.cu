@@ -118,7 +118,7 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
   const int prec = params[0].precision;
   for (int i = 0; i < n; ++i) {
     if (hydro_state_pitch(&params[i]) == 0 || params[i].precision != prec || params[i].split ||
-        params[i].riemann_solver != HYDRO_RIEMANN_TWO_SHOCK)
+        params[i].riemann_solver != HYDRO_RIEMANN_TWO_SHOCK || params[i].reconstruction != HYDRO_RECON_PLM)
       return HYDRO_EINVAL;
     if (!d_states[i] || !d_states_alt[i] || ((uintptr_t)d_states[i] & 255) || ((uintptr_t)d_states_alt[i] & 255))
       return HYDRO_EINVAL;

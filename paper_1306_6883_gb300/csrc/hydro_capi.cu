@@ -140,6 +140,10 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
     BAD("riemann_solver must be HYDRO_RIEMANN_TWO_SHOCK or HYDRO_RIEMANN_HLLC");
   if (p->riemann_solver == HYDRO_RIEMANN_HLLC && p->use_learned_guess != 0)
     BAD("the learned proposal starts the two-shock iteration; HLLC has none");
+  if (p->reconstruction != HYDRO_RECON_PLM && p->reconstruction != HYDRO_RECON_PPM)
+    BAD("reconstruction must be HYDRO_RECON_PLM or HYDRO_RECON_PPM");
+  if (p->reconstruction == HYDRO_RECON_PPM && p->use_learned_guess != 0)
+    BAD("the learned proposal runs with the piecewise-linear step only");
   return 1;
 #undef BAD
 }
@@ -190,6 +194,7 @@ void fill_kparams(const hydro_params* p, KParams* kp) {
   k.grav_f = (float)p->grav;
   k.use_grav = p->grav != 0.0;
   k.riemann_solver = p->riemann_solver;
+  k.reconstruction = p->reconstruction;
   k.gamma_f = (float)k.gamma;
   k.gm1_f = (float)k.gm1;
   k.igm1_f = (float)(1.0 / k.gm1);
@@ -233,6 +238,7 @@ hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision
   p->grav = 0.0;
   p->split = 0;
   p->riemann_solver = HYDRO_RIEMANN_TWO_SHOCK;
+  p->reconstruction = HYDRO_RECON_PLM;
   return HYDRO_OK;
 }
 
@@ -438,8 +444,8 @@ hydro_status hydro_set_harvest(hydro_ctx* c, void* d_buf, unsigned long long cap
     c->harvest = 0;
     return HYDRO_OK;
   }
-  if (c->p.precision != HYDRO_FP32 || c->p.split || c->p.riemann_solver != HYDRO_RIEMANN_TWO_SHOCK || !d_count ||
-      capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
+  if (c->p.precision != HYDRO_FP32 || c->p.split || c->p.riemann_solver != HYDRO_RIEMANN_TWO_SHOCK ||
+      c->p.reconstruction != HYDRO_RECON_PLM || !d_count || capacity == 0 || !(rate > 0.0) || !(rate <= 1.0))
     return HYDRO_EINVAL;
   c->hook.hbuf = (float*)d_buf;
   c->hook.hcount = d_count;

@@ -38,6 +38,7 @@ struct KParams {
   float grav_f;
   int use_grav;  // grav != 0: the step applies the gravity terms
   int riemann_solver;  // 0 two-shock iteration, 1 HLLC
+  int reconstruction;  // 0 piecewise linear, 1 piecewise parabolic
 };
 
 // Time-step dependent factors of one CTU step, computed once in double (host, or the last block of
@@ -142,7 +143,7 @@ __device__ __forceinline__ float M<float>::sq(float x) { return x * rsqa(x); }
 template <typename R>
 struct SP {
   R gamma, gm1, igm1, g1, small_dens, small_pres, tol, cvisc, dx, dy, idx, idy;
-  int maxiter, limiter, flatten, hllc;
+  int maxiter, limiter, flatten, hllc, ppm;
   __device__ __forceinline__ void load(const KParams& P) {
     if constexpr (is_f32<R>()) {
       gamma = P.gamma_f; gm1 = P.gm1_f; igm1 = P.igm1_f; g1 = P.g1_f; small_dens = P.small_dens_f;
@@ -156,6 +157,7 @@ struct SP {
     limiter = P.limiter;
     flatten = P.use_flattening;
     hllc = P.riemann_solver;
+    ppm = P.reconstruction;
   }
 };
 
@@ -373,6 +375,151 @@ __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], con
   r3 = r3 < s.small_pres ? s.small_pres : r3;
   qL[0] = l0; qL[1] = l1; qL[2] = l2; qL[3] = l3;
   qR[0] = r0; qR[1] = r1; qR[2] = r2; qR[3] = r3;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Piecewise-parabolic reconstruction (PPM, Colella & Woodward 1984; the upgrade §3.2 points to).  Edges of
+// the middle cell of a0..a4 (one primitive variable along one direction): interface values
+// a_{i+1/2} = a_i + (a_{i+1} - a_i)/2 - (da_{i+1} - da_i)/6 from MC-limited slopes da; a local extremum
+// flattens the profile to the average; a parabola whose extremum falls inside the cell has it moved to the
+// nearer edge (aL = 3 a_i - 2 aR or aR = 3 a_i - 2 aL); flattening blends the edges toward the average.
+template <typename R>
+__device__ __forceinline__ void ppm_edges(R a0, R a1, R a2, R a3, R a4, R xi, R& eL, R& eR) {
+  const R dm = mc2(a0, a1, a2), d0 = mc2(a1, a2, a3), dp = mc2(a2, a3, a4);
+  const R c = a2;
+  R l, r;
+  if constexpr (is_f32<R>()) {
+    l = a1 + 0.5f * (a2 - a1) - (d0 - dm) * (1.0f / 6.0f);
+    r = a2 + 0.5f * (a3 - a2) - (dp - d0) * (1.0f / 6.0f);
+  } else {
+    l = a1 + 0.5 * (a2 - a1) - (d0 - dm) / 6.0;
+    r = a2 + 0.5 * (a3 - a2) - (dp - d0) / 6.0;
+  }
+  const bool flat = (r - c) * (c - l) <= (R)0;
+  const R da = r - l, mid = c - (R)0.5 * (l + r);
+  R d6;
+  if constexpr (is_f32<R>())
+    d6 = da * da * (1.0f / 6.0f);
+  else
+    d6 = da * da / 6.0;
+  const bool left_ex = da * mid > d6;
+  const bool right_ex = !left_ex && -(da * da) / (R)6 > da * mid;
+  const R l2 = flat ? c : (left_ex ? (R)3 * c - (R)2 * r : l);
+  const R r2 = flat ? c : (right_ex ? (R)3 * c - (R)2 * l : r);
+  eL = xi * l2 + ((R)1 - xi) * c;
+  eR = xi * r2 + ((R)1 - xi) * c;
+}
+
+// PPM characteristic tracing in the face frame.  The cell's profile is a(x) = aL + x (da + a6 (1 - x)) on
+// [0, 1], da = aR - aL, a6 = 6 (q - (aL + aR)/2); its average over the fraction s of the cell next to the
+// right edge is Ip(s) = aR - (s/2)(da - (1 - 2s/3) a6), next to the left edge Im(s) = aL + (s/2)(da + (1 - 2s/3) a6).
+// Left state at i+1/2: ref = Ip(max(sigma lam4, 0)), minus, for each wave with lam_nu >= 0, its component
+// (l_nu . (ref - Ip(sigma lam_nu))) r_nu; right state at i-1/2 with Im, ref = Im(max(-sigma lam1, 0)) and the
+// waves with lam_nu <= 0.  Eigenvectors as in trace (only their non-zero entries multiplied out, in the
+// order of the wave sums); floors on the results.
+template <typename R>
+__device__ __forceinline__ void trace_ppm(const SP<R>& s, R sigma, const R q[4], const R eL[4], const R eR[4],
+                                          R qL[4], R qR[4]) {
+  const R rho = q[0], un = q[1], pres = q[3];
+  R c, c2, roc, ic2h, ic2, cor;
+  if constexpr (is_f32<R>()) {
+    const float ir = rcpa(rho);
+    const float x = s.gamma * pres * ir;
+    const float ic = rsqa(x);
+    c = x * ic;
+    c2 = c * c;
+    roc = 0.5f * rho * ic;
+    ic2 = ic * ic;
+    ic2h = 0.5f * ic2;
+    cor = c * ir;
+  } else {
+    c = sqrt(s.gamma * pres / rho);
+    c2 = c * c;
+    roc = (0.5 * rho) / c;
+    ic2h = 0.5 / c2;
+    ic2 = 1.0 / c2;
+    cor = c / rho;
+  }
+  const R lam1 = un - c, lam2 = un, lam4 = un + c;
+  R da[4], a6[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    da[m] = eR[m] - eL[m];
+    a6[m] = (R)6 * (q[m] - (R)0.5 * (eL[m] + eR[m]));
+  }
+  const R two3 = (R)2 / (R)3;
+  // ---- left state at i+1/2
+  {
+    const R s4 = sigma * lam4 > (R)0 ? sigma * lam4 : (R)0;
+    R ref[4], o[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      ref[m] = eR[m] - (R)0.5 * s4 * (da[m] - ((R)1 - two3 * s4) * a6[m]);
+      o[m] = ref[m];
+    }
+    auto dif = [&](int m, R sn) { return ref[m] - (eR[m] - (R)0.5 * sn * (da[m] - ((R)1 - two3 * sn) * a6[m])); };
+    if (lam1 >= (R)0) {
+      const R sn = sigma * lam1;
+      const R b = -roc * dif(1, sn) + ic2h * dif(3, sn);
+      o[0] -= b;
+      o[1] -= b * (-cor);
+      o[3] -= b * c2;
+    }
+    if (lam2 >= (R)0) {
+      const R sn = sigma * lam2;
+      const R b2 = dif(0, sn) + (-ic2) * dif(3, sn);
+      o[0] -= b2;
+      const R b3 = dif(2, sn);
+      o[2] -= b3;
+    }
+    if (lam4 >= (R)0) {
+      const R sn = sigma * lam4;
+      const R b = roc * dif(1, sn) + ic2h * dif(3, sn);
+      o[0] -= b;
+      o[1] -= b * cor;
+      o[3] -= b * c2;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) qL[m] = o[m];
+  }
+  // ---- right state at i-1/2
+  {
+    const R s1 = -sigma * lam1 > (R)0 ? -sigma * lam1 : (R)0;
+    R ref[4], o[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      ref[m] = eL[m] + (R)0.5 * s1 * (da[m] + ((R)1 - two3 * s1) * a6[m]);
+      o[m] = ref[m];
+    }
+    auto dif = [&](int m, R sn) { return ref[m] - (eL[m] + (R)0.5 * sn * (da[m] + ((R)1 - two3 * sn) * a6[m])); };
+    if (lam1 <= (R)0) {
+      const R sn = -sigma * lam1;
+      const R b = -roc * dif(1, sn) + ic2h * dif(3, sn);
+      o[0] -= b;
+      o[1] -= b * (-cor);
+      o[3] -= b * c2;
+    }
+    if (lam2 <= (R)0) {
+      const R sn = -sigma * lam2;
+      const R b2 = dif(0, sn) + (-ic2) * dif(3, sn);
+      o[0] -= b2;
+      const R b3 = dif(2, sn);
+      o[2] -= b3;
+    }
+    if (lam4 <= (R)0) {
+      const R sn = -sigma * lam4;
+      const R b = roc * dif(1, sn) + ic2h * dif(3, sn);
+      o[0] -= b;
+      o[1] -= b * cor;
+      o[3] -= b * c2;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) qR[m] = o[m];
+  }
+  qL[0] = qL[0] < s.small_dens ? s.small_dens : qL[0];
+  qR[0] = qR[0] < s.small_dens ? s.small_dens : qR[0];
+  qL[3] = qL[3] < s.small_pres ? s.small_pres : qL[3];
+  qR[3] = qR[3] < s.small_pres ? s.small_pres : qR[3];
 }
 
 // ---------------------------------------------------------------------------------------------------

@@ -53,6 +53,18 @@ cudaError_t ctu_step_hllc_f64(const KParams& P, const double* Uin, double* Uout,
 cudaError_t ctu_step_fused_hllc_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
                                     StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
 
+// The same two launches with piecewise-parabolic reconstruction, with either solver (k_ctu_ppm.cu,
+// k_ctu_ppm_f64.cu); ctu_step and ctu_step_fused dispatch to them when P.reconstruction == 1.
+cudaError_t ctu_step_ppm(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
+                         const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, const CUtensorMap* tmap);
+cudaError_t ctu_step_fused_ppm(int precision, const KParams& P, const void* Uin, void* Uout,
+                               const StepScalars* sc_cur, StepScalars* sc_next, DevScratch* scr, double tmax,
+                               const CUtensorMap* tmap, cudaStream_t stream);
+cudaError_t ctu_step_ppm_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,
+                             const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
+cudaError_t ctu_step_fused_ppm_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
+                                   StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
+
 // Tile box of the FP32 single-problem step kernels (the TMA box is (F32_TILE_X + 8) x (F32_TILE_Y + 8) x 4).
 int f32_tile_x();
 int f32_tile_y();

@@ -9,6 +9,7 @@ int f32_tile_y() { return F32_TY; }
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
                            cudaStream_t stream) {
+  if (P.reconstruction == 1) return ctu_step_fused_ppm(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream);
   if (P.riemann_solver == 1) return ctu_step_fused_hllc(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream);
   if (precision == 0) return ctu_step_fused_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream);
   return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr,
@@ -18,6 +19,7 @@ cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, voi
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,
                      const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, int mode, const FaceHook* hook,
                      const CUtensorMap* tmap) {
+  if (P.reconstruction == 1) return ctu_step_ppm(precision, P, Uin, Uout, sc_host, sc_dev, scr, stream, tmap);
   if (P.riemann_solver == 1) return ctu_step_hllc(precision, P, Uin, Uout, sc_host, sc_dev, scr, stream, tmap);
   if (precision == 0) return ctu_step_f64(P, (const double*)Uin, (double*)Uout, sc_host, sc_dev, scr, stream);
   const FaceHook h = hook ? *hook : FaceHook{};

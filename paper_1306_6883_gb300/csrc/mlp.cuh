@@ -46,7 +46,10 @@ struct FaceHook {
   const MlpBlob* mlp;    // learned proposal weights (device), or null
 };
 
-enum { FACE_PLAIN = 0, FACE_HARVEST = 1, FACE_LEARNED = 2, FACE_HLLC = 3 };
+// Tile modes: the face-solve variant in the low two bits, and RECON_PPM for piecewise-parabolic
+// reconstruction instead of piecewise-linear.
+enum { FACE_PLAIN = 0, FACE_HARVEST = 1, FACE_LEARNED = 2, FACE_HLLC = 3, RECON_PPM = 4 };
+constexpr int face_kind(int mode) { return mode & 3; }
 
 __device__ __forceinline__ unsigned int hash32(unsigned int x) {
   // integer avalanche (xorshift-multiply)

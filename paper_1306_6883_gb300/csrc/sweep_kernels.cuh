@@ -166,15 +166,26 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
     }
     sxi[e] = xi;
     sun[e] = qn[b];
-    R q[4], dq[4];
+    R q[4], ql[4], qr[4];
+    if (s.ppm) {
+      R eL[4], eR[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const R* a = sq + k * nQ + b;
-      q[k] = a[0];
-      dq[k] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+      for (int k = 0; k < 4; ++k) {
+        const R* a = sq + k * nQ + b;
+        q[k] = a[0];
+        ppm_edges<R>(a[-2 * st], a[-st], a[0], a[st], a[2 * st], xi, eL[k], eR[k]);
+      }
+      trace_ppm<R>(s, sigma, q, eL, eR, ql, qr);
+    } else {
+      R dq[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const R* a = sq + k * nQ + b;
+        q[k] = a[0];
+        dq[k] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+      }
+      trace<R>(s, sigma, q, dq, ql, qr);
     }
-    R ql[4], qr[4];
-    trace<R>(s, sigma, q, dq, ql, qr);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       sl[k * nC + e] = ql[k];

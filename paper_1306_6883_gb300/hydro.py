@@ -17,6 +17,7 @@ NOALLOC_MAX_ROWS = 16384
 HYDRO_FP64, HYDRO_FP32 = 0, 1
 BC = {"outflow": 0, "periodic": 1, "reflect": 2, "hydrostatic": 3}
 RIEMANN = {"two-shock": 0, "hllc": 1}
+RECON = {"plm": 0, "ppm": 1}
 
 
 class HydroParams(ctypes.Structure):
@@ -30,6 +31,7 @@ class HydroParams(ctypes.Structure):
         ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double),
         ("precision", ctypes.c_int), ("use_learned_guess", ctypes.c_int),
         ("grav", ctypes.c_double), ("split", ctypes.c_int), ("riemann_solver", ctypes.c_int),
+        ("reconstruction", ctypes.c_int),
     ]
 
 
@@ -126,6 +128,8 @@ def default_params(nx, ny, precision=HYDRO_FP64, **overrides):
             p.bc_xlo, p.bc_xhi, p.bc_ylo, p.bc_yhi = (BC[b] if isinstance(b, str) else b for b in v)
         elif k == "riemann_solver" and isinstance(v, str):
             p.riemann_solver = RIEMANN[v]
+        elif k == "reconstruction" and isinstance(v, str):
+            p.reconstruction = RECON[v]
         else:
             setattr(p, k, v)
     return p

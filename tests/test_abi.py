@@ -106,9 +106,19 @@ def test_hllc_rejects_what_it_does_not_implement(lib, extra):
     assert H.state_pitch(p) == 0
 
 
+@pytest.mark.parametrize("extra", [dict(use_learned_guess=1, precision=1), dict(reconstruction=2)])
+def test_ppm_rejects_what_it_does_not_implement(lib, extra):
+    from paper_1306_6883_gb300 import hydro as H
+    p = H.default_params(16, 16, reconstruction="ppm")
+    assert H.state_pitch(p) > 0 and p.reconstruction == 1
+    for k, v in extra.items():
+        setattr(p, k, v)
+    assert H.state_pitch(p) == 0
+
+
 def test_ensembles_take_the_two_shock_unsplit_step_only(lib):
     from paper_1306_6883_gb300 import hydro as H
-    for kw in (dict(riemann_solver="hllc"), dict(split=1)):
+    for kw in (dict(riemann_solver="hllc"), dict(split=1), dict(reconstruction="ppm")):
         p = H.default_params(16, 16, H.HYDRO_FP32, **kw)
         arr = (H.HydroParams * 1)(p)
         ptrs = (ctypes.c_void_p * 1)(256)
