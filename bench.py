@@ -165,8 +165,7 @@ def max_over_ranks(x, world):
 # ---------------------------------------------------------------------------------------------------- our arm
 def time_device_path(pr, precision, steps, warmup, flush, **kw):
     """Value: steps of the driver loop (ghost cells, CFL dt, CTU step) with the state resident in HBM through
-    hydro_step_fused: one launch of the fused step kernel, or for reflecting / hydrostatic sides the three
-    launches fill, dt, step."""
+    hydro_step_fused: one launch of the fused step kernel (two sweep launches for the split variant)."""
     import torch
 
     from paper_1306_6883_gb300 import hydro as H
@@ -193,8 +192,7 @@ def time_device_path(pr, precision, steps, warmup, flush, **kw):
     s.close()
     solves = stats1[0] - stats0[0]
     iters = stats1[1] - stats0[1]
-    plain = all(b in ("outflow", "periodic") for b in pr.bc)
-    launches = 2 if kw.get("split") else (1 if plain else 3)  # split: x (y) sweep, y (x) sweep + dt
+    launches = 2 if kw.get("split") else 1  # split: x (y) sweep, y (x) sweep folding in the dt
     return {"step_ms": step_ms, "kernel_ms": step_ms, "iters_per_solve": iters / max(solves, 1),
             "t_sim": t_sim, "totals": tot, "launches_per_step": launches}
 

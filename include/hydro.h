@@ -47,8 +47,8 @@ typedef enum {
  * OUTFLOW: zero gradient.  PERIODIC: wrap (both sides of an axis).  REFLECT: mirror image of the interior
  * with the normal momentum negated.  HYDROSTATIC (y sides only): density and momenta copied from the row
  * next to the wall, pressure integrated with dp/dy = rho g from that row's cell, energy rebuilt from it.
- * REFLECT and HYDROSTATIC are filled by hydro_fill_ghost; hydro_step_fused and hydro_advance then run the
- * fill / dt / step passes instead of one fused launch. */
+ * The fused step (hydro_step_fused, hydro_advance) and the split sweeps read every kind of side through
+ * the same map instead of a ghost fill. */
 /* Riemann solvers (paper §3.2).  TWO_SHOCK: Newton iteration of the two-shock approximation (the default).
  * HLLC: Toro's three-wave HLLC flux, outer wave speeds min(u_L - c_L, u_R - c_R), max(u_L + c_L, u_R + c_R);
  * no iterations (the iteration counters then stay 0). */
@@ -171,13 +171,14 @@ hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
  * nsteps x hydro_step_fused(tmax); the ghost cells of the final state are not filled. */
 
 /* One step of the driver loop as a single kernel launch: the step kernel reads ghost cells through the
- * boundary conditions' map of the interior (the values hydro_fill_ghost would write, so no fill pass),
+ * boundary conditions' map of the interior (the values hydro_fill_ghost would write, for every kind of
+ * side, so no fill pass),
  * and reduces the CFL time step of the state it writes (so no dt pass); its last block advances the
  * device time by this step's dt and keeps the next step's dt (clamped to reach tmax when tmax > 0).  The
  * first call after any other state change (hydro_step, hydro_step_device_dt, hydro_upload) computes this
  * step's dt with one extra reduction.  With split = 1: the two sweeps of hydro_step, the second one
- * reducing the next dt.  FP32 contexts with a learned model or a harvest, and reflecting or hydrostatic
- * sides of the unsplit step, run the separate passes instead.  Asynchronous. */
+ * reducing the next dt.  FP32 contexts with a learned model or a harvest run the separate passes instead.
+ * Asynchronous. */
 hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
 /* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */

@@ -22,7 +22,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # They hold the FP64 kernels (which then round exactly like the plain C implementation of the method) and
 # the dt, ghost and totals kernels (memory-bound; both precisions).
 EXACT_UNITS = {"k_ctu_f64.cu", "k_ctu_hllc_f64.cu", "k_ctu_ppm_f64.cu", "k_batch_f64.cu", "k_split_f64.cu",
-               "k_aux.cu", "k_totals_noalloc.cu"}
+               "k_split_ppm_f64.cu", "k_aux.cu", "k_totals_noalloc.cu"}
 
 
 def _nvcc():

@@ -43,6 +43,23 @@ struct TileLayout {
   static constexpr size_t bytes = sizeof(R) * (size_t)elems;
 };
 
+// The four conserved values of padded cell (gi, gj) as the step sees them: through the boundary map for the
+// fused step (bc_cell where a side is reflecting or hydrostatic), else from the ghost-filled array.
+template <bool FUSED, typename R>
+__device__ __forceinline__ void tile_cell(const KParams& P, const R* __restrict__ U, int gi, int gj, size_t plane,
+                                          R v[4]) {
+  if (FUSED && P.bc_general) {
+    R w[4];
+    bc_cell_clamped(P, U, gi, gj, plane, w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = w[k];
+  } else {
+    const size_t o = cell_offset<FUSED>(P, gi, gj);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __ldg(U + o + k * plane);
+  }
+}
+
 // Counters each thread accumulates over the tiles it works on.
 struct TileCounters {
   unsigned int solves = 0, iters = 0, nonconv = 0, flags = 0;
@@ -217,9 +234,17 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     for (int it = 0; it < NLD; ++it) {
       const int e = tid + it * NT;
       if (e < QX * QY) {
-        const size_t o = cell_offset<FUSED>(P, x0 - 4 + e % QX, y0 - 4 + e / QX);
+        const int gi = x0 - 4 + e % QX, gj = y0 - 4 + e / QX;
+        if (FUSED && P.bc_general) {  // reflecting or hydrostatic sides: the ghost fill's values
+          R v[4];
+          bc_cell_clamped(P, Uin, gi, gj, plane, v);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
+          for (int k = 0; k < 4; ++k) Ul[it][k] = v[k];
+        } else {
+          const size_t o = cell_offset<FUSED>(P, gi, gj);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
+        }
       }
     }
 #pragma unroll
@@ -447,9 +472,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             for (int k = 0; k < 4; ++k) F[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
           } else {
             const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
-            const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi - 1, gj);
+            R uL[4], uR[4];
+            tile_cell<FUSED>(P, Uin, gi - 1, gj, plane, uL);
+            tile_cell<FUSED>(P, Uin, gi, gj, plane, uR);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+            for (int k = 0; k < 4; ++k) F[k] += av * (uL[k] - uR[k]);
           }
         }
 #pragma unroll
@@ -472,10 +499,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             for (int k = 0; k < 4; ++k) G[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
           } else {
             const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
-            const size_t oR = cell_offset<FUSED>(P, gi, gj), oL = cell_offset<FUSED>(P, gi, gj - 1);
+            R uL[4], uR[4];
+            tile_cell<FUSED>(P, Uin, gi, gj - 1, plane, uL);
+            tile_cell<FUSED>(P, Uin, gi, gj, plane, uR);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              G[k] += av * (__ldg(Uin + oL + k * plane) - __ldg(Uin + oR + k * plane));
+            for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
           }
         }
 #pragma unroll

@@ -195,6 +195,8 @@ void fill_kparams(const hydro_params* p, KParams* kp) {
   k.use_grav = p->grav != 0.0;
   k.riemann_solver = p->riemann_solver;
   k.reconstruction = p->reconstruction;
+  k.bc_general = p->bc_xlo >= HYDRO_BC_REFLECT || p->bc_xhi >= HYDRO_BC_REFLECT || p->bc_ylo >= HYDRO_BC_REFLECT ||
+                 p->bc_yhi >= HYDRO_BC_REFLECT;
   k.gamma_f = (float)k.gamma;
   k.gm1_f = (float)k.gm1;
   k.igm1_f = (float)(1.0 / k.gm1);
@@ -392,10 +394,6 @@ hydro_status hydro_step(hydro_ctx* c, double dt) {
 
 hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
   if (!c) return HYDRO_EINVAL;
-  // the optional face variants, and reflecting or hydrostatic sides (whose ghost cells are not plain copies
-  // of interior cells), use the separate passes: ghost fill, dt, step
-  const bool plain_bc = c->p.bc_xlo <= HYDRO_BC_PERIODIC && c->p.bc_xhi <= HYDRO_BC_PERIODIC &&
-                        c->p.bc_ylo <= HYDRO_BC_PERIODIC && c->p.bc_yhi <= HYDRO_BC_PERIODIC;
   if (c->p.split) {
     // two sweeps, the second folding in the next step's dt; the new state is in the current buffer
     cudaError_t e = cudaSuccess;
@@ -411,7 +409,7 @@ hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
     c->fused_valid = 1;
     return HYDRO_OK;
   }
-  if (c->p.use_learned_guess == 1 || c->harvest || !plain_bc) {
+  if (c->p.use_learned_guess == 1 || c->harvest) {  // the optional face variants use the separate passes
     if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);

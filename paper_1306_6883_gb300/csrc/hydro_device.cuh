@@ -39,6 +39,7 @@ struct KParams {
   int use_grav;  // grav != 0: the step applies the gravity terms
   int riemann_solver;  // 0 two-shock iteration, 1 HLLC
   int reconstruction;  // 0 piecewise linear, 1 piecewise parabolic
+  int bc_general;      // some side is reflecting or hydrostatic (ghost values are not plain copies)
 };
 
 // Time-step dependent factors of one CTU step, computed once in double (host, or the last block of
@@ -143,7 +144,7 @@ __device__ __forceinline__ float M<float>::sq(float x) { return x * rsqa(x); }
 template <typename R>
 struct SP {
   R gamma, gm1, igm1, g1, small_dens, small_pres, tol, cvisc, dx, dy, idx, idy;
-  int maxiter, limiter, flatten, hllc, ppm;
+  int maxiter, limiter, flatten;
   __device__ __forceinline__ void load(const KParams& P) {
     if constexpr (is_f32<R>()) {
       gamma = P.gamma_f; gm1 = P.gm1_f; igm1 = P.igm1_f; g1 = P.g1_f; small_dens = P.small_dens_f;
@@ -156,8 +157,6 @@ struct SP {
     maxiter = P.riemann_maxiter;
     limiter = P.limiter;
     flatten = P.use_flattening;
-    hllc = P.riemann_solver;
-    ppm = P.reconstruction;
   }
 };
 
@@ -205,6 +204,16 @@ __device__ __forceinline__ void bc_cell(const KParams& P, const R* U, int i, int
     const double pg = __dadd_rn(pe, __dmul_rn(__dmul_rn(rho, P.grav), __dmul_rn((double)(j - sj), P.dy)));
     v[3] = (R)__dadd_rn(__ddiv_rn(pg, P.gm1), ke);
   }
+}
+
+// bc_cell of a padded index clamped into the padded array (a ragged tile's halo can reach past it).  Not
+// inlined: only boundary tiles of problems with reflecting or hydrostatic sides call it from the fused step,
+// whose register allocation then stays that of the plain path.
+template <typename R>
+__device__ __noinline__ void bc_cell_clamped(const KParams& P, const R* U, int gi, int gj, size_t plane, R v[4]) {
+  gi = gi < 0 ? 0 : (gi >= P.NX ? P.NX - 1 : gi);
+  gj = gj < 0 ? 0 : (gj >= P.NY ? P.NY - 1 : gj);
+  bc_cell(P, U, gi, gj, plane, v);
 }
 
 // Writes the ghost cell (i, j) with its boundary value (bc_cell).

@@ -87,6 +87,14 @@ cudaError_t split_sweep(int precision, const KParams& P, const void* Uin, void* 
 cudaError_t split_sweep_f64(const KParams& P, const double* Uin, double* Uout, int dir, const StepScalars& sc_host,
                             const StepScalars* sc_dev, DevScratch* scr, int check_state, StepScalars* sc_next,
                             double tmax, cudaStream_t stream);
+// The same sweeps with piecewise-parabolic reconstruction (k_split_ppm.cu, k_split_ppm_f64.cu); split_sweep
+// dispatches to them when P.reconstruction == 1.
+cudaError_t split_sweep_ppm(int precision, const KParams& P, const void* Uin, void* Uout, int dir,
+                            const StepScalars& sc_host, const StepScalars* sc_dev, DevScratch* scr, int check_state,
+                            StepScalars* sc_next, double tmax, cudaStream_t stream);
+cudaError_t split_sweep_ppm_f64(const KParams& P, const double* Uin, double* Uout, int dir,
+                                const StepScalars& sc_host, const StepScalars* sc_dev, DevScratch* scr,
+                                int check_state, StepScalars* sc_next, double tmax, cudaStream_t stream);
 
 // Host copy of the device hash32 (mlp.cuh), for per-step sampling seeds.
 inline unsigned int host_hash32(unsigned int x) {

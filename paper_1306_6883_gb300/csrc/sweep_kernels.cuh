@@ -53,7 +53,7 @@ __device__ __forceinline__ void sweep_item(int e, int& a, int& l) {
   }
 }
 
-template <typename R, int DIR, int LN, int NL, int NT, bool FUSED>
+template <typename R, int DIR, int LN, int NL, int NT, bool FUSED, int MODE>
 __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
                                                    StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
                                                    DevScratch* __restrict__ scr, int check_state,
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
     sxi[e] = xi;
     sun[e] = qn[b];
     R q[4], ql[4], qr[4];
-    if (s.ppm) {
+    if constexpr ((MODE & RECON_PPM) != 0) {
       R eL[4], eR[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
     }
     int it = 0;
     bool ok = true;
-    if (s.hllc) {
+    if constexpr (face_kind(MODE) == FACE_HLLC) {
       hllc(s, a, bq, F);
     } else {
       R pst;
@@ -315,8 +315,10 @@ __global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restric
 }
 
 // Launch of one sweep with the tile shape of the precision (dynamic shared memory raised once per device).
-// sc_next == NULL: a plain sweep; otherwise the fused second sweep of a step (FUSED instantiation).
-template <typename R, int DIR, int LN, int NL, int NT>
+// sc_next == NULL: a plain sweep; otherwise the fused second sweep of a step (FUSED instantiation).  MODE:
+// FACE_PLAIN or FACE_HLLC, with RECON_PPM for piecewise-parabolic reconstruction (each its own instantiation,
+// so the paper's configuration keeps its registers).
+template <typename R, int DIR, int LN, int NL, int NT, int MODE>
 struct Sweep {
   static cudaError_t launch(const KParams& P, const R* Uin, R* Uout, const StepScalars& sc_host,
                             const StepScalars* sc_dev, DevScratch* scr, int check_state, StepScalars* sc_next,
@@ -328,15 +330,15 @@ struct Sweep {
     const dim3 grid(DIR == 0 ? ta : tl, DIR == 0 ? tl : ta);
     cudaError_t e;
     if (sc_next) {
-      e = smem_attr_once(sweep_kernel<R, DIR, LN, NL, NT, true>, L::bytes, done_fused);
+      e = smem_attr_once(sweep_kernel<R, DIR, LN, NL, NT, true, MODE>, L::bytes, done_fused);
       if (e != cudaSuccess) return e;
-      sweep_kernel<R, DIR, LN, NL, NT, true><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
-                                                                             check_state, sc_next, tmax);
+      sweep_kernel<R, DIR, LN, NL, NT, true, MODE><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
+                                                                                  check_state, sc_next, tmax);
     } else {
-      e = smem_attr_once(sweep_kernel<R, DIR, LN, NL, NT, false>, L::bytes, done_plain);
+      e = smem_attr_once(sweep_kernel<R, DIR, LN, NL, NT, false, MODE>, L::bytes, done_plain);
       if (e != cudaSuccess) return e;
-      sweep_kernel<R, DIR, LN, NL, NT, false><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
-                                                                              check_state, nullptr, 0.0);
+      sweep_kernel<R, DIR, LN, NL, NT, false, MODE><<<grid, NT, L::bytes, stream>>>(P, Uin, Uout, sc_host, sc_dev, scr,
+                                                                                   check_state, nullptr, 0.0);
     }
     return cudaGetLastError();
   }
