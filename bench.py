@@ -48,8 +48,8 @@ ALU_PEAK_SOURCE = {"fp32": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit 
 # DRAM bytes (read + write) of one launch of the FP32 fused step kernel on the KH 1024^2 workload, from an
 # ncu capture of the kernel built from the sources whose SHA-256 is recorded; reported only while the
 # kernel's sources are unchanged (otherwise the counters describe another kernel and traffic is null)
-TRAFFIC_CAPTURE = {"bytes_per_launch": 17382912 + 4864,
-                   "sources_sha256": "e6cfb67fd912882c20343d07b51aa919b100ce4a6470ec4730dc9053216715a0"}
+TRAFFIC_CAPTURE = {"bytes_per_launch": 17379072 + 768,
+                   "sources_sha256": "3d5c4c548a607da359ee9a493714eaa4d316d707c7b9ade26f41bf38c6e313c5"}
 KERNEL_SOURCES = ["paper_1306_6883_gb300/csrc/" + f for f in
                   ("k_ctu.cu", "ctu_kernels.cuh", "ctu_tile.cuh", "hydro_device.cuh", "mlp.cuh", "hydro_kernels.h",
                    "tma.cuh")] + ["include/hydro.h"]

@@ -1,11 +1,13 @@
 """Command-line driver, after the paper's single driver (§2: ./pyro.py solver problem infile):
 
     python -m paper_1306_6883_gb300 PROBLEM [--nx N] [--ny N] [--precision fp32|fp64]
-                                            [--steps K | --tmax T] [--seed S] [--split] [--dump FILE]
+                                            [--steps K | --tmax T] [--seed S] [--split]
+                                            [--riemann two-shock|hllc] [--recon plm|ppm] [--dump FILE]
 
 PROBLEM is one of sod, sod_y, kh, sedov, quad, pulse, rt (seeded set-ups of hydro_problems; rt is the
 Rayleigh-Taylor column with gravity, nx x 3nx by default).  Runs the device-resident loop (fill ghost
-cells, CFL dt, CTU step; --split: the dimensionally split step) and prints one JSON line with the simulated
+cells, CFL dt, CTU step; --split: the dimensionally split step; --riemann and --recon choose the Riemann
+solver and the reconstruction) and prints one JSON line with the simulated
 time, step count, wall time, conserved totals and the Riemann-solver counters.  --dump writes the final
 state (dense float64 array, shape (4, ny+8, nx+8)) with numpy.save.
 """
@@ -51,6 +53,8 @@ def main(argv=None):
     ap.add_argument("--tmax", type=float, default=None)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--split", action="store_true")
+    ap.add_argument("--riemann", choices=["two-shock", "hllc"], default="two-shock")
+    ap.add_argument("--recon", choices=["plm", "ppm"], default="plm")
     ap.add_argument("--dump", default=None)
     a = ap.parse_args(argv)
 
@@ -64,7 +68,7 @@ def main(argv=None):
     ny = a.ny or (3 * a.nx if a.problem == "rt" else a.nx)
     pr = make_problem(a.problem, a.nx, ny, a.seed)
     prec = H.HYDRO_FP32 if a.precision == "fp32" else H.HYDRO_FP64
-    s = Solver(params_for(pr, prec, split=int(a.split)), pr.U)
+    s = Solver(params_for(pr, prec, split=int(a.split), riemann_solver=a.riemann, reconstruction=a.recon), pr.U)
     tmax = a.tmax if a.tmax is not None else (pr.tmax if np.isfinite(pr.tmax) and a.steps is None else 0.0)
     steps = a.steps if a.steps is not None else 10 ** 9
     torch.cuda.synchronize()
@@ -83,7 +87,8 @@ def main(argv=None):
     wall = time.perf_counter() - t0
     st, stats = s.status(raise_on_error=False)
     t, nsteps = s.time()
-    out = {"problem": a.problem, "nx": pr.nx, "ny": pr.ny, "precision": a.precision, "split": a.split, "t": t,
+    out = {"problem": a.problem, "nx": pr.nx, "ny": pr.ny, "precision": a.precision, "split": a.split, "riemann": a.riemann,
+           "recon": a.recon, "t": t,
            "steps": nsteps,
            "wall_s": wall, "zone_updates_per_s": pr.nx * pr.ny * nsteps / wall if wall > 0 else None,
            "totals": s.totals(), "status": H.STATUS_NAMES[st], "riemann_solves": stats[0],
