@@ -16,15 +16,15 @@ cudaError_t split_sweep(int precision, const KParams& P, const void* Uin, void* 
   // consecutive addresses); both 61-64 KB of shared memory, 3 CTAs per SM
   if (P.riemann_solver == 1) {
     if (dir == 0)
-      return Sweep<float, 0, 64, 16, 256, FACE_HLLC>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
+      return Sweep<float, 0, 64, 16, SWEEP_F32_NT, FACE_HLLC>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
                                                              tmax, stream);
-    return Sweep<float, 1, 32, 32, 256, FACE_HLLC>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
+    return Sweep<float, 1, 32, 32, SWEEP_F32_NT, FACE_HLLC>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
                                                            tmax, stream);
   }
   if (dir == 0)
-    return Sweep<float, 0, 64, 16, 256, FACE_PLAIN>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
+    return Sweep<float, 0, 64, 16, SWEEP_F32_NT, FACE_PLAIN>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
                                                             tmax, stream);
-  return Sweep<float, 1, 32, 32, 256, FACE_PLAIN>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
+  return Sweep<float, 1, 32, 32, SWEEP_F32_NT, FACE_PLAIN>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next,
                                                           tmax, stream);
 }
 

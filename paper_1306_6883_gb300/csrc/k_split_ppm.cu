@@ -9,9 +9,9 @@ static cudaError_t sweep_ppm_f32(const KParams& P, const float* in, float* out, 
                                  const StepScalars* sc_dev, DevScratch* scr, int check_state, StepScalars* sc_next,
                                  double tmax, cudaStream_t stream) {
   if (dir == 0)
-    return Sweep<float, 0, 64, 16, 256, MODE>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next, tmax,
+    return Sweep<float, 0, 64, 16, SWEEP_F32_NT, MODE>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next, tmax,
                                                       stream);
-  return Sweep<float, 1, 32, 32, 256, MODE>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next, tmax,
+  return Sweep<float, 1, 32, 32, SWEEP_F32_NT, MODE>::launch(P, in, out, sc_host, sc_dev, scr, check_state, sc_next, tmax,
                                                     stream);
 }
 

@@ -53,8 +53,22 @@ __device__ __forceinline__ void sweep_item(int e, int& a, int& l) {
   }
 }
 
+// Threads of the FP32 sweep CTAs (overridable at compile time for sweeps of the launch shape).  Measured per
+// split step, KH 1024^2 / Sedov 2048^2: 256 threads 77.9 / 225 us, 384 threads (36 warps per SM, 56
+// registers) 70.3 / 206 us, 512 threads (two CTAs per SM) 77.3 / 245 us.
+#ifndef HYDRO_SWEEP_F32_NT
+#define HYDRO_SWEEP_F32_NT 384
+#endif
+constexpr int SWEEP_F32_NT = HYDRO_SWEEP_F32_NT;
+
+// Resident CTAs per SM the register allocator must allow (shared memory admits three tiles of either
+// precision's shapes).
+#ifndef HYDRO_SWEEP_MINB
+#define HYDRO_SWEEP_MINB 3
+#endif
+
 template <typename R, int DIR, int LN, int NL, int NT, bool FUSED, int MODE>
-__global__ void __launch_bounds__(NT) sweep_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
+__global__ void __launch_bounds__(NT, HYDRO_SWEEP_MINB) sweep_kernel(KParams P, const R* __restrict__ Uin, R* __restrict__ Uout,
                                                    StepScalars sc_host, const StepScalars* __restrict__ sc_dev,
                                                    DevScratch* __restrict__ scr, int check_state,
                                                    StepScalars* __restrict__ sc_next, double tmax) {
