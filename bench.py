@@ -198,10 +198,10 @@ def time_device_path(pr, precision, steps, warmup, flush, **kw):
 
 
 def time_e2e(pr, precision, steps, warmup):
-    """Same metric through the public C-ABI calls with host buffers: every step uploads the state from
-    pinned host memory (hydro_upload), advances it one fused step (hydro_step_fused: dt of the uploaded
-    state, then the step) and downloads the new state (hydro_download, which waits for it); the two pinned
-    host buffers alternate as input and output."""
+    """Same metric through the public C-ABI call for host-resident state, hydro_step_host: every step
+    uploads the state from pinned host memory, reduces its dt, runs the fused step as concurrent bands of
+    tile rows and copies each band's rows back while later bands compute, returning when the new state is
+    in host memory; the two pinned host buffers alternate as input and output."""
     import torch
 
     from paper_1306_6883_gb300 import hydro as H
@@ -213,9 +213,7 @@ def time_e2e(pr, precision, steps, warmup):
     host = [torch.from_numpy(np.ascontiguousarray(pr.U)).to(dt_).pin_memory() for _ in range(2)]
 
     def one(k):
-        s.upload(host[k % 2])
-        s.step_fused()
-        s.download(host[(k + 1) % 2])
+        s.step_host(host[k % 2], host[(k + 1) % 2])
 
     for k in range(warmup):
         one(k)

@@ -181,6 +181,14 @@ hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
  * Asynchronous. */
 hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
+/* One step with host-resident state: host_in (pinned, layout of hydro_upload) is uploaded, stepped as
+ * hydro_step_fused(tmax) does, and the new state written to host_out (layout of hydro_download; must not
+ * be host_in).  The fused step runs as four launches over bands of tile rows on the context's own streams,
+ * and each band's rows are copied back while later bands compute.  Returns when host_out holds the new
+ * state.  Contexts whose fused step takes the separate passes (learned model, harvest, split = 1) run
+ * upload, hydro_step_fused and hydro_download in turn.  Same results as those three calls. */
+hydro_status hydro_step_host(hydro_ctx* ctx, const void* host_in, void* host_out, double tmax);
+
 /* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */
 hydro_status hydro_get_time(hydro_ctx* ctx, double* t, long long* nsteps);
 

@@ -125,13 +125,16 @@ cudaError_t launch_ctu_step(const KParams& P, const R* Uin, R* Uout, const StepS
 
 // Fused step: the tile reads ghost cells through the boundary map and folds the CFL constraint of its new
 // cells into a block minimum; the last block to finish advances the time by this step's dt and writes
-// the next step's factors, so a run needs one launch per step and no ghost-fill or dt pass.
+// the next step's factors, so a run needs one launch per step and no ghost-fill or dt pass.  A step may be
+// split into launches over bands of tile rows (by0: the band's first tile row; nblocks: the tiles of the
+// whole step), which run concurrently; the last block of all of them finishes the step.
 template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KParams P, const R* __restrict__ Uin,
                                                             R* __restrict__ Uout, const StepScalars* __restrict__ sc_cur,
                                                             StepScalars* __restrict__ sc_next,
                                                             DevScratch* __restrict__ scr, double tmax,
-                                                            const __grid_constant__ CUtensorMap tmap, int use_tma) {
+                                                            const __grid_constant__ CUtensorMap tmap, int use_tma,
+                                                            int by0, unsigned int nblocks) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SP<R> s;
   s.load(P);
@@ -139,12 +142,13 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   f.load(*sc_cur);
   TileCounters cnt;
   R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
+  const int by = by0 + (int)blockIdx.y;
   if (sc_cur->dt == 0.0) {
     // a step of length zero (the run has reached tmax) leaves the state as it is: copy the tile's interior
     // cells and take their CFL constraint as a step would (the next dt is then clamped to 0 again)
     const size_t plane = (size_t)P.NY * P.pitch;
     for (int e = threadIdx.x; e < TX * TY; e += NT) {
-      const int gi = P.ng + blockIdx.x * TX + e % TX, gj = P.ng + blockIdx.y * TY + e / TX;
+      const int gi = P.ng + blockIdx.x * TX + e % TX, gj = P.ng + by * TY + e / TX;
       if (gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
       const size_t o = (size_t)gj * P.pitch + gi;
       R u[4];
@@ -153,8 +157,8 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
       cfl_value(s, u[0], u[1], u[2], u[3], cmin, cnt.flags);
     }
   } else {
-    ctu_tile<R, TX, TY, NT, MODE, true>(P, s, f, Uin, Uout, blockIdx.x, blockIdx.y, smem_raw, cnt, FaceHook{},
-                                        nullptr, &cmin, use_tma ? &tmap : nullptr);
+    ctu_tile<R, TX, TY, NT, MODE, true>(P, s, f, Uin, Uout, blockIdx.x, by, smem_raw, cnt, FaceHook{}, nullptr,
+                                        &cmin, use_tma ? &tmap : nullptr);
   }
   flush_counters<NT>(cnt, scr);
 #pragma unroll
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
     for (int k = 1; k < NT / 32; ++k) b = wmin[k] < b ? wmin[k] : b;
     atomicMin(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong((double)b));
     __threadfence();
-    last = atomicAdd(&scr->step_blocks_done, 1u) == gridDim.x * gridDim.y - 1u;
+    last = atomicAdd(&scr->step_blocks_done, 1u) == nblocks - 1u;
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
@@ -193,18 +197,22 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   }
 }
 
+// band: tile rows [band.x, band.x + band.y) of the step (band.y <= 0: all of them)
 template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
                                   StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, int2 band = make_int2(0, 0)) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
   static std::atomic<unsigned long long> attr_done{0};
   cudaError_t e = smem_attr_once(ctu_step_fused_kernel<R, TX, TY, NT, MODE>, smem, attr_done);
   if (e != cudaSuccess) return e;
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  ctu_step_fused_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
-                                                                         tmap ? *tmap : CUtensorMap{},
-                                                                         tmap ? 1 : 0);
+  const int tx = (P.nx + TX - 1) / TX, ty = (P.ny + TY - 1) / TY;
+  const int y0 = band.y > 0 ? band.x : 0, ny = band.y > 0 ? band.y : ty;
+  if (y0 < 0 || ny <= 0 || y0 + ny > ty) return cudaErrorInvalidValue;
+  dim3 grid(tx, ny);
+  ctu_step_fused_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(
+      P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0, y0,
+      (unsigned int)tx * (unsigned int)ty);
   return cudaGetLastError();
 }
 

@@ -25,9 +25,14 @@ cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* s
 // tmap (FP32 only, may be NULL): TMA descriptor of Uin as a 3-D tensor (x over the padded width, y over the
 // padded height, the 4 conserved components) with a (TX+8) x (TY+8) x 4 box; tiles whose box is valid are
 // then loaded by one bulk tensor copy.
+// band (optional): tile rows [band.x, band.x + band.y) only (band.y <= 0: the whole step); bands of one
+// step may run concurrently, the last tile of all of them finishes the step.  fused_tile_rows: the step's
+// number of tile rows for the precision.
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
-                           cudaStream_t stream);
+                           cudaStream_t stream, int2 band = make_int2(0, 0));
+int fused_tile_rows(int precision, const KParams& P);
+int fused_tile_height(int precision);
 
 // Conserved totals into scr->totals (deterministic two-level reduction; partials has room for
 // totals_max_blocks() * 4 doubles).
@@ -47,11 +52,12 @@ cudaError_t ctu_step_hllc(int precision, const KParams& P, const void* Uin, void
                           const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, const CUtensorMap* tmap);
 cudaError_t ctu_step_fused_hllc(int precision, const KParams& P, const void* Uin, void* Uout,
                                 const StepScalars* sc_cur, StepScalars* sc_next, DevScratch* scr, double tmax,
-                                const CUtensorMap* tmap, cudaStream_t stream);
+                                const CUtensorMap* tmap, cudaStream_t stream, int2 band);
 cudaError_t ctu_step_hllc_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,
                               const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
 cudaError_t ctu_step_fused_hllc_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
-                                    StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
+                                    StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream,
+                                    int2 band);
 
 // The same two launches with piecewise-parabolic reconstruction, with either solver (k_ctu_ppm.cu,
 // k_ctu_ppm_f64.cu); ctu_step and ctu_step_fused dispatch to them when P.reconstruction == 1.
@@ -59,11 +65,12 @@ cudaError_t ctu_step_ppm(int precision, const KParams& P, const void* Uin, void*
                          const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream, const CUtensorMap* tmap);
 cudaError_t ctu_step_fused_ppm(int precision, const KParams& P, const void* Uin, void* Uout,
                                const StepScalars* sc_cur, StepScalars* sc_next, DevScratch* scr, double tmax,
-                               const CUtensorMap* tmap, cudaStream_t stream);
+                               const CUtensorMap* tmap, cudaStream_t stream, int2 band);
 cudaError_t ctu_step_ppm_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,
                              const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
 cudaError_t ctu_step_fused_ppm_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
-                                   StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
+                                   StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream,
+                                   int2 band);
 
 // Tile box of the FP32 single-problem step kernels (the TMA box is (F32_TILE_X + 8) x (F32_TILE_Y + 8) x 4).
 int f32_tile_x();
@@ -71,7 +78,8 @@ int f32_tile_y();
 
 // FP64 forms of the two step launches (k_ctu_f64.cu, compiled without multiply-add contraction).
 cudaError_t ctu_step_fused_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
-                               StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream);
+                               StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream,
+                               int2 band = make_int2(0, 0));
 cudaError_t ctu_step_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,
                          const StepScalars* sc_dev, DevScratch* scr, cudaStream_t stream);
 

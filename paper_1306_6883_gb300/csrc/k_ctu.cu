@@ -8,12 +8,22 @@ int f32_tile_y() { return F32_TY; }
 
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
-                           cudaStream_t stream) {
-  if (P.reconstruction == 1) return ctu_step_fused_ppm(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream);
-  if (P.riemann_solver == 1) return ctu_step_fused_hllc(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream);
-  if (precision == 0) return ctu_step_fused_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream);
+                           cudaStream_t stream, int2 band) {
+  if (P.reconstruction == 1)
+    return ctu_step_fused_ppm(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream, band);
+  if (P.riemann_solver == 1)
+    return ctu_step_fused_hllc(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream, band);
+  if (precision == 0)
+    return ctu_step_fused_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream, band);
   return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT>(P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr,
-                                                              tmax, tmap, stream);
+                                                              tmax, tmap, stream, band);
+}
+
+int fused_tile_height(int precision) { return precision == 0 ? 16 : F32_TY; }  // FP64 tiles are 16 x 16
+
+int fused_tile_rows(int precision, const KParams& P) {
+  const int th = fused_tile_height(precision);
+  return (P.ny + th - 1) / th;
 }
 
 cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars& sc_host,

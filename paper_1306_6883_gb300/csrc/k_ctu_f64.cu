@@ -6,8 +6,8 @@
 namespace hydro {
 
 cudaError_t ctu_step_fused_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
-                               StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
-  return launch_ctu_step_fused<double, 16, 16, 256>(P, Uin, Uout, sc_cur, sc_next, scr, tmax, nullptr, stream);
+                               StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream, int2 band) {
+  return launch_ctu_step_fused<double, 16, 16, 256>(P, Uin, Uout, sc_cur, sc_next, scr, tmax, nullptr, stream, band);
 }
 
 cudaError_t ctu_step_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars& sc_host,

@@ -14,11 +14,11 @@ cudaError_t ctu_step_hllc(int precision, const KParams& P, const void* Uin, void
 
 cudaError_t ctu_step_fused_hllc(int precision, const KParams& P, const void* Uin, void* Uout,
                                 const StepScalars* sc_cur, StepScalars* sc_next, DevScratch* scr, double tmax,
-                                const CUtensorMap* tmap, cudaStream_t stream) {
+                                const CUtensorMap* tmap, cudaStream_t stream, int2 band) {
   if (precision == 0)
-    return ctu_step_fused_hllc_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream);
+    return ctu_step_fused_hllc_f64(P, (const double*)Uin, (double*)Uout, sc_cur, sc_next, scr, tmax, stream, band);
   return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT, FACE_HLLC>(P, (const float*)Uin, (float*)Uout, sc_cur,
-                                                                          sc_next, scr, tmax, tmap, stream);
+                                                                          sc_next, scr, tmax, tmap, stream, band);
 }
 
 }  // namespace hydro

@@ -11,9 +11,10 @@ cudaError_t ctu_step_hllc_f64(const KParams& P, const double* Uin, double* Uout,
 }
 
 cudaError_t ctu_step_fused_hllc_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
-                                    StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+                                    StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream,
+                                    int2 band) {
   return launch_ctu_step_fused<double, 16, 16, 256, FACE_HLLC>(P, Uin, Uout, sc_cur, sc_next, scr, tmax, nullptr,
-                                                               stream);
+                                                               stream, band);
 }
 
 }  // namespace hydro

@@ -15,12 +15,13 @@ cudaError_t ctu_step_ppm_f64(const KParams& P, const double* Uin, double* Uout, 
 }
 
 cudaError_t ctu_step_fused_ppm_f64(const KParams& P, const double* Uin, double* Uout, const StepScalars* sc_cur,
-                                   StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream) {
+                                   StepScalars* sc_next, DevScratch* scr, double tmax, cudaStream_t stream,
+                                   int2 band) {
   if (P.riemann_solver == 1)
     return launch_ctu_step_fused<double, 16, 16, 256, RECON_PPM | FACE_HLLC>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
-                                                                             nullptr, stream);
+                                                                             nullptr, stream, band);
   return launch_ctu_step_fused<double, 16, 16, 256, RECON_PPM | FACE_PLAIN>(P, Uin, Uout, sc_cur, sc_next, scr, tmax,
-                                                                            nullptr, stream);
+                                                                            nullptr, stream, band);
 }
 
 }  // namespace hydro

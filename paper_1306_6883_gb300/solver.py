@@ -69,6 +69,10 @@ class Solver:
     def download(self, host_tensor):
         H.hydro_download(self.ctx, host_tensor.data_ptr())
 
+    def step_host(self, host_in, host_out, tmax=0.0):
+        """One step from a pinned host tensor to another (upload, fused step, download, overlapped)."""
+        H.hydro_step_host(self.ctx, host_in.data_ptr(), host_out.data_ptr(), tmax)
+
     def time(self):
         return H.hydro_get_time(self.ctx)
 
