@@ -48,8 +48,8 @@ ALU_PEAK_SOURCE = {"fp32": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit 
 # DRAM bytes (read + write) of one launch of the FP32 fused step kernel on the KH 1024^2 workload, from an
 # ncu capture of the kernel built from the sources whose SHA-256 is recorded; reported only while the
 # kernel's sources are unchanged (otherwise the counters describe another kernel and traffic is null)
-TRAFFIC_CAPTURE = {"bytes_per_launch": 17379072 + 768,
-                   "sources_sha256": "3d5c4c548a607da359ee9a493714eaa4d316d707c7b9ade26f41bf38c6e313c5"}
+TRAFFIC_CAPTURE = {"bytes_per_launch": 17379072 + 1536, "issue_active": 0.7843, "warp_instructions": 79683296,
+                   "sources_sha256": "90d58d30984d1220f41227698db957f337eb03be4531cfbb2d8ced83d5369e73"}
 KERNEL_SOURCES = ["paper_1306_6883_gb300/csrc/" + f for f in
                   ("k_ctu.cu", "ctu_kernels.cuh", "ctu_tile.cuh", "hydro_device.cuh", "mlp.cuh", "hydro_kernels.h",
                    "tma.cuh")] + ["include/hydro.h"]
@@ -547,6 +547,10 @@ def run_ours(args, world, rank, local):
             line["roofline"]["traffic"] = TRAFFIC_CAPTURE["bytes_per_launch"]
             line["roofline"]["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch; "
                                                 "the new state stays in L2 and is written back after the launch")
+            # the bound that binds: the kernel is issue-bound (share of cycles in which a warp instruction
+            # issues, from the same capture), far from both the FP32 ALU and the HBM ceilings
+            line["roofline"]["issue_active_ncu"] = TRAFFIC_CAPTURE["issue_active"]
+            line["roofline"]["warp_instructions_per_launch_ncu"] = TRAFFIC_CAPTURE["warp_instructions"]
         else:
             line["roofline"]["traffic_note"] = "kernel sources changed since the last ncu capture"
 
