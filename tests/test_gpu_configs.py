@@ -1,10 +1,12 @@
-"""Whole runs of the Kelvin-Helmholtz and Sedov workloads on the GPU, at their full sizes.
+"""Whole runs of the Kelvin-Helmholtz, Sedov and Rayleigh-Taylor workloads on the GPU, at their full sizes.
 
 * KH 1024^2, periodic, 200 steps (the plain-FP64 and FP32-bulk variants): the FP64 run equals the oracle's
   200-step driver loop bit for bit; the FP32 run's error against it and both runs' conservation are stated.
 * Sedov 4096^2 to t = 0.1 (FP32 bulk with FP64 energy recovery): the blast stays round, its radius follows
   the self-similar law R ~ t^(1/2) of a cylindrical point explosion, and mass and energy are conserved while
   the shock is inside the domain.
+* The variant legs (split, HLLC, PPM and all three together) on KH 1024^2 and Rayleigh-Taylor 1024 x 3072:
+  FP64 loops equal the oracle's bit for bit.
 """
 import numpy as np
 import pytest
@@ -108,3 +110,44 @@ def test_sedov_4096_blast_grows_self_similarly():
     # mass and total energy (FP64 totals of the FP32 state): conserved to float storage (observed ~1e-8)
     for k in (0, 3):
         assert abs(tot1[k] - tot0[k]) <= 1e-6 * abs(tot0[k]), (k, tot0[k], tot1[k])
+
+
+@pytest.mark.parametrize("variant", [dict(split=1), dict(riemann_solver="hllc"), dict(reconstruction="ppm"),
+                                     dict(reconstruction="ppm", riemann_solver="hllc", split=1)])
+def test_kh_1024_fp64_variants_equal_the_oracle_loop(variant):
+    # the variant legs of bench.py (split, HLLC, PPM) at the benchmark's full size, in the launches it times
+    # (hydro_step_fused): 5 FP64 steps equal the oracle's driver loop bit for bit
+    from paper_1306_6883_gb300.solver import Solver, params_for
+    pr = hp.kh(1024, 1024, seed=0)
+    s = Solver(params_for(pr, 0, **variant), pr.U)
+    s.advance(5)
+    t, n = s.time()
+    got = _interior(s.state_numpy())
+    s.close()
+    xmin, xmax, ymin, ymax = pr.domain
+    po = oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl, xmin=xmin, xmax=xmax, ymin=ymin,
+                       ymax=ymax, riemann_solver=variant.get("riemann_solver", 0),
+                       reconstruction=variant.get("reconstruction", 0))
+    U = np.array(pr.U, dtype=np.float64)
+    to, no = oracle.advance(po, U, nsteps=5, split=bool(variant.get("split")))
+    assert (t, n) == (to, no)
+    np.testing.assert_array_equal(got, _interior(U))
+
+
+def test_rayleigh_taylor_1024x3072_fp64_equals_the_oracle_loop():
+    # the bench's Rayleigh-Taylor leg at its full size: 3 FP64 fused steps (gravity, hydrostatic walls read
+    # through the boundary map) equal the oracle's loop bit for bit
+    from paper_1306_6883_gb300.solver import Solver, params_for
+    pr = hp.rt(1024, 3072)
+    s = Solver(params_for(pr, 0), pr.U)
+    s.advance(3)
+    t, n = s.time()
+    got = _interior(s.state_numpy())
+    s.close()
+    xmin, xmax, ymin, ymax = pr.domain
+    po = oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl, xmin=xmin, xmax=xmax, ymin=ymin,
+                       ymax=ymax, grav=pr.grav)
+    U = np.array(pr.U, dtype=np.float64)
+    to, no = oracle.advance(po, U, nsteps=3)
+    assert (t, n) == (to, no)
+    np.testing.assert_array_equal(got, _interior(U))
