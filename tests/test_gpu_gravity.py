@@ -4,8 +4,8 @@ FP64 oracle, through the C ABI.
 
 * ghost fill: bit equality for every combination of outflow, periodic, reflecting and hydrostatic sides, in
   both state precisions (the hydrostatic energy is formed in double on both sides);
-* one FP64 step and FP64 driver loops (the three-pass loop for reflecting / hydrostatic sides, the fused
-  launch for gravity with periodic sides): bit equality with the oracle;
+* one FP64 step and FP64 driver loops (the fused launch, which reads reflecting and hydrostatic sides through
+  the boundary map): bit equality with the oracle;
 * FP32: one step within the same bound as the other problems;
 * ensembles: a Rayleigh-Taylor member evolves exactly as the same problem alone.
 """
@@ -120,8 +120,8 @@ def test_fp64_step_matches_the_oracle(name):
 @pytest.mark.parametrize("name,nsteps", [("rt_32x96", 30), ("walls_grav_45x33", 20),
                                          ("outflow_x_hydro_y_40x24", 20), ("fall_periodic_48x40", 20)])
 def test_fp64_driver_loop_is_bit_identical_to_the_oracle_loop(name, nsteps):
-    # reflecting / hydrostatic sides run the fill / dt / step passes; gravity with periodic sides runs the
-    # fused launch (ghost cells read through the periodic map): both against the oracle's loop
+    # the fused launch reads reflecting / hydrostatic sides through the boundary map (bc_cell) and periodic
+    # sides through the wrap; both against the oracle's fill / dt / step loop
     H, Solver, params_for = _mods()
     pr = PROBLEMS[name]()
     s = Solver(params_for(pr), pr.U)

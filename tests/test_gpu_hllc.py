@@ -1,6 +1,6 @@
 """GPU parity of the HLLC solver (paper §3.2's alternative Riemann solver, after Toro 1997) against the FP64
-oracle, through the C ABI: FP64 steps and driver loops (fused unsplit launch, the separate passes of
-reflecting / hydrostatic sides with gravity, and the split sweeps) equal the oracle's bit for bit and count
+oracle, through the C ABI: FP64 steps and driver loops (fused unsplit launch, also with reflecting /
+hydrostatic sides and gravity, and the split sweeps) equal the oracle's bit for bit and count
 no iterations; FP32 steps stay within the bound of the two-shock path.
 """
 import numpy as np

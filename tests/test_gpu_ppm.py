@@ -1,6 +1,6 @@
 """GPU parity of piecewise-parabolic reconstruction (the PPM upgrade paper §3.2 points to) against the FP64
 oracle, through the C ABI: FP64 steps with either Riemann solver and driver loops (fused unsplit launch, the
-separate passes of reflecting / hydrostatic sides with gravity, and the split sweeps) equal the oracle's bit
+fused launch with reflecting / hydrostatic sides and gravity, and the split sweeps) equal the oracle's bit
 for bit; FP32 steps stay within the bound of the piecewise-linear path.
 """
 import numpy as np
