@@ -1,8 +1,9 @@
 // C-ABI layer of ensembles (include/hydro.h, hydro_batch_*): members with their own grids and time steps
 // advanced together.  Each step is three batched launches -- ghost fill of every member, CFL dt of every
-// member, and per size class one persistent CTU kernel over that class's tiles -- and hydro_batch_run
-// captures nsteps such steps into one CUDA graph, launched once.  hydro_batch_autotune times the tile
-// shapes of each size class and keeps the fastest.
+// member, and one persistent CTU kernel over the tiles of every size class that uses the same tile shape
+// (one launch when all classes share it, so small classes do not each end in a partial wave) -- and
+// hydro_batch_run captures nsteps such steps into one CUDA graph, launched once.  hydro_batch_autotune
+// times the tile shapes of each size class and keeps the fastest.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -31,6 +32,15 @@ struct SizeClass {
   unsigned int* d_queue = nullptr;
 };
 
+// Size classes that share a tile shape, stepped by one persistent launch: their tiles in class order
+// (largest classes first) behind one work queue.
+struct ShapeGroup {
+  int shape = 0;
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+  unsigned int* d_queue = nullptr;
+};
+
 }  // namespace
 
 struct hydro_batch {
@@ -50,6 +60,7 @@ struct hydro_batch {
   int4* d_dt = nullptr;
   int ndt = 0;
   std::vector<SizeClass> classes;
+  std::vector<ShapeGroup> groups;
   CUtensorMap* d_tmaps = nullptr; // FP32: two TMA descriptors per member (its buffers, its class's tile box)
   int parity = 0;                 // members' current state is U[parity]
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> executable graph
@@ -61,15 +72,54 @@ static hydro_status fail(hydro_batch* b, cudaError_t e, const char* where) {
   return HYDRO_ECUDA;
 }
 
-static cudaError_t build_tiles(hydro_batch* b, SizeClass& c, int shape) {
+// tiles (member, tile x, tile y, 0) of a class for a tile shape, appended to `tiles`
+static void class_tiles(const hydro_batch* b, const SizeClass& c, int shape, std::vector<int4>& tiles) {
   const hydro::TileShape ts = hydro::kTileShapes[shape];
   const int tx = b->precision == HYDRO_FP64 ? 16 : ts.tx, ty = b->precision == HYDRO_FP64 ? 16 : ts.ty;
-  std::vector<int4> tiles;
   for (int m : c.members) {
     const int nbx = (c.nx + tx - 1) / tx, nby = (c.ny + ty - 1) / ty;
     for (int by = 0; by < nby; ++by)
       for (int bx = 0; bx < nbx; ++bx) tiles.push_back(make_int4(m, bx, by, 0));
   }
+}
+
+static void free_groups(hydro_batch* b) {
+  for (auto& g : b->groups) {
+    if (g.d_tiles) cudaFree(g.d_tiles);
+    if (g.d_queue) cudaFree(g.d_queue);
+  }
+  b->groups.clear();
+}
+
+// one group per distinct tile shape of the classes, in the order the shapes first appear
+static cudaError_t rebuild_groups(hydro_batch* b) {
+  free_groups(b);
+  cudaError_t e = cudaSuccess;
+  std::vector<int> shapes;
+  for (const auto& c : b->classes)
+    if (std::find(shapes.begin(), shapes.end(), c.shape) == shapes.end()) shapes.push_back(c.shape);
+  for (int sh : shapes) {
+    std::vector<int4> tiles;
+    for (const auto& c : b->classes)
+      if (c.shape == sh) class_tiles(b, c, sh, tiles);
+    ShapeGroup g;
+    g.shape = sh;
+    g.ntiles = (int)tiles.size();
+    e = cudaMalloc((void**)&g.d_tiles, sizeof(int4) * std::max<size_t>(tiles.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g.d_queue, sizeof(unsigned int));
+    b->groups.push_back(g);  // owned by the batch from here on, freed with it
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->groups.back().d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+  }
+  return e;
+}
+
+static cudaError_t build_tiles(hydro_batch* b, SizeClass& c, int shape) {
+  const hydro::TileShape ts = hydro::kTileShapes[shape];
+  const int tx = b->precision == HYDRO_FP64 ? 16 : ts.tx, ty = b->precision == HYDRO_FP64 ? 16 : ts.ty;
+  std::vector<int4> tiles;
+  class_tiles(b, c, shape, tiles);
   if (c.d_tiles) cudaFree(c.d_tiles);
   c.d_tiles = nullptr;
   cudaError_t e = cudaMalloc((void**)&c.d_tiles, sizeof(int4) * std::max<size_t>(tiles.size(), 1));
@@ -100,9 +150,9 @@ static void drop_graphs(hydro_batch* b) {
 static cudaError_t enqueue_step(hydro_batch* b, int parity, cudaStream_t s) {
   cudaError_t e = hydro::batch_fill(b->precision, b->d_mem, b->d_fill, b->nfill, parity, s);
   if (e == cudaSuccess) e = hydro::batch_dt(b->precision, b->d_mem, b->d_dt, b->ndt, parity, 1, s);
-  for (auto& c : b->classes) {
+  for (auto& g : b->groups) {
     if (e != cudaSuccess) break;
-    e = hydro::batch_step(b->precision, c.shape, b->d_mem, c.d_tiles, c.ntiles, c.d_queue, parity, b->d_agg, s,
+    e = hydro::batch_step(b->precision, g.shape, b->d_mem, g.d_tiles, g.ntiles, g.d_queue, parity, b->d_agg, s,
                           nullptr, b->d_tmaps);
   }
   return e;
@@ -184,6 +234,7 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
     e = cudaMalloc((void**)&c.d_queue, sizeof(unsigned int));
     if (e == cudaSuccess) e = build_tiles(b, c, 0);
   }
+  if (e == cudaSuccess) e = rebuild_groups(b);
   if (e == cudaSuccess) e = hydro::batch_prepare(prec);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
@@ -197,6 +248,7 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
 void hydro_batch_destroy(hydro_batch* b) {
   if (!b) return;
   drop_graphs(b);
+  free_groups(b);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   for (auto& c : b->classes) {
     if (c.d_tiles) cudaFree(c.d_tiles);
@@ -250,6 +302,7 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes) 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = rebuild_groups(b);
   // the trial launches counted solves; clear the aggregate counters
   if (e == cudaSuccess) e = hydro::init_scratch(b->d_agg, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
