@@ -1,6 +1,9 @@
 // Batched kernels for ensembles of independent problems on uneven grids (one problem per member, each with
-// its own CFL time step): ghost fill and dt reduction over all members at once, and a persistent CTU step
-// kernel whose CTAs pull tiles of any member from a work queue.  Instantiated for FP32 in k_batch.cu and for
+// its own CFL time step): a dt reduction over all members at once, and a persistent fused CTU
+// step kernel whose CTAs pull tiles of any member from a work queue.  The step reads cells outside each
+// member's domain through its boundary map and folds the CFL constraint of its new cells into the member's
+// accumulator; the member's last tile advances its time and writes its next step's factors, so a run needs
+// one dt pass at its start and then one launch per step and tile shape.  Instantiated for FP32 in k_batch.cu and for
 // FP64 in k_batch_f64.cu, which is compiled without multiply-add contraction.
 #pragma once
 #include <float.h>
@@ -11,37 +14,6 @@
 #include "hydro_batch_internal.h"
 
 namespace hydro {
-
-// ---------------------------------------------------------------------------------------------------
-// Ghost cells of every member.  Block b fills 256 consecutive ghost cells of member tab[b].x starting at
-// tab[b].y, enumerated as in the single-problem kernel (bottom band, top band, left, right).
-template <typename R>
-__global__ void __launch_bounds__(256) batch_fill_kernel(const BatchMember* __restrict__ mem, const int2* __restrict__ tab,
-                                                        int parity) {
-  const int2 t = tab[blockIdx.x];
-  const BatchMember& m = mem[t.x];
-  const KParams& P = m.P;
-  R* U = (R*)m.U[parity];
-  const int band = P.ng * P.NX;
-  const int side = P.ny * P.ng;
-  const int n = 2 * band + 2 * side;
-  const int e = t.y + threadIdx.x;
-  if (e >= n) return;
-  int i, j;
-  if (e < band) {
-    j = e / P.NX; i = e % P.NX;
-  } else if (e < 2 * band) {
-    const int f = e - band;
-    j = P.ng + P.ny + f / P.NX; i = f % P.NX;
-  } else if (e < 2 * band + side) {
-    const int f = e - 2 * band;
-    j = P.ng + f / P.ng; i = f % P.ng;
-  } else {
-    const int f = e - 2 * band - side;
-    j = P.ng + f / P.ng; i = P.ng + P.nx + f % P.ng;
-  }
-  fill_ghost_cell(P, U, i, j, (size_t)P.NY * P.pitch);
-}
 
 // ---------------------------------------------------------------------------------------------------
 // CFL dt of every member.  Block b reduces BATCH_DT_CELLS cells of member tab[b].x from cell tab[b].y;
@@ -99,6 +71,7 @@ __global__ void __launch_bounds__(256) batch_dt_kernel(const BatchMember* __rest
     const double dt = P.cfl * __longlong_as_double((long long)bits);
     scr->dt = dt;
     scr->sc = make_step_scalars(dt, P.dx, P.dy, P.grav);
+    scr->scf[parity] = scr->sc;  // the factors the fused step at this parity reads
     if (advance) {
       scr->t = scr->t + dt;
       scr->nsteps = scr->nsteps + 1;
@@ -108,16 +81,43 @@ __global__ void __launch_bounds__(256) batch_dt_kernel(const BatchMember* __rest
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Persistent CTU step over a tile list (member, tile x, tile y), largest members first: each CTA takes
-// the next tile from an atomic queue until the list is exhausted.
+// One tile of a member is done: fold its CFL minimum into the member's accumulator; the member's last tile
+// (of `ntiles`) turns the minimum into the next step's factors scf[1 - parity] and, if advance, adds this
+// step to the member's time.  Not inlined: one thread per tile calls it, and the step loop's registers stay
+// those of the tile.
+static __device__ __noinline__ void member_tile_done(const BatchMember& m, double tile_min, int ntiles, int parity,
+                                              int advance) {
+  DevScratch* scr = m.scr;
+  atomicMin(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong(tile_min));
+  __threadfence();
+  if (atomicAdd(&scr->step_blocks_done, 1u) != (unsigned int)ntiles - 1u) return;
+  __threadfence();
+  const unsigned long long bits = atomicExch(&scr->dtn_min_bits, (unsigned long long)__double_as_longlong(DBL_MAX));
+  if (advance) {
+    scr->t = scr->t + scr->scf[parity].dt;
+    scr->nsteps = scr->nsteps + 1;
+  }
+  const double dt = m.P.cfl * __longlong_as_double((long long)bits);
+  scr->dt = dt;
+  scr->sc = make_step_scalars(dt, m.P.dx, m.P.dy, m.P.grav);
+  scr->scf[1 - parity] = scr->sc;
+  scr->step_blocks_done = 0u;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Persistent fused CTU step over a tile list (member, tile x, tile y, the member's tile count), largest
+// members first: each CTA takes the next tile from an atomic queue until the list is exhausted.  A tile
+// reads the member's factors scf[parity], folds its cells' CFL minimum into the member's accumulator, and
+// the member's last tile sets its next factors scf[1 - parity] (and, if advance, its time and step count).
 template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(const BatchMember* __restrict__ mem,
                                                        const int4* __restrict__ tiles, int ntiles,
                                                        unsigned int* __restrict__ queue, int parity,
                                                        DevScratch* __restrict__ agg,
-                                                       const CUtensorMap* __restrict__ tmaps) {
+                                                       const CUtensorMap* __restrict__ tmaps, int advance) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int cur;
+  __shared__ R wmin[NT / 32];
   TileCounters cnt;
   while (true) {
     if (threadIdx.x == 0) cur = (int)atomicAdd(queue, 1u);
@@ -129,11 +129,23 @@ __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(con
     SP<R> s;
     s.load(m.P);
     StepFactors<R> f;
-    f.load(m.scr->sc);
+    f.load(m.scr->scf[parity]);
     const CUtensorMap* tm = (tmaps != nullptr && m.tma) ? tmaps + 2 * t.x + parity : nullptr;
-    ctu_tile<R, TX, TY, NT, FACE_PLAIN, false, true>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y,
-                                                     t.z, smem_raw, cnt,
-                            FaceHook{}, nullptr, nullptr, tm);
+    R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
+    ctu_tile<R, TX, TY, NT, FACE_PLAIN, true, true>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z,
+                                                    smem_raw, cnt, FaceHook{}, nullptr, &cmin, tm);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const R o = __shfl_xor_sync(0xffffffffu, cmin, off);
+      cmin = o < cmin ? o : cmin;
+    }
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = cmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R b = wmin[0];
+      for (int w = 1; w < NT / 32; ++w) b = wmin[w] < b ? wmin[w] : b;
+      member_tile_done(m, (double)b, t.w, parity, advance);
+    }
     __syncthreads();  // the tile's last shared-memory reads finish before the next tile's loads
   }
   if (cnt.nonconv) cnt.flags |= STATUS_NONCONV;
@@ -173,8 +185,8 @@ struct BatchStep {
     return cudaSuccess;
   }
   static cudaError_t launch(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
-                            DevScratch* agg, cudaStream_t stream, int* grid_out,
-                            const CUtensorMap* tmaps = nullptr) {
+                            DevScratch* agg, cudaStream_t stream, int* grid_out, const CUtensorMap* tmaps,
+                            int advance) {
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
@@ -188,7 +200,7 @@ struct BatchStep {
     e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), stream);
     if (e != cudaSuccess) return e;
     batch_step_kernel<R, TX, TY, NT><<<grid, NT, TileLayout<R, TX, TY>::bytes, stream>>>(mem, tiles, ntiles, queue,
-                                                                                         parity, agg, tmaps);
+                                                                                         parity, agg, tmaps, advance);
     return cudaGetLastError();
   }
 };

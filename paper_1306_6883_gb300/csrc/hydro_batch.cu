@@ -1,8 +1,9 @@
 // C-ABI layer of ensembles (include/hydro.h, hydro_batch_*): members with their own grids and time steps
-// advanced together.  Each step is three batched launches -- ghost fill of every member, CFL dt of every
-// member, and one persistent CTU kernel over the tiles of every size class that uses the same tile shape
-// (one launch when all classes share it, so small classes do not each end in a partial wave) -- and
-// hydro_batch_run captures nsteps such steps into one CUDA graph, launched once.  hydro_batch_autotune
+// advanced together.  A run of n steps is one CFL dt pass over every member and then, per step, one
+// persistent fused CTU kernel over the tiles of every size class that uses the same tile shape (one launch
+// when all classes share it, so small classes do not each end in a partial wave); the step reads ghost cells
+// through each member's boundary map and reduces each member's next dt.  hydro_batch_run captures such a
+// run into one CUDA graph, launched once.  hydro_batch_autotune
 // times the tile shapes of each size class and keeps the fastest.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -55,8 +56,6 @@ struct hydro_batch {
   DevScratch* d_agg = nullptr;    // aggregate counters of the step kernels
   DevScratch* h_scr = nullptr;    // pinned host mirror of one scratch block
   double* d_partials = nullptr;   // totals partials
-  int2* d_fill = nullptr;
-  int nfill = 0;
   int4* d_dt = nullptr;
   int ndt = 0;
   std::vector<SizeClass> classes;
@@ -79,7 +78,7 @@ static void class_tiles(const hydro_batch* b, const SizeClass& c, int shape, std
   for (int m : c.members) {
     const int nbx = (c.nx + tx - 1) / tx, nby = (c.ny + ty - 1) / ty;
     for (int by = 0; by < nby; ++by)
-      for (int bx = 0; bx < nbx; ++bx) tiles.push_back(make_int4(m, bx, by, 0));
+      for (int bx = 0; bx < nbx; ++bx) tiles.push_back(make_int4(m, bx, by, nbx * nby));
   }
 }
 
@@ -146,15 +145,16 @@ static void drop_graphs(hydro_batch* b) {
   b->graphs.clear();
 }
 
-// one step of every member at the given parity on stream s (used directly and under stream capture)
-static cudaError_t enqueue_step(hydro_batch* b, int parity, cudaStream_t s) {
-  cudaError_t e = hydro::batch_fill(b->precision, b->d_mem, b->d_fill, b->nfill, parity, s);
-  if (e == cudaSuccess) e = hydro::batch_dt(b->precision, b->d_mem, b->d_dt, b->ndt, parity, 1, s);
-  for (auto& g : b->groups) {
-    if (e != cudaSuccess) break;
-    e = hydro::batch_step(b->precision, g.shape, b->d_mem, g.d_tiles, g.ntiles, g.d_queue, parity, b->d_agg, s,
-                          nullptr, b->d_tmaps);
-  }
+// nsteps steps of every member from parity p0 on stream s (used directly and under stream capture): the dt
+// of the current states, then the fused steps, each handing its members' next factors to the following one
+static cudaError_t enqueue_run(hydro_batch* b, int nsteps, int p0, cudaStream_t s) {
+  cudaError_t e = hydro::batch_dt(b->precision, b->d_mem, b->d_dt, b->ndt, p0, 0, s);
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
+    for (auto& g : b->groups) {
+      if (e != cudaSuccess) break;
+      e = hydro::batch_step(b->precision, g.shape, b->d_mem, g.d_tiles, g.ntiles, g.d_queue, (p0 + k) & 1, b->d_agg,
+                            s, nullptr, b->d_tmaps, 1);
+    }
   return e;
 }
 
@@ -192,7 +192,6 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
   }
   // member table: the same kernel parameters a single-problem context would use
   b->hmem.resize(n);
-  std::vector<int2> fill;
   std::vector<int4> dtab;
   std::map<std::pair<int, int>, int> class_of;
   for (int i = 0; i < n; ++i) {
@@ -203,8 +202,6 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
     m.U[0] = d_states[i];
     m.U[1] = d_states_alt[i];
     m.scr = b->d_scr + i;
-    const int ghosts = 2 * p.ng * m.P.NX + 2 * p.ny * p.ng;
-    for (int s = 0; s < ghosts; s += 256) fill.push_back(make_int2(i, s));
     const int cells = p.nx * p.ny;
     const int nb = (cells + hydro::BATCH_DT_CELLS - 1) / hydro::BATCH_DT_CELLS;
     for (int s = 0; s < nb; ++s) dtab.push_back(make_int4(i, s * hydro::BATCH_DT_CELLS, nb, 0));
@@ -221,12 +218,9 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
   // largest classes first, so their tiles start early
   std::sort(b->classes.begin(), b->classes.end(),
             [](const SizeClass& a, const SizeClass& c) { return (long long)a.nx * a.ny > (long long)c.nx * c.ny; });
-  b->nfill = (int)fill.size();
   b->ndt = (int)dtab.size();
   e = cudaMemcpy(b->d_mem, b->hmem.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && prec == HYDRO_FP32) e = cudaMalloc((void**)&b->d_tmaps, sizeof(CUtensorMap) * 2 * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_fill, sizeof(int2) * std::max(b->nfill, 1));
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_fill, fill.data(), sizeof(int2) * b->nfill, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_dt, sizeof(int4) * std::max(b->ndt, 1));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_dt, dtab.data(), sizeof(int4) * b->ndt, cudaMemcpyHostToDevice);
   for (auto& c : b->classes) {
@@ -259,7 +253,6 @@ void hydro_batch_destroy(hydro_batch* b) {
   if (b->d_agg) cudaFree(b->d_agg);
   if (b->h_scr) cudaFreeHost(b->h_scr);
   if (b->d_partials) cudaFree(b->d_partials);
-  if (b->d_fill) cudaFree(b->d_fill);
   if (b->d_dt) cudaFree(b->d_dt);
   if (b->d_tmaps) cudaFree(b->d_tmaps);
   delete b;
@@ -268,8 +261,7 @@ void hydro_batch_destroy(hydro_batch* b) {
 hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes) {
   if (!b || reps < 1) return HYDRO_EINVAL;
   // valid step factors for the current state, without advancing time
-  cudaError_t e = hydro::batch_fill(b->precision, b->d_mem, b->d_fill, b->nfill, b->parity, b->stream);
-  if (e == cudaSuccess) e = hydro::batch_dt(b->precision, b->d_mem, b->d_dt, b->ndt, b->parity, 0, b->stream);
+  cudaError_t e = hydro::batch_dt(b->precision, b->d_mem, b->d_dt, b->ndt, b->parity, 0, b->stream);
   if (e != cudaSuccess) return fail(b, e, "autotune set-up");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -285,7 +277,7 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes) 
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
         if (r == 1) cudaEventRecord(e0, b->stream);
         e = hydro::batch_step(b->precision, sh, b->d_mem, c.d_tiles, c.ntiles, c.d_queue, b->parity, b->d_agg,
-                              b->stream, nullptr, b->d_tmaps);
+                              b->stream, nullptr, b->d_tmaps, 0);
       }
       cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -331,7 +323,7 @@ hydro_status hydro_batch_run(hydro_batch* b, int nsteps, int use_graph) {
   if (nsteps == 0) return HYDRO_OK;
   cudaError_t e = cudaSuccess;
   if (!use_graph) {
-    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(b, (b->parity + k) & 1, b->stream);
+    e = enqueue_run(b, nsteps, b->parity, b->stream);
   } else {
     auto key = std::make_pair(nsteps, b->parity);
     auto it = b->graphs.find(key);
@@ -342,7 +334,7 @@ hydro_status hydro_batch_run(hydro_batch* b, int nsteps, int use_graph) {
       if (e != cudaSuccess) return fail(b, e, "capture stream");
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
-      for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(b, (b->parity + k) & 1, b->capture_stream);
+      if (e == cudaSuccess) e = enqueue_run(b, nsteps, b->parity, b->capture_stream);
       cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
       if (e == cudaSuccess) e = e2;
       cudaGraphExec_t ge = nullptr;

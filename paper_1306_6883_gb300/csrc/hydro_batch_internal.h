@@ -23,18 +23,18 @@ struct TileShape {
 extern const TileShape kTileShapes[];
 extern const int kNumTileShapes;
 
-// tab[b] = (member, first ghost cell) for each 256-cell block
-cudaError_t batch_fill(int precision, const BatchMember* mem, const int2* tab, int nblocks, int parity,
-                       cudaStream_t stream);
-// tab[b] = (member, first cell, member's block count, 0); advance = 0 leaves time and step count alone
+// tab[b] = (member, first cell, member's block count, 0); advance = 0 leaves time and step count alone; the
+// member's factors are also written to scf[parity] for the fused step
 cudaError_t batch_dt(int precision, const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
                      cudaStream_t stream);
-// tiles[k] = (member, tile x, tile y, 0) for tile shape `shape` (FP64 always uses 16 x 16)
+// tiles[k] = (member, tile x, tile y, the member's tile count) for tile shape `shape` (FP64 always uses
+// 16 x 16).  The fused step: reads each member's factors scf[parity] (set by batch_dt or by the previous
+// step), and the member's last tile writes scf[1 - parity] and, if advance, adds the step to its time.
 // tmaps (FP32, may be NULL): device array of two TMA descriptors per member (one per state buffer) with the
 // box of `shape`, used for members whose tma flag is set
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
                        unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out,
-                       const CUtensorMap* tmaps = nullptr);
+                       const CUtensorMap* tmaps, int advance);
 // set the kernel attributes of every shape (call once before any stream capture)
 cudaError_t batch_prepare(int precision);
 
@@ -42,7 +42,7 @@ cudaError_t batch_prepare(int precision);
 cudaError_t batch_dt_f64(const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
                          cudaStream_t stream);
 cudaError_t batch_step_f64(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
-                           DevScratch* agg, cudaStream_t stream, int* grid_out);
+                           DevScratch* agg, cudaStream_t stream, int* grid_out, int advance);
 cudaError_t batch_prepare_f64();
 
 }  // namespace hydro

@@ -6,16 +6,6 @@ namespace hydro {
 // ---------------------------------------------------------------------------------------------------
 // launchers
 
-cudaError_t batch_fill(int precision, const BatchMember* mem, const int2* tab, int nblocks, int parity,
-                       cudaStream_t stream) {
-  if (nblocks <= 0) return cudaSuccess;
-  if (precision == 0)
-    batch_fill_kernel<double><<<nblocks, 256, 0, stream>>>(mem, tab, parity);
-  else
-    batch_fill_kernel<float><<<nblocks, 256, 0, stream>>>(mem, tab, parity);
-  return cudaGetLastError();
-}
-
 cudaError_t batch_dt(int precision, const BatchMember* mem, const int4* tab, int nblocks, int parity, int advance,
                      cudaStream_t stream) {
   if (nblocks <= 0) return cudaSuccess;
@@ -32,18 +22,18 @@ const int kNumTileShapes = sizeof(kTileShapes) / sizeof(kTileShapes[0]);
 
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
                        unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out,
-                       const CUtensorMap* tmaps) {
+                       const CUtensorMap* tmaps, int advance) {
   if (precision == 0)  // the FP64 path keeps one shape (its cost is the FP64 pipe, not the tile)
-    return batch_step_f64(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+    return batch_step_f64(mem, tiles, ntiles, queue, parity, agg, stream, grid_out, advance);
   switch (shape) {
     case 0: return BatchStep<float, 32, 16, 384>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
-                                                              tmaps);
+                                                              tmaps, advance);
     case 1: return BatchStep<float, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
-                                                              tmaps);
+                                                              tmaps, advance);
     case 2: return BatchStep<float, 32, 8, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
-                                                              tmaps);
+                                                              tmaps, advance);
     case 3: return BatchStep<float, 32, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
-                                                              tmaps);
+                                                              tmaps, advance);
     default: return cudaErrorInvalidValue;
   }
 }

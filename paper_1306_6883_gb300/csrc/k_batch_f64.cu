@@ -11,8 +11,9 @@ cudaError_t batch_dt_f64(const BatchMember* mem, const int4* tab, int nblocks, i
 }
 
 cudaError_t batch_step_f64(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
-                           DevScratch* agg, cudaStream_t stream, int* grid_out) {
-  return BatchStep<double, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out);
+                           DevScratch* agg, cudaStream_t stream, int* grid_out, int advance) {
+  return BatchStep<double, 16, 16, 256>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out, nullptr,
+                                                advance);
 }
 
 cudaError_t batch_prepare_f64() { return BatchStep<double, 16, 16, 256>::prepare(); }
