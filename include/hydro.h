@@ -185,8 +185,8 @@ hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
  * hydro_step_fused(tmax) does, and the new state written to host_out (layout of hydro_download; must not
  * be host_in).  The fused step runs as four launches over bands of tile rows on the context's own streams,
  * and each band's rows are copied back while later bands compute.  Returns when host_out holds the new
- * state.  Contexts whose fused step takes the separate passes (learned model, harvest, split = 1) run
- * upload, hydro_step_fused and hydro_download in turn.  Same results as those three calls. */
+ * state.  Contexts with a learned model, a harvest or split = 1 run upload, hydro_step_fused and
+ * hydro_download in turn.  Same results as those three calls. */
 hydro_status hydro_step_host(hydro_ctx* ctx, const void* host_in, void* host_out, double tmax);
 
 /* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */
@@ -292,10 +292,11 @@ hydro_status hydro_set_harvest_gate(hydro_ctx* ctx, double gate_dp, double gate_
 /* ---- Ensembles of independent problems (uneven grids, own time steps) ----------------------------
  * Not in the paper, which runs one problem at a time; this batches many independent copies of the §2
  * driver loop.  Each member has its own parameters (all members share one precision) and two caller-owned
- * state buffers, as for hydro_init.  One ensemble step = ghost fill of every member, CFL dt of every
- * member (its own), and one CTU step of every member with its own dt; the step runs as one persistent
- * kernel per size class (members with the same nx x ny) whose CTAs take tiles of any member of the class
- * from a work queue. */
+ * state buffers, as for hydro_init.  A run of n steps = the CFL dt of every member (its own), then n fused
+ * CTU steps of every member with its own dt: each step runs as one persistent kernel per tile shape whose
+ * CTAs take tiles of any member from a work queue, read ghost cells through the member's boundary map, and
+ * reduce the member's next dt (the member's last tile hands it on).  Ghost cells of the states are not
+ * filled. */
 typedef struct hydro_batch hydro_batch;
 
 /* Create an ensemble of n members.  params, d_states, d_states_alt: arrays of n entries.  Members take the
@@ -306,7 +307,7 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
                                 void* cuda_stream, hydro_batch** out);
 void hydro_batch_destroy(hydro_batch* b);
 
-/* Project autotuner: for every size class time `reps` launches of each candidate tile shape on the
+/* Tile-shape autotuner: for every size class time `reps` launches of each candidate tile shape on the
  * current states (without advancing them) and keep the fastest.  chosen_shapes (optional) receives one
  * shape id per class.  Synchronises.  Cached graphs are dropped. */
 hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes);
