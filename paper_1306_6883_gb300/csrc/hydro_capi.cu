@@ -588,16 +588,31 @@ static cudaError_t make_host_pipe(hydro_ctx* c) {
   if (c->host_pipe) return cudaSuccess;
   int least = 0, greatest = 0;
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming);
+  cudaStream_t streams[hydro_ctx::HOST_BANDS + 1] = {};
+  cudaEvent_t events[hydro_ctx::HOST_BANDS + 1] = {};
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&streams[hydro_ctx::HOST_BANDS], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&events[hydro_ctx::HOST_BANDS], cudaEventDisableTiming);
   for (int b = 0; b < hydro_ctx::HOST_BANDS && e == cudaSuccess; ++b) {
     // priorities run from `greatest` (numerically lowest) to `least`
     const int prio = greatest + b < least ? greatest + b : least;
-    e = cudaStreamCreateWithPriority(&c->band_stream[b], cudaStreamNonBlocking, prio);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_band[b], cudaEventDisableTiming);
+    e = cudaStreamCreateWithPriority(&streams[b], cudaStreamNonBlocking, prio);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&events[b], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) c->host_pipe = 1;  // (a partial failure leaks the objects created so far)
-  return e;
+  if (e != cudaSuccess) {  // release whatever was created
+    for (int b = 0; b <= hydro_ctx::HOST_BANDS; ++b) {
+      if (streams[b]) cudaStreamDestroy(streams[b]);
+      if (events[b]) cudaEventDestroy(events[b]);
+    }
+    return e;
+  }
+  for (int b = 0; b < hydro_ctx::HOST_BANDS; ++b) {
+    c->band_stream[b] = streams[b];
+    c->ev_band[b] = events[b];
+  }
+  c->d2h_stream = streams[hydro_ctx::HOST_BANDS];
+  c->ev_ready = events[hydro_ctx::HOST_BANDS];
+  c->host_pipe = 1;
+  return cudaSuccess;
 }
 
 hydro_status hydro_step_host(hydro_ctx* c, const void* host_in, void* host_out, double tmax) {
