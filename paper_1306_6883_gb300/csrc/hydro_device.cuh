@@ -466,7 +466,13 @@ __device__ __forceinline__ void trace_ppm(const SP<R>& s, R sigma, const R q[4],
       ref[m] = eR[m] - (R)0.5 * s4 * (da[m] - ((R)1 - two3 * s4) * a6[m]);
       o[m] = ref[m];
     }
-    auto dif = [&](int m, R sn) { return ref[m] - (eR[m] - (R)0.5 * sn * (da[m] - ((R)1 - two3 * sn) * a6[m])); };
+    // ref - Ip(sn); FP32 in the factored form 0.5 (sn - s4)(da - a6 (1 - 2 (sn + s4) / 3))
+    auto dif = [&](int m, R sn) {
+      if constexpr (is_f32<R>())
+        return 0.5f * (sn - s4) * (da[m] - a6[m] * (1.0f - two3 * (sn + s4)));
+      else
+        return ref[m] - (eR[m] - (R)0.5 * sn * (da[m] - ((R)1 - two3 * sn) * a6[m]));
+    };
     if (lam1 >= (R)0) {
       const R sn = sigma * lam1;
       const R b = -roc * dif(1, sn) + ic2h * dif(3, sn);
@@ -500,7 +506,13 @@ __device__ __forceinline__ void trace_ppm(const SP<R>& s, R sigma, const R q[4],
       ref[m] = eL[m] + (R)0.5 * s1 * (da[m] + ((R)1 - two3 * s1) * a6[m]);
       o[m] = ref[m];
     }
-    auto dif = [&](int m, R sn) { return ref[m] - (eL[m] + (R)0.5 * sn * (da[m] + ((R)1 - two3 * sn) * a6[m])); };
+    // ref - Im(sn); FP32 in the factored form 0.5 (s1 - sn)(da + a6 (1 - 2 (sn + s1) / 3))
+    auto dif = [&](int m, R sn) {
+      if constexpr (is_f32<R>())
+        return 0.5f * (s1 - sn) * (da[m] + a6[m] * (1.0f - two3 * (sn + s1)));
+      else
+        return ref[m] - (eL[m] + (R)0.5 * sn * (da[m] + ((R)1 - two3 * sn) * a6[m]));
+    };
     if (lam1 <= (R)0) {
       const R sn = -sigma * lam1;
       const R b = -roc * dif(1, sn) + ic2h * dif(3, sn);
