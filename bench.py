@@ -437,6 +437,23 @@ def cpu_baseline(pr, budget_s=12.0, max_steps=50):
                                         f"{el:.1f} s, FP64"}
 
 
+def cpu_variant(pr, steps=5, **kw):
+    """The oracle beside a variant leg: `steps` whole FP64 steps of the same workload with the same options
+    (split, riemann_solver, reconstruction; gravity from the problem), on all host cores."""
+    import oracle
+
+    xmin, xmax, ymin, ymax = pr.domain
+    p = oracle.params(pr.nx, pr.ny, bc=pr.bc, gamma=pr.gamma, cfl=pr.cfl, xmin=xmin, xmax=xmax, ymin=ymin,
+                      ymax=ymax, grav=pr.grav, riemann_solver=kw.get("riemann_solver", 0),
+                      reconstruction=kw.get("reconstruction", 0))
+    U = pr.U.copy()
+    t0 = time.perf_counter()
+    oracle.advance(p, U, nsteps=steps, split=bool(kw.get("split")))
+    el = time.perf_counter() - t0
+    return {"value": pr.nx * pr.ny * steps / el, "unit": "zone-updates/s", "cores": oracle.num_threads(),
+            "sample": f"{steps} whole FP64 steps, {el:.2f} s"}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -478,6 +495,11 @@ def run_ours(args, world, rank, local):
         rt = {"workload": rtname, "steps": 20, "value": prt.nx * prt.ny * 20 / (sum(r["step_ms"]) / 1e3),
               "ms_per_step": sum(r["step_ms"]) / 20, "launches_per_step": r["launches_per_step"],
               "riemann_iters_per_solve": r["iters_per_solve"]}
+        if world == 1:  # the oracle beside each variant leg, on a single-GPU run only
+            ppm["cpu_oracle"] = cpu_variant(pr, reconstruction=1)
+            hllc["cpu_oracle"] = cpu_variant(pr, riemann_solver=1)
+            split["cpu_oracle"] = cpu_variant(pr, split=1)
+            rt["cpu_oracle"] = cpu_variant(prt, steps=2)
     learned = None
     if args.precision == "fp32":
         model, training = harvest_and_train()
