@@ -183,7 +183,7 @@ hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
 /* One step with host-resident state: host_in (pinned, layout of hydro_upload) is uploaded, stepped as
  * hydro_step_fused(tmax) does, and the new state written to host_out (layout of hydro_download; must not
- * be host_in).  The fused step runs as four launches over bands of tile rows on the context's own streams,
+ * be host_in).  The fused step runs as five launches over bands of tile rows on the context's own streams,
  * and each band's rows are copied back while later bands compute.  Returns when host_out holds the new
  * state.  Contexts with a learned model, a harvest or split = 1 run upload, hydro_step_fused and
  * hydro_download in turn.  Same results as those three calls. */

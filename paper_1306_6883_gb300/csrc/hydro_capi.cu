@@ -40,8 +40,8 @@ struct hydro_ctx {
   unsigned long long split_steps;  // split variant: steps taken (x sweep first on even counts)
   // hydro_step_host: streams for the bands of the fused step and for their downloads, and their events
   // (created on first use).  KH 1024^2 FP32 step from and to pinned host memory: 291 us as three calls,
-  // 245 us with four bands, 255 us with eight.
-  static constexpr int HOST_BANDS = 4;
+  // 245 us with four equal bands, 255 us with eight, 241 us with five of 1/8, 1/8, 1/4, 1/4, 1/4.
+  static constexpr int HOST_BANDS = 5;
   int host_pipe;
   cudaStream_t band_stream[HOST_BANDS];
   cudaStream_t d2h_stream;
@@ -640,7 +640,11 @@ hydro_status hydro_step_host(hydro_ctx* c, const void* host_in, void* host_out, 
   const unsigned char* out = (const unsigned char*)c->state[1 - c->cur];
   unsigned char* host = (unsigned char*)host_out;
   for (int b = 0; b < nb && e == cudaSuccess; ++b) {
-    const int y0 = b * ty / nb, y1 = (b + 1) * ty / nb;
+    // bands of 1/8, 1/8, 1/4, 1/4 and 1/4 of the tile rows (small first bands start the copies back early);
+    // grids of fewer than 8 tile rows split evenly
+    static const int eighths[hydro_ctx::HOST_BANDS + 1] = {0, 1, 2, 4, 6, 8};
+    const int y0 = ty >= 8 ? ty * eighths[b] / 8 : b * ty / nb;
+    const int y1 = ty >= 8 ? ty * eighths[b + 1] / 8 : (b + 1) * ty / nb;
     cudaStream_t bs = c->band_stream[b];
     e = cudaStreamWaitEvent(bs, c->ev_ready, 0);
     if (e == cudaSuccess)
