@@ -898,6 +898,10 @@ done:
  *   5. Riemann solves at the interior faces of the line;
  *   6. artificial viscosity with the divergence along the line, (u_m - u_{m-1}) / h;
  *   7. conservative update of the line's interior cells, U += sigma (F_{m-1/2} - F_{m+1/2}).
+ * Gravity (along y): as in the unsplit step, every traced state's v gains dt g / 2 (transverse in the x
+ * sweep, normal in the y sweep); the time-centred sources (rho v) += dt g (rho^n + rho^{n+1}) / 2,
+ * (rho E) += dt g ((rho v)^n + (rho v)^{n+1}) / 2 are added once per step, by the y sweep, with n the state
+ * the y sweep starts from.
  * The state must be ghost-filled on entry.  Lines are independent; each keeps its own work arrays. */
 static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_stats* st) {
   const int ng = p->ng, nx = p->nx, ny = p->ny, NX = nx + 2 * ng, NY = ny + 2 * ng;
@@ -910,6 +914,7 @@ static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_s
   const size_t sl = dir == 0 ? (size_t)NX : 1;  /* stride between lines */
   const int kn = dir == 0 ? 1 : 2, kt = dir == 0 ? 2 : 1;  /* normal and transverse momentum components */
   const double sigma = dt / h;
+  const double hdtg = 0.5 * dt * p->grav;
   long long n_solves = 0, n_iters = 0, n_nonconv = 0;
   int max_iters = 0, err = 0;
 
@@ -966,6 +971,11 @@ static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_s
         for (int t = 0; t < 5; ++t) a5[k][t] = q[k * N + m - 2 + t];
       }
       trace_cell(p, sigma, qc, d4, (const double(*)[5])a5, xi[m], a, b);
+      if (p->grav != 0.0) { /* half-step gravity on v: transverse in the x sweep, normal in the y sweep */
+        const int kv = dir == 0 ? 2 : 1;
+        a[kv] = a[kv] + hdtg;
+        b[kv] = b[kv] + hdtg;
+      }
       for (int k = 0; k < 4; ++k) {
         ql[k * N + m] = a[k];
         qr[k * N + m] = b[k];
@@ -996,9 +1006,15 @@ static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_s
       }
       for (int k = 0; k < 4; ++k) G[k * (N + 1) + f] = Gf[k];
     }
-    /* 7. update */
-    for (int m = ng; m < ng + n; ++m)
+    /* 7. update; the y sweep adds the time-centred gravity sources as the unsplit step does */
+    for (int m = ng; m < ng + n; ++m) {
+      const double rho_n = C(0, m), my_n = C(2, m);
       for (int k = 0; k < 4; ++k) C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m] - G[k * (N + 1) + m + 1]);
+      if (dir == 1 && p->grav != 0.0) {
+        C(2, m) = C(2, m) + hdtg * (rho_n + C(0, m));
+        C(3, m) = C(3, m) + hdtg * (my_n + C(2, m));
+      }
+    }
 #undef C
     free(w);
   }
@@ -1013,7 +1029,6 @@ static int sweep(const oracle_params* p, double* U, double dt, int dir, oracle_s
 
 int oracle_step_split(const oracle_params* p, double* U, double dt, int first_dir, oracle_stats* st) {
   if (!params_ok(p) || !U || !(dt >= 0.0) || (first_dir != 0 && first_dir != 1)) return 1;
-  if (p->grav != 0.0) return 1; /* the split variant is defined here without source terms */
   int err = sweep(p, U, dt, first_dir, st);
   if (!err) err = oracle_fill_ghost(p, U);
   if (!err) err = sweep(p, U, dt, 1 - first_dir, st);

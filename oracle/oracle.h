@@ -50,7 +50,7 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st);
 int oracle_conserved_totals(const oracle_params* p, const double* U, double out[4]);
 /* Dimensionally split step (§3.1): a one-dimensional sweep along first_dir (0: x, 1: y), a ghost fill of
  * the intermediate state, then a sweep along the other direction, each with the full dt.  The caller
- * alternates first_dir from step to step.  U must be ghost-filled on entry; grav must be 0. */
+ * alternates first_dir from step to step.  U must be ghost-filled on entry.  Gravity acts in the y sweep. */
 int oracle_step_split(const oracle_params* p, double* U, double dt, int first_dir, oracle_stats* st);
 
 /* ---- per-cell / per-face stages, exported so tests can pin each one on its own ---- */

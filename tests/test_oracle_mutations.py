@@ -67,6 +67,8 @@ MUTATIONS = {
     "ppm: reference state from the slowest wave": [
         ("double s4 = sigma * lam[3] > 0.0 ? sigma * lam[3] : 0.0;",
          "double s4 = sigma * lam[1] > 0.0 ? sigma * lam[1] : 0.0;")],
+    "split: gravity sources in both sweeps": [
+        ("      if (dir == 1 && p->grav != 0.0) {\n        C(2, m)", "      if (p->grav != 0.0) {\n        C(2, m)")],
     "split: flux difference reversed": [
         ("C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m] - G[k * (N + 1) + m + 1]);",
          "C(k, m) = C(k, m) + sigma * (G[k * (N + 1) + m + 1] - G[k * (N + 1) + m]);")],
