@@ -96,8 +96,9 @@ typedef struct {
   int split;                        /* 0: unsplit CTU step (default).  1: dimensionally split step (paper
                                        §3.1: a one-dimensional sweep along x and one along y, each acting on
                                        the state the other left; the context's k-th step, counted from
-                                       hydro_init, sweeps x first when k is even).  Needs grav = 0 and
-                                       use_learned_guess = 0; single problems only (not hydro_batch_*). */
+                                       hydro_init, sweeps x first when k is even; gravity's sources are
+                                       added by the y sweep).  Needs use_learned_guess = 0; single problems
+                                       only (not hydro_batch_*). */
   int riemann_solver;               /* hydro_riemann: the two-shock iteration (default) or HLLC (§3.2 names
                                        both; HLLC needs use_learned_guess = 0, no harvest, and is for single
                                        problems only, not hydro_batch_*) */

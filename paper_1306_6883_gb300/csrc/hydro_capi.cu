@@ -142,7 +142,6 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
   if (p->use_learned_guess != 0 && p->use_learned_guess != 1) BAD("use_learned_guess must be 0 or 1");
   if (p->use_learned_guess == 1 && p->precision != HYDRO_FP32) BAD("the learned proposal is an FP32 path");
   if (p->split != 0 && p->split != 1) BAD("split must be 0 or 1");
-  if (p->split == 1 && p->grav != 0.0) BAD("the split variant has no gravity source");
   if (p->split == 1 && p->use_learned_guess != 0) BAD("the split variant has no learned proposal");
   if (p->riemann_solver != HYDRO_RIEMANN_TWO_SHOCK && p->riemann_solver != HYDRO_RIEMANN_HLLC)
     BAD("riemann_solver must be HYDRO_RIEMANN_TWO_SHOCK or HYDRO_RIEMANN_HLLC");

@@ -7,6 +7,9 @@
 //   2. limited slopes along the line times xi, characteristic tracing (Eq. 13) with sigma = dt / h;
 //   3. Riemann solves at the faces, artificial viscosity from the divergence along the line;
 //   4. conservative update U += sigma (F_{m-1/2} - F_{m+1/2}).
+// Gravity (along y): every traced v gains dt g / 2 (transverse in the x sweep, normal in the y sweep), and
+// the y sweep adds the time-centred sources (rho v) += dt g (rho^n + rho^{n+1}) / 2 and (rho E) +=
+// dt g ((rho v)^n + (rho v)^{n+1}) / 2, n being the state it starts from.
 // A CTA takes NL lines of LN cells along the sweep (plus the 4 halo cells each side the flattening needs).
 // Halo cells outside the domain are read through the boundary conditions' map of the interior (bc_cell: the
 // values a ghost fill would write), so neither sweep needs a ghost-fill pass.  FUSED (the second sweep of a
@@ -92,6 +95,11 @@ __global__ void __launch_bounds__(NT, HYDRO_SWEEP_MINB) sweep_kernel(KParams P, 
   else
     sigma = DIR == 0 ? sc.sigx : sc.sigy;
   const R h = DIR == 0 ? s.dx : s.dy;
+  R hdtg;  // dt g / 2
+  if constexpr (is_f32<R>())
+    hdtg = sc.hdtg_f;
+  else
+    hdtg = sc.hdtg;
   const int n = DIR == 0 ? P.nx : P.ny;      // interior cells along a line
   const int nlines = DIR == 0 ? P.ny : P.nx;
   const int bt = DIR == 0 ? blockIdx.x : blockIdx.y;  // tile along the sweep
@@ -200,6 +208,11 @@ __global__ void __launch_bounds__(NT, HYDRO_SWEEP_MINB) sweep_kernel(KParams P, 
       }
       trace<R>(s, sigma, q, dq, ql, qr);
     }
+    if (P.use_grav) {  // half-step gravity on v: transverse in the x sweep, normal in the y sweep
+      constexpr int kv = DIR == 0 ? 2 : 1;
+      ql[kv] = ql[kv] + hdtg;
+      qr[kv] = qr[kv] + hdtg;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       sl[k * nC + e] = ql[k];
@@ -270,12 +283,19 @@ __global__ void __launch_bounds__(NT, HYDRO_SWEEP_MINB) sweep_kernel(KParams P, 
     if (l0 + l >= P.ng + nlines || a0 + u >= P.ng + n) continue;
     const size_t o = interior_offset(a0 + u, l0 + l);
     const int g = u * L::FA + l * L::FL;
-    R Un[4];
+    R Un[4], U0[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      Un[k] = __ldg(Uin + o + k * plane) + sigma * (sG[k * nF + g] - sG[k * nF + g + L::FA]);
-      Uout[o + k * plane] = Un[k];
+      U0[k] = __ldg(Uin + o + k * plane);
+      Un[k] = U0[k] + sigma * (sG[k * nF + g] - sG[k * nF + g + L::FA]);
     }
+    if (DIR == 1 && P.use_grav) {
+      // the time-centred gravity sources, once per step, from the state this sweep starts from
+      Un[2] = Un[2] + hdtg * (U0[0] + Un[0]);
+      Un[3] = Un[3] + hdtg * (U0[2] + Un[2]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Uout[o + k * plane] = Un[k];
     if constexpr (FUSED) {
       cfl_value(s, Un[0], Un[1], Un[2], Un[3], cmin, cnt.flags);  // the next step's constraint (Eq. 6)
     } else if (check_state) {

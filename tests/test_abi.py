@@ -86,7 +86,7 @@ def test_oracle_library_builds_and_loads():
     assert oracle.num_threads() >= 1
 
 
-@pytest.mark.parametrize("extra", [dict(grav=-1.0), dict(use_learned_guess=1, precision=1)])
+@pytest.mark.parametrize("extra", [dict(use_learned_guess=1, precision=1)])
 def test_split_variant_rejects_what_it_does_not_implement(lib, extra):
     from paper_1306_6883_gb300 import hydro as H
     p = H.default_params(16, 16, split=1)
