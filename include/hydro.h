@@ -49,6 +49,13 @@ typedef enum {
  * next to the wall, pressure integrated with dp/dy = rho g from that row's cell, energy rebuilt from it.
  * The fused step (hydro_step_fused, hydro_advance) and the split sweeps read every kind of side through
  * the same map instead of a ghost fill. */
+typedef enum {
+  HYDRO_BC_OUTFLOW = 0,
+  HYDRO_BC_PERIODIC = 1,
+  HYDRO_BC_REFLECT = 2,
+  HYDRO_BC_HYDROSTATIC = 3
+} hydro_bc;
+
 /* Riemann solvers (paper §3.2).  TWO_SHOCK: Newton iteration of the two-shock approximation (the default).
  * HLLC: Toro's three-wave HLLC flux, outer wave speeds min(u_L - c_L, u_R - c_R), max(u_L + c_L, u_R + c_R);
  * no iterations (the iteration counters then stay 0). */
@@ -59,13 +66,6 @@ typedef enum { HYDRO_RIEMANN_TWO_SHOCK = 0, HYDRO_RIEMANN_HLLC = 1 } hydro_riema
  * flattening toward the cell average) traced along the characteristics, the fastest wave's average as the
  * reference state. */
 typedef enum { HYDRO_RECON_PLM = 0, HYDRO_RECON_PPM = 1 } hydro_recon;
-
-typedef enum {
-  HYDRO_BC_OUTFLOW = 0,
-  HYDRO_BC_PERIODIC = 1,
-  HYDRO_BC_REFLECT = 2,
-  HYDRO_BC_HYDROSTATIC = 3
-} hydro_bc;
 
 typedef enum {
   HYDRO_FP64 = 0, /* state and arithmetic in double */
@@ -134,8 +134,9 @@ void hydro_destroy(hydro_ctx* ctx);
 void* hydro_state(const hydro_ctx* ctx);
 
 /* Fill the ghost cells of the current state (paper §2, CellCenterData2d ghost filling; Fig. 1):
- * outflow copies the nearest interior cell (zero gradient), periodic wraps; a ghost cell (i, j)
- * takes the value of interior cell (map_x(i), map_y(j)), which also defines the corners.  Async. */
+ * outflow copies the nearest interior cell (zero gradient), periodic wraps, reflect mirrors with the
+ * normal momentum negated, hydrostatic integrates the pressure (see hydro_bc); a ghost cell (i, j) takes
+ * its value from interior cell (map_x(i), map_y(j)), which also defines the corners.  Async. */
 hydro_status hydro_fill_ghost(hydro_ctx* ctx);
 
 /* CFL time step (Eq. 6 with signal speeds |u| + c and |v| + c):
@@ -145,9 +146,9 @@ hydro_status hydro_fill_ghost(hydro_ctx* ctx);
 hydro_status hydro_cfl_dt(hydro_ctx* ctx, double* dt_out);
 
 /* One unsplit CTU step of length dt > 0 on the (ghost-filled) current state (paper §3.2 algorithm,
- * update Eq. 5): slopes + flattening, characteristic tracing (Eq. 13), two-shock Riemann solves on the
- * traced states, transverse flux-difference correction, final Riemann solves + artificial viscosity,
- * conservative update.  Writes the other buffer and swaps.  Asynchronous: problems found on the device
+ * update Eq. 5): slopes + flattening, characteristic tracing (Eq. 13), Riemann solves on the traced
+ * states, transverse flux-difference correction, final Riemann solves + artificial viscosity,
+ * conservative update, with the Riemann solver and reconstruction the parameters select.  Writes the other buffer and swaps.  Asynchronous: problems found on the device
  * (non-finite or non-positive results, unconverged Riemann solves) are recorded in the context's status
  * word and reported by hydro_sync_status().  With split = 1 the step is the dimensionally split one (§3.1):
  * a one-dimensional sweep into the other buffer and the other sweep back into the current buffer (two
@@ -173,9 +174,9 @@ hydro_status hydro_advance(hydro_ctx* ctx, int nsteps, double tmax);
 
 /* One step of the driver loop as a single kernel launch: the step kernel reads ghost cells through the
  * boundary conditions' map of the interior (the values hydro_fill_ghost would write, for every kind of
- * side, so no fill pass),
- * and reduces the CFL time step of the state it writes (so no dt pass); its last block advances the
- * device time by this step's dt and keeps the next step's dt (clamped to reach tmax when tmax > 0).  The
+ * side, so no fill pass), and reduces the CFL time step of the state it writes (so no dt pass); its last
+ * block advances the device time by this step's dt and keeps the next step's dt (clamped to reach tmax
+ * when tmax > 0).  The
  * first call after any other state change (hydro_step, hydro_step_device_dt, hydro_upload) computes this
  * step's dt with one extra reduction.  With split = 1: the two sweeps of hydro_step, the second one
  * reducing the next dt.  FP32 contexts with a learned model or a harvest run the separate passes instead.
@@ -190,7 +191,8 @@ hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
  * hydro_download in turn.  Same results as those three calls. */
 hydro_status hydro_step_host(hydro_ctx* ctx, const void* host_in, void* host_out, double tmax);
 
-/* Simulated time and number of steps taken through hydro_step / hydro_advance.  Synchronises. */
+/* Simulated time and number of steps of the device-side loop (hydro_cfl_dt_async, hydro_step_fused,
+ * hydro_advance, hydro_step_host; hydro_step with a host dt does not count).  Synchronises. */
 hydro_status hydro_get_time(hydro_ctx* ctx, double* t, long long* nsteps);
 
 /* Conserved totals out[k] = sum over interior cells of U_k dx dy, accumulated in double in a fixed
