@@ -303,7 +303,7 @@ def harvest_and_train(train_steps=6000, batch=4096, lr=1e-3, seed=0):
 
     import hydro_problems as hp
     from paper_1306_6883_gb300 import hydro as H
-    from paper_1306_6883_gb300.solver import Harvest, Model, Solver, params_for
+    from paper_1306_6883_gb300.solver import Model, Solver, params_for
 
     cap = 12_000_000
     buf = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")

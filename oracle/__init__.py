@@ -7,7 +7,6 @@ Arrays are numpy float64 of shape (4, ny + 2 ng, nx + 2 ng), C-contiguous: U[k, 
 k in (rho, rho u, rho v, rho E), j the row (y) and i the column (x).
 """
 import ctypes
-import os
 
 import numpy as np
 
