@@ -84,6 +84,23 @@ def rt(nx=128, ny=384, rho1=1.0, rho2=2.0, grav=-1.0, p0=5.0, amp=0.01, sigma=0.
                    gamma=gamma, cfl=0.8, tmax=3.0, domain=domain, grav=grav)
 
 
+def bubble(nx=128, ny=256, grav=-1.0, rho0=1.0, H=1.0, amp=2.0, radius=0.1, yc=0.5, gamma=1.4, lx=1.0, ly=2.0):
+    """Buoyant bubble in a stratified atmosphere (the paper's Table 1 `bubble` problem; it gives no set-up,
+    so this one is the generator's choice): an isothermal atmosphere in hydrostatic equilibrium,
+    rho_atm = rho0 exp(-y / H), p = rho_atm |g| H (so dp/dy = rho g), with a hot, light bubble at
+    (lx / 2, yc): rho = rho_atm / (1 + amp exp(-r^2 / radius^2)) at the same pressure; at rest.  Reflecting
+    walls in x, hydrostatic boundaries in y, gravity along -y."""
+    domain = (0.0, lx, 0.0, ly)
+    X, Y = _centres(nx, ny, domain)
+    rho_atm = rho0 * np.exp(-Y / H)
+    p = rho_atm * abs(grav) * H
+    r2 = (X - 0.5 * lx) ** 2 + (Y - yc) ** 2
+    rho = rho_atm / (1.0 + amp * np.exp(-r2 / radius ** 2))
+    z = np.zeros_like(rho)
+    return Problem("bubble", nx, ny, _pack(rho, z, z, p, gamma), ("reflect", "reflect", "hydrostatic", "hydrostatic"),
+                   gamma=gamma, cfl=0.8, tmax=3.0, domain=domain, grav=grav)
+
+
 def kh(nx=1024, ny=1024, seed=0, gamma=1.4):
     """Kelvin-Helmholtz shear layer (Table 1 "kh"): rho = 2, u = +0.5 for |y - 0.5| < 0.25, else rho = 1,
     u = -0.5; p = 2.5; v = 0.01 sin(4 pi x) * w with w ~ U[-1, 1] per cell (seeded).  Periodic."""

@@ -4,8 +4,9 @@
                                             [--steps K | --tmax T] [--seed S] [--split]
                                             [--riemann two-shock|hllc] [--recon plm|ppm] [--dump FILE]
 
-PROBLEM is one of sod, sod_y, kh, sedov, quad, pulse, rt (seeded set-ups of hydro_problems; rt is the
-Rayleigh-Taylor column with gravity, nx x 3nx by default).  Runs the device-resident loop (fill ghost
+PROBLEM is one of sod, sod_y, kh, sedov, quad, pulse, rt, bubble (seeded set-ups of hydro_problems; rt is
+the Rayleigh-Taylor column with gravity, nx x 3nx by default; bubble a buoyant bubble in a stratified
+atmosphere, nx x 2nx by default).  Runs the device-resident loop (fill ghost
 cells, CFL dt, CTU step; --split: the dimensionally split step; --riemann and --recon choose the Riemann
 solver and the reconstruction) and prints one JSON line with the simulated
 time, step count, wall time, conserved totals and the Riemann-solver counters.  --dump writes the final
@@ -40,6 +41,8 @@ def make_problem(name, nx, ny, seed):
         return hp.pulse(nx, ny)
     if name == "rt":
         return hp.rt(nx, ny)
+    if name == "bubble":
+        return hp.bubble(nx, ny)
     raise SystemExit(f"unknown problem {name}")
 
 
@@ -65,7 +68,7 @@ def main(argv=None):
     from .solver import Solver, params_for
 
     build.build()
-    ny = a.ny or (3 * a.nx if a.problem == "rt" else a.nx)
+    ny = a.ny or (3 * a.nx if a.problem == "rt" else 2 * a.nx if a.problem == "bubble" else a.nx)
     pr = make_problem(a.problem, a.nx, ny, a.seed)
     prec = H.HYDRO_FP32 if a.precision == "fp32" else H.HYDRO_FP64
     s = Solver(params_for(pr, prec, split=int(a.split), riemann_solver=a.riemann, reconstruction=a.recon), pr.U)

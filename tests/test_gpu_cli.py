@@ -21,7 +21,8 @@ def _cuda():
 @pytest.mark.parametrize("args", [["sod", "--nx", "64", "--tmax", "0.05"],
                                   ["kh", "--nx", "96", "--precision", "fp32", "--steps", "20"],
                                   ["rt", "--nx", "32", "--steps", "12", "--riemann", "hllc", "--recon", "ppm"],
-                                  ["sedov", "--nx", "64", "--precision", "fp32", "--steps", "10", "--split"]])
+                                  ["sedov", "--nx", "64", "--precision", "fp32", "--steps", "10", "--split"],
+                                  ["bubble", "--nx", "32", "--steps", "15", "--split"]])
 def test_cli_runs_and_reports(args):
     r = subprocess.run([sys.executable, "-m", "paper_1306_6883_gb300", *args], cwd=ROOT, capture_output=True,
                        text=True, timeout=600)

@@ -65,6 +65,7 @@ PROBLEMS = {
     "reflect_lo_outflow_hi_20x20": lambda: _random_box(20, 20, ("reflect", "outflow", "reflect", "outflow"), 0.7, 4),
     "fall_periodic_48x40": lambda: _random_box(48, 40, ("periodic",) * 4, -1.0, 5),
     "rt_4x4": lambda: hp.rt(4, 4),
+    "bubble_32x64": lambda: hp.bubble(32, 64),
 }
 
 
@@ -118,7 +119,8 @@ def test_fp64_step_matches_the_oracle(name):
 
 
 @pytest.mark.parametrize("name,nsteps", [("rt_32x96", 30), ("walls_grav_45x33", 20),
-                                         ("outflow_x_hydro_y_40x24", 20), ("fall_periodic_48x40", 20)])
+                                         ("outflow_x_hydro_y_40x24", 20), ("fall_periodic_48x40", 20),
+                                         ("bubble_32x64", 40)])
 def test_fp64_driver_loop_is_bit_identical_to_the_oracle_loop(name, nsteps):
     # the fused launch reads reflecting / hydrostatic sides through the boundary map (bc_cell) and periodic
     # sides through the wrap; both against the oracle's fill / dt / step loop
@@ -135,7 +137,8 @@ def test_fp64_driver_loop_is_bit_identical_to_the_oracle_loop(name, nsteps):
     np.testing.assert_array_equal(_interior(got), _interior(U))
 
 
-@pytest.mark.parametrize("name", ["rt_32x96", "walls_grav_45x33", "outflow_x_hydro_y_40x24", "fall_periodic_48x40"])
+@pytest.mark.parametrize("name", ["rt_32x96", "walls_grav_45x33", "outflow_x_hydro_y_40x24", "fall_periodic_48x40",
+                                  "bubble_32x64"])
 def test_fp32_step_error_is_within_its_bound(name):
     # the same bound as the problems without gravity: float rounding of ~10^2 dependent operations per output.
     # Momenta are measured against rho c as well as their own size: the pressure term of the momentum flux
