@@ -48,8 +48,8 @@ ALU_PEAK_SOURCE = {"fp32": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit 
 # DRAM bytes (read + write) of one launch of the FP32 fused step kernel on the KH 1024^2 workload, from an
 # ncu capture of the kernel built from the sources whose SHA-256 is recorded; reported only while the
 # kernel's sources are unchanged (otherwise the counters describe another kernel and traffic is null)
-TRAFFIC_CAPTURE = {"bytes_per_launch": 17379584 + 1280, "issue_active": 0.7859, "warp_instructions": 79682836,
-                   "sources_sha256": "62b0233da23ae753f57b106e44c206c57012e0a2d6588ae036f080c8586e23ff"}
+TRAFFIC_CAPTURE = {"bytes_per_launch": 17378816 + 1024, "issue_active": 0.7882, "warp_instructions": 79743152,
+                   "sources_sha256": "472f1932619ece4588de8e4e77ed15e12edaa6738965092c67af0d80ae8ad680"}
 KERNEL_SOURCES = ["paper_1306_6883_gb300/csrc/" + f for f in
                   ("k_ctu.cu", "ctu_kernels.cuh", "ctu_tile.cuh", "hydro_device.cuh", "mlp.cuh", "hydro_kernels.h",
                    "tma.cuh")] + ["include/hydro.h"]
@@ -198,10 +198,12 @@ def time_device_path(pr, precision, steps, warmup, flush, **kw):
 
 
 def time_e2e(pr, precision, steps, warmup):
-    """Same metric through the public C-ABI call for host-resident state, hydro_step_host: every step
-    uploads the state from pinned host memory, reduces its dt, runs the fused step as concurrent bands of
-    tile rows and copies each band's rows back while later bands compute, returning when the new state is
-    in host memory; the two pinned host buffers alternate as input and output."""
+    """Same metric through the public C-ABI call for a run kept in host memory, hydro_step_host_chained:
+    every step uploads the whole state from pinned host memory in chunks of tile-row bands, runs the fused
+    step band by band as the rows arrive (its time step is the one the previous call reduced from the state
+    it wrote, which is this call's input) and copies each band's rows back while later bands compute,
+    returning when the new state is in host memory; the two pinned host buffers alternate as input and
+    output.  The first warm-up call reduces the time step from the uploaded state (no chain yet)."""
     import torch
 
     from paper_1306_6883_gb300 import hydro as H
@@ -213,13 +215,13 @@ def time_e2e(pr, precision, steps, warmup):
     host = [torch.from_numpy(np.ascontiguousarray(pr.U)).to(dt_).pin_memory() for _ in range(2)]
 
     def one(k):
-        s.step_host(host[k % 2], host[(k + 1) % 2])
+        s.step_host(host[k % 2], host[(k + 1) % 2], chained=True)
 
     for k in range(warmup):
         one(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(steps):
+    for k in range(warmup, warmup + steps):  # the run goes on: each input is the previous step's output
         one(k)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
@@ -549,7 +551,7 @@ def run_ours(args, world, rank, local):
                      "traffic": None, "traffic_note": None},
         "cpu_baseline": None,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": e2e["h2d"],
-                "d2h_bytes_per_step": e2e["d2h"]},
+                "d2h_bytes_per_step": e2e["d2h"], "call": "hydro_step_host_chained"},
         "gpu_launches": main["launches_per_step"] * args.steps,
         "clocks": clk.summary(),
         "variants": {other: {"value": var_value, "ms_per_step": 1e3 / var_value * zones,

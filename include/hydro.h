@@ -185,11 +185,27 @@ hydro_status hydro_step_fused(hydro_ctx* ctx, double tmax);
 
 /* One step with host-resident state: host_in (pinned, layout of hydro_upload) is uploaded, stepped as
  * hydro_step_fused(tmax) does, and the new state written to host_out (layout of hydro_download; must not
- * be host_in).  The fused step runs as five launches over bands of tile rows on the context's own streams,
- * and each band's rows are copied back while later bands compute.  Returns when host_out holds the new
- * state.  Contexts with a learned model, a harvest or split = 1 run upload, hydro_step_fused and
- * hydro_download in turn.  Same results as those three calls. */
+ * be host_in).  The rows go up into an unpitched device copy of the state, one chunk per band of tile
+ * rows; the fused step runs as one launch per band (five bands) on the context's own streams, and each
+ * band's rows are copied back while later bands compute.  The whole pipeline is captured once as a CUDA
+ * graph for each pair of host buffers (and tmax) and replayed.  Returns when host_out holds the new state; the
+ * context's current buffer holds it too.  The interior of host_out and of the current state equals what
+ * hydro_upload, hydro_step_fused and hydro_download give; ghost cells are not filled (host_out's read as
+ * 0 or as the values an earlier step left there).  Contexts with a learned model, a harvest or split = 1
+ * run those three calls in turn.  The first call allocates two device copies of the state (unpitched,
+ * 4 (nx + 2 ng)(ny + 2 ng) elements each), which the context keeps until hydro_destroy.
+ * Errors: HYDRO_EINVAL (NULL pointers, host_in == host_out), HYDRO_ECUDA. */
 hydro_status hydro_step_host(hydro_ctx* ctx, const void* host_in, void* host_out, double tmax);
+
+/* hydro_step_host for a run kept in host memory, step after step: when host_in is the host_out of the
+ * previous hydro_step_host / hydro_step_host_chained call on this context, unchanged since, with the same
+ * tmax and no other call that steps or replaces the state in between, this step's CFL time step is the
+ * one the previous step reduced from the state it wrote (as hydro_step_fused keeps it), so no reduction
+ * waits for the whole upload: each band of tile rows starts as soon as its rows and their 4-row halo
+ * have arrived (eight bands), and the upload overlaps the step.  Otherwise the same as hydro_step_host.  The caller
+ * must not modify host_out between the calls (the library checks the pointer, not the contents).  Same
+ * results as hydro_step_host. */
+hydro_status hydro_step_host_chained(hydro_ctx* ctx, const void* host_in, void* host_out, double tmax);
 
 /* Simulated time and number of steps of the device-side loop (hydro_cfl_dt_async, hydro_step_fused,
  * hydro_advance, hydro_step_host; hydro_step with a host dt does not count).  Synchronises. */

@@ -38,14 +38,36 @@ struct hydro_ctx {
   CUtensorMap tmap[2];
   int tma_ok;
   unsigned long long split_steps;  // split variant: steps taken (x sweep first on even counts)
-  // hydro_step_host: streams for the bands of the fused step and for their downloads, and their events
-  // (created on first use).  KH 1024^2 FP32 step from and to pinned host memory: 291 us as three calls,
-  // 245 us with four equal bands, 255 us with eight, 241 us with five of 1/8, 1/8, 1/4, 1/4, 1/4.
-  static constexpr int HOST_BANDS = 5;
+  // host steps (created on first use): streams for the bands of the fused step, for the copies up and
+  // for the copies back, and their events; two unpitched copies of the state (input and output of the
+  // banded step).  Without row padding a band's rows in the four planes are four contiguous blocks, which
+  // one 2-D copy (a row per plane) moves at the link's rate; the copy engine moves the padded layout's
+  // 4 KB rows at under half of it.
+  static constexpr int HOST_BANDS = 8;
   int host_pipe;
   cudaStream_t band_stream[HOST_BANDS];
-  cudaStream_t d2h_stream;
-  cudaEvent_t ev_ready, ev_band[HOST_BANDS];
+  cudaStream_t d2h_stream, h2d_stream;
+  cudaEvent_t ev_ready, ev_start, ev_done, ev_band[HOST_BANDS], ev_up[HOST_BANDS];
+  void* stage[2];
+  CUtensorMap stage_map;  // of stage[0], when stage_tma
+  int stage_tma;
+  // host steps replay as CUDA graphs: the pipeline of one host step (copies up, bands, copies back, the
+  // copy into the context's buffer) is captured once for each set of values it bakes in and then runs as
+  // one launch instead of ~40 API calls (KH 64^2 FP32, chained: 46 us per step against 53 us; at 1024^2
+  // the link bounds the step either way); a few graphs are kept, replaced in turn
+  static constexpr int HOST_GRAPHS = 4;
+  struct HostGraph {
+    const void* in;
+    void* out;
+    int cur, parity, chained;
+    double tmax;
+    cudaGraphExec_t exec;
+  } hgraph[HOST_GRAPHS];
+  int hgraph_next;
+  // chained host steps: the buffer the last host step wrote, and the step count and tmax it left behind
+  const void* chain_out;
+  unsigned int chain_step;
+  double chain_tmax;
   char err[512];
 };
 
@@ -305,9 +327,17 @@ void hydro_destroy(hydro_ctx* c) {
     for (int b = 0; b < hydro_ctx::HOST_BANDS; ++b) {
       cudaStreamDestroy(c->band_stream[b]);
       cudaEventDestroy(c->ev_band[b]);
+      cudaEventDestroy(c->ev_up[b]);
     }
+    for (int k = 0; k < hydro_ctx::HOST_GRAPHS; ++k)
+      if (c->hgraph[k].exec) cudaGraphExecDestroy(c->hgraph[k].exec);
     cudaStreamDestroy(c->d2h_stream);
+    cudaStreamDestroy(c->h2d_stream);
     cudaEventDestroy(c->ev_ready);
+    cudaEventDestroy(c->ev_start);
+    cudaEventDestroy(c->ev_done);
+    cudaFree(c->stage[0]);
+    cudaFree(c->stage[1]);
   }
   if (c->scr) cudaFree(c->scr);
   if (c->partials) cudaFree(c->partials);
@@ -581,100 +611,239 @@ hydro_status hydro_download(hydro_ctx* c, void* host) {
   return e == cudaSuccess ? HYDRO_OK : cuda_fail(c, e, "download");
 }
 
+// The staging copies have no row padding.
+static hydro::KParams stage_kparams(const hydro_ctx* c) {
+  hydro::KParams ks = c->kp;
+  ks.pitch = ks.NX;
+  return ks;
+}
+
 // Band b's stream gets a higher priority than band b + 1's, so that the block scheduler finishes the bands
 // in order and the first rows can go back to the host while the later ones compute.
 static cudaError_t make_host_pipe(hydro_ctx* c) {
   if (c->host_pipe) return cudaSuccess;
+  constexpr int NB = hydro_ctx::HOST_BANDS;
   int least = 0, greatest = 0;
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  cudaStream_t streams[hydro_ctx::HOST_BANDS + 1] = {};
-  cudaEvent_t events[hydro_ctx::HOST_BANDS + 1] = {};
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&streams[hydro_ctx::HOST_BANDS], cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&events[hydro_ctx::HOST_BANDS], cudaEventDisableTiming);
-  for (int b = 0; b < hydro_ctx::HOST_BANDS && e == cudaSuccess; ++b) {
-    // priorities run from `greatest` (numerically lowest) to `least`
-    const int prio = greatest + b < least ? greatest + b : least;
+  // streams: the bands (priorities from `greatest`, numerically lowest, down to `least`), the copies back
+  // (least), the copies up (greatest); events: ready, start, done, one per band, one per band's rows up
+  cudaStream_t streams[NB + 2] = {};
+  cudaEvent_t events[2 * NB + 3] = {};
+  void* stage[2] = {};
+  for (int b = 0; b < NB + 2 && e == cudaSuccess; ++b) {
+    const int prio = b == NB + 1 ? greatest : b == NB ? least : (greatest + b < least ? greatest + b : least);
     e = cudaStreamCreateWithPriority(&streams[b], cudaStreamNonBlocking, prio);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&events[b], cudaEventDisableTiming);
   }
+  for (int k = 0; k < 2 * NB + 3 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&events[k], cudaEventDisableTiming);
+  const size_t bytes = 4 * (size_t)c->kp.NX * (size_t)c->kp.NY * elem_size(c->p.precision);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&stage[k], bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(stage[k], 0, bytes, c->stream);  // ghost cells read as 0
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {  // release whatever was created
-    for (int b = 0; b <= hydro_ctx::HOST_BANDS; ++b) {
+    for (int b = 0; b < NB + 2; ++b)
       if (streams[b]) cudaStreamDestroy(streams[b]);
-      if (events[b]) cudaEventDestroy(events[b]);
-    }
+    for (int k = 0; k < 2 * NB + 3; ++k)
+      if (events[k]) cudaEventDestroy(events[k]);
+    for (int k = 0; k < 2; ++k)
+      if (stage[k]) cudaFree(stage[k]);
     return e;
   }
-  for (int b = 0; b < hydro_ctx::HOST_BANDS; ++b) {
+  for (int b = 0; b < NB; ++b) {
     c->band_stream[b] = streams[b];
-    c->ev_band[b] = events[b];
+    c->ev_band[b] = events[3 + b];
+    c->ev_up[b] = events[3 + NB + b];
   }
-  c->d2h_stream = streams[hydro_ctx::HOST_BANDS];
-  c->ev_ready = events[hydro_ctx::HOST_BANDS];
+  c->ev_done = events[2];
+  c->d2h_stream = streams[NB];
+  c->h2d_stream = streams[NB + 1];
+  c->ev_ready = events[0];
+  c->ev_start = events[1];
+  c->stage[0] = stage[0];
+  c->stage[1] = stage[1];
+  c->stage_tma = c->tma_ok && hydro::make_state_tensor_map(&c->stage_map, stage_kparams(c), c->p.precision, stage[0],
+                                                           hydro::f32_tile_x(), hydro::f32_tile_y());
   c->host_pipe = 1;
   return cudaSuccess;
 }
 
-hydro_status hydro_step_host(hydro_ctx* c, const void* host_in, void* host_out, double tmax) {
-  if (!c || !host_in || !host_out || host_in == host_out) return HYDRO_EINVAL;
-  hydro_status st = hydro_upload(c, host_in);
-  if (st != HYDRO_OK) return st;
-  if (c->p.use_learned_guess == 1 || c->harvest || c->p.split) {  // no banded fused launch for these
-    st = hydro_step_fused(c, tmax);
-    return st == HYDRO_OK ? hydro_download(c, host_out) : st;
-  }
-  cudaError_t e = make_host_pipe(c);
-  if (e != cudaSuccess) return cuda_fail(c, e, "step_host streams");
+// Enqueue one host step through the staging copies, all of it forked from and joined back into the upload
+// stream (so that it can be captured as one graph from there).  The input's rows go up in one chunk per
+// band of tile rows, each chunk one 2-D copy of the band's rows (and their 4-row halo) in the four planes;
+// the bands of the fused step run on their streams, and each band's rows go back as soon as it has
+// finished; the new state is then copied into the context's other buffer.  When `chained`, this step's
+// factors are those the previous host step reduced from the state it wrote, which is host_in, so band b
+// starts as soon as its rows have arrived; otherwise the CFL step of the uploaded state is reduced first
+// and every band waits for it.
+static cudaError_t enqueue_host_step(hydro_ctx* c, const void* host_in, void* host_out, double tmax, int chained) {
+  constexpr int NB = hydro_ctx::HOST_BANDS;
   const int prec = c->p.precision;
+  const hydro::KParams ks = stage_kparams(c);
+  const size_t es = elem_size(prec), w = (size_t)ks.NX * es, plane = w * (size_t)ks.NY;
+  const size_t pitchb = (size_t)c->kp.pitch * es;
+  const unsigned char* hin = (const unsigned char*)host_in;
+  unsigned char* hout = (unsigned char*)host_out;
+  unsigned char* s_in = (unsigned char*)c->stage[0];
+  unsigned char* s_out = (unsigned char*)c->stage[1];
   hydro::StepScalars* sc_cur = &c->scr->scf[c->fused_parity];
   hydro::StepScalars* sc_next = &c->scr->scf[1 - c->fused_parity];
-  // this step's factors from the uploaded state; then the bands of the fused step run concurrently and each
-  // band's rows go back to the host as soon as the band has finished
-  e = hydro::cfl_dt(prec, c->kp, c->state[c->cur], c->scr, tmax, 0, sc_cur, c->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev_ready, c->stream);
+  cudaStream_t up = c->h2d_stream;
+  // bands of tile rows, in sixteenths: 1/8, 1/8, 1/4, 1/4, 1/4 when every band waits for the dt (small
+  // first bands start the copies back early); when chained, eight bands of 1/16, 1/8, 1/8, 3/16, 3/16, 1/8,
+  // 1/8, 1/16 (a small first band starts the copies back early, a small last one ends the step early after
+  // the whole upload; KH 1024^2 FP32: 181 us per step, 186 us with 1/8, 1/4, 1/4, 1/4, 1/8, 185-200 us with
+  // five other splits); grids of fewer than 16 tile rows split evenly into at most five bands
+  static const int sixteenths_dt[6] = {0, 2, 4, 8, 12, 16};
+  static const int sixteenths_chain[NB + 1] = {0, 1, 3, 5, 8, 11, 13, 15, 16};
   const int ty = hydro::fused_tile_rows(prec, c->kp);
   const int tile_h = hydro::fused_tile_height(prec);  // cells per tile row
-  const int nb = ty < hydro_ctx::HOST_BANDS ? ty : hydro_ctx::HOST_BANDS;
-  const size_t es = elem_size(prec);
-  const size_t w = (size_t)c->kp.NX * es, pitchb = (size_t)c->kp.pitch * es;
-  const unsigned char* out = (const unsigned char*)c->state[1 - c->cur];
-  unsigned char* host = (unsigned char*)host_out;
+  const int nb = ty < 16 ? (ty < 5 ? ty : 5) : chained ? NB : 5;
+  const int* sixteenths = chained ? sixteenths_chain : sixteenths_dt;
+  int yb[NB + 1];
+  for (int b = 0; b <= nb; ++b) yb[b] = ty >= 16 ? ty * sixteenths[b] / 16 : b * ty / nb;
+  auto rows_up = [&](int r0, int r1) -> cudaError_t {  // padded rows [r0, r1) of the four planes
+    return r1 > r0 ? cudaMemcpy2DAsync(s_in + (size_t)r0 * w, plane, hin + (size_t)r0 * w, plane,
+                                       (size_t)(r1 - r0) * w, 4, cudaMemcpyHostToDevice, up)
+                   : cudaSuccess;
+  };
+  // the first chunk also carries the rows the first band reads as periodic images of the top edge
+  // (interior rows ny - 4 .. ny - 1 and the ghost rows above them); band b needs padded rows up to
+  // ng + (its last tile row's end) + 4
+  cudaError_t e = cudaSuccess;
+  int top = ks.NY - ks.ng - 4;
+  int done = 0;  // padded rows [0, done) and [top, NY) are on their way up
   for (int b = 0; b < nb && e == cudaSuccess; ++b) {
-    // bands of 1/8, 1/8, 1/4, 1/4 and 1/4 of the tile rows (small first bands start the copies back early);
-    // grids of fewer than 8 tile rows split evenly
-    static const int eighths[hydro_ctx::HOST_BANDS + 1] = {0, 1, 2, 4, 6, 8};
-    const int y0 = ty >= 8 ? ty * eighths[b] / 8 : b * ty / nb;
-    const int y1 = ty >= 8 ? ty * eighths[b + 1] / 8 : (b + 1) * ty / nb;
+    int hi = b == nb - 1 ? ks.NY : ks.ng + yb[b + 1] * tile_h + 4;
+    if (hi > ks.NY) hi = ks.NY;
+    if (b == 0) {
+      if (top <= hi) top = ks.NY;  // the first chunk reaches the top already
+      e = rows_up(top, ks.NY);
+    }
+    if (hi > top) hi = top;
+    if (e == cudaSuccess && hi > done) {
+      e = rows_up(done, hi);
+      done = hi;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_up[b], up);
+  }
+  if (!chained) {  // this step's factors from the uploaded state, time unchanged
+    if (e == cudaSuccess) e = hydro::cfl_dt(prec, ks, s_in, c->scr, tmax, 0, sc_cur, up);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_ready, up);
+  }
+  for (int b = 0; b < nb && e == cudaSuccess; ++b) {
     cudaStream_t bs = c->band_stream[b];
-    e = cudaStreamWaitEvent(bs, c->ev_ready, 0);
+    e = cudaStreamWaitEvent(bs, chained ? c->ev_up[b] : c->ev_ready, 0);
     if (e == cudaSuccess)
-      e = hydro::ctu_step_fused(prec, c->kp, c->state[c->cur], c->state[1 - c->cur], sc_cur, sc_next, c->scr, tmax,
-                                c->tma_ok ? &c->tmap[c->cur] : nullptr, bs, make_int2(y0, y1 - y0));
+      e = hydro::ctu_step_fused(prec, ks, s_in, s_out, sc_cur, sc_next, c->scr, tmax,
+                                c->stage_tma ? &c->stage_map : nullptr, bs, make_int2(yb[b], yb[b + 1] - yb[b]));
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_band[b], bs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->d2h_stream, c->ev_band[b], 0);
-    // padded rows of the band in all four planes, one 3-D copy (the first and last bands also carry the
-    // ghost rows below and above)
-    const int r0 = b == 0 ? 0 : c->kp.ng + y0 * tile_h;
-    const int r1 = b == nb - 1 ? c->kp.NY : c->kp.ng + y1 * tile_h;
-    if (e == cudaSuccess) {
-      cudaMemcpy3DParms cp = {};
-      cp.srcPtr = make_cudaPitchedPtr((void*)out, pitchb, c->kp.NX, c->kp.NY);
-      cp.dstPtr = make_cudaPitchedPtr(host, w, c->kp.NX, c->kp.NY);
-      cp.srcPos = make_cudaPos(0, r0, 0);
-      cp.dstPos = make_cudaPos(0, r0, 0);
-      cp.extent = make_cudaExtent(w, (size_t)(r1 - r0), 4);
-      cp.kind = cudaMemcpyDeviceToHost;
-      e = cudaMemcpy3DAsync(&cp, c->d2h_stream);
-    }
+    // the band's padded rows in the four planes (the first and last bands also carry the ghost rows below
+    // and above)
+    const int r0 = b == 0 ? 0 : ks.ng + yb[b] * tile_h;
+    const int r1 = b == nb - 1 ? ks.NY : ks.ng + yb[b + 1] * tile_h;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(hout + (size_t)r0 * w, plane, s_out + (size_t)r0 * w, plane, (size_t)(r1 - r0) * w, 4,
+                            cudaMemcpyDeviceToHost, c->d2h_stream);
   }
-  // the context's stream continues after every band
-  for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(c->stream, c->ev_band[b], 0);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->d2h_stream);
+  // after every band, the new state into the context's other buffer by the row-copy kernel (here from
+  // device memory; the copy engine takes several times longer over the padded layout's short rows); the
+  // copies back join last
+  for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(up, c->ev_band[b], 0);
+  if (e == cudaSuccess) e = hydro::upload_rows(s_out, c->state[1 - c->cur], w, pitchb, 4 * ks.NY, up);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_done, c->d2h_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(up, c->ev_done, 0);
+  return e;
+}
+
+static void drop_host_graphs(hydro_ctx* c) {
+  for (int k = 0; k < hydro_ctx::HOST_GRAPHS; ++k)
+    if (c->hgraph[k].exec) {
+      cudaGraphExecDestroy(c->hgraph[k].exec);
+      c->hgraph[k].exec = nullptr;
+    }
+}
+
+// The graph of this host step: found among the kept ones, else captured from the upload stream and
+// instantiated.  nullptr when capture or instantiation fails (the step then runs uncaptured).
+static cudaGraphExec_t host_step_graph(hydro_ctx* c, const void* host_in, void* host_out, double tmax, int chained) {
+  for (int k = 0; k < hydro_ctx::HOST_GRAPHS; ++k) {
+    const hydro_ctx::HostGraph& g = c->hgraph[k];
+    if (g.exec && g.in == host_in && g.out == host_out && g.cur == c->cur && g.parity == c->fused_parity &&
+        g.chained == chained && g.tmax == tmax)
+      return g.exec;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(c->h2d_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const cudaError_t e = enqueue_host_step(c, host_in, host_out, tmax, chained);
+  const cudaError_t ec = cudaStreamEndCapture(c->h2d_stream, &graph);
+  if (e == cudaSuccess && ec == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+    exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();  // a failed capture leaves no sticky error; the step then runs uncaptured
+  if (!exec) return nullptr;
+  hydro_ctx::HostGraph& slot = c->hgraph[c->hgraph_next];
+  c->hgraph_next = (c->hgraph_next + 1) % hydro_ctx::HOST_GRAPHS;
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot = hydro_ctx::HostGraph{host_in, host_out, c->cur, c->fused_parity, chained, tmax, exec};
+  return exec;
+}
+
+// One host step: the graph of its pipeline launched on the context's stream (so it follows the work
+// enqueued there before), or the same work enqueued directly, then a wait for the new state in host_out.
+static hydro_status step_host(hydro_ctx* c, const void* host_in, void* host_out, double tmax, int chained) {
+  cudaError_t e = make_host_pipe(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step_host streams");
+  c->chain_out = nullptr;
+  cudaGraphExec_t exec = host_step_graph(c, host_in, host_out, tmax, chained);
+  if (exec) {
+    e = cudaGraphLaunch(exec, c->stream);
+  } else {
+    e = cudaEventRecord(c->ev_start, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->h2d_stream, c->ev_start, 0);
+    if (e == cudaSuccess) e = enqueue_host_step(c, host_in, host_out, tmax, chained);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_start, c->h2d_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_start, 0);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step_host");
   ++c->step_calls;
   c->cur = 1 - c->cur;
   c->fused_parity = 1 - c->fused_parity;
   c->fused_valid = 1;
+  c->chain_out = host_out;
+  c->chain_step = c->step_calls;
+  c->chain_tmax = tmax;
   return HYDRO_OK;
+}
+
+static hydro_status host_step_entry(hydro_ctx* c, const void* host_in, void* host_out, double tmax, int chain) {
+  if (!c || !host_in || !host_out || host_in == host_out) return HYDRO_EINVAL;
+  if (c->p.use_learned_guess == 1 || c->harvest || c->p.split) {  // no banded fused launch for these
+    c->chain_out = nullptr;
+    hydro_status st = hydro_upload(c, host_in);
+    if (st == HYDRO_OK) st = hydro_step_fused(c, tmax);
+    return st == HYDRO_OK ? hydro_download(c, host_out) : st;
+  }
+  // a chain holds while host_in is the buffer the last host step wrote and nothing has stepped or replaced
+  // the state since (each of those clears fused_valid or counts a step)
+  const int chained = chain && c->fused_valid && c->chain_out == host_in && c->chain_step == c->step_calls &&
+                      c->chain_tmax == tmax;
+  return step_host(c, host_in, host_out, tmax, chained);
+}
+
+hydro_status hydro_step_host(hydro_ctx* c, const void* host_in, void* host_out, double tmax) {
+  return host_step_entry(c, host_in, host_out, tmax, 0);
+}
+
+hydro_status hydro_step_host_chained(hydro_ctx* c, const void* host_in, void* host_out, double tmax) {
+  return host_step_entry(c, host_in, host_out, tmax, 1);
 }
 
 const char* hydro_last_error(const hydro_ctx* c) { return c ? c->err : "no context"; }
@@ -690,6 +859,7 @@ hydro_status hydro_test_drop_tile_copies(hydro_ctx* c, int drop, unsigned int po
   if (!c || (drop != 0 && drop != 1)) return HYDRO_EINVAL;
   c->kp.tma_test_drop = drop;
   c->kp.tma_polls = drop ? (polls ? polls : 1000u) : 0u;
+  drop_host_graphs(c);  // they hold the old parameters
   c->fused_valid = 0;
   return HYDRO_OK;
 }

@@ -803,22 +803,28 @@ __device__ __forceinline__ void cfl_value(const SP<R>& s, R U0, R U1, R U2, R U3
     return;
   }
   if constexpr (is_f32<R>()) {
+    // every product and sum rounds on its own (no multiply-add contraction, which the compiler would
+    // choose differently in each kernel that inlines this), so the step kernels that fold in the CFL value
+    // of their new state and the standalone reduction give the same time step
     const float rho = U0 < s.small_dens ? s.small_dens : U0;
     const float ir = rcpa(rho);
-    const float u = U1 * ir, v = U2 * ir;
-    const float ke = 0.5f * rho * (u * u + v * v);
-    if (!(U0 > 0.0f) || !(U3 - ke > 0.0f)) flags |= STATUS_NEGATIVE;
+    const float u = __fmul_rn(U1, ir), v = __fmul_rn(U2, ir);
+    const float ke = __fmul_rn(__fmul_rn(0.5f, rho), __fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v)));
+    const float e = __fsub_rn(U3, ke);
+    if (!(U0 > 0.0f) || !(e > 0.0f)) flags |= STATUS_NEGATIVE;
     float p;
-    if (ke > 0.999f * U3) {  // as cons_to_prim: recover e = E - rho |u|^2 / 2 in double
-      const double rd = (double)rho, ud = (double)U1 / rd, vd = (double)U2 / rd;
-      p = (float)(((double)s.gm1) * ((double)U3 - 0.5 * rd * (ud * ud + vd * vd)));
+    if (ke > __fmul_rn(0.999f, U3)) {  // as cons_to_prim: recover e = E - rho |u|^2 / 2 in double
+      const double rd = (double)rho, ud = __ddiv_rn((double)U1, rd), vd = __ddiv_rn((double)U2, rd);
+      p = (float)__dmul_rn((double)s.gm1,
+                           __dsub_rn((double)U3, __dmul_rn(__dmul_rn(0.5, rd), __dadd_rn(__dmul_rn(ud, ud),
+                                                                                      __dmul_rn(vd, vd)))));
     } else {
-      p = s.gm1 * (U3 - ke);
+      p = __fmul_rn(s.gm1, e);
     }
     p = p < s.small_pres ? s.small_pres : p;
-    const float c2 = s.gamma * p * ir;
-    const float cs = c2 * rsqa(c2);
-    const float rate = fmaxf((fabsf(u) + cs) * s.idx, (fabsf(v) + cs) * s.idy);
+    const float c2 = __fmul_rn(__fmul_rn(s.gamma, p), ir);
+    const float cs = __fmul_rn(c2, rsqa(c2));
+    const float rate = fmaxf(__fmul_rn(__fadd_rn(fabsf(u), cs), s.idx), __fmul_rn(__fadd_rn(fabsf(v), cs), s.idy));
     const float t = rcpa(rate);
     rbest = t < rbest ? t : rbest;
   } else {

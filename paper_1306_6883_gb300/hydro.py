@@ -68,6 +68,7 @@ SIGNATURES = {
     "hydro_upload": (ctypes.c_int, [_VP, _VP]),
     "hydro_download": (ctypes.c_int, [_VP, _VP]),
     "hydro_step_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double]),
+    "hydro_step_host_chained": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double]),
     "hydro_mlp_create": (ctypes.c_int, [ctypes.c_ulonglong, _VP, ctypes.POINTER(_VP)]),
     "hydro_mlp_destroy": (None, [_VP]),
     "hydro_mlp_set_weights": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -233,6 +234,11 @@ def hydro_download(ctx, host_ptr):
 
 def hydro_step_host(ctx, host_in_ptr, host_out_ptr, tmax=0.0):
     _check(load().hydro_step_host(ctx, _VP(host_in_ptr), _VP(host_out_ptr), tmax), ctx, "hydro_step_host")
+
+
+def hydro_step_host_chained(ctx, host_in_ptr, host_out_ptr, tmax=0.0):
+    _check(load().hydro_step_host_chained(ctx, _VP(host_in_ptr), _VP(host_out_ptr), tmax), ctx,
+           "hydro_step_host_chained")
 
 
 def hydro_build_info():

@@ -69,9 +69,12 @@ class Solver:
     def download(self, host_tensor):
         H.hydro_download(self.ctx, host_tensor.data_ptr())
 
-    def step_host(self, host_in, host_out, tmax=0.0):
-        """One step from a pinned host tensor to another (upload, fused step, download, overlapped)."""
-        H.hydro_step_host(self.ctx, host_in.data_ptr(), host_out.data_ptr(), tmax)
+    def step_host(self, host_in, host_out, tmax=0.0, chained=False):
+        """One step from a pinned host tensor to another (upload, fused step, download, overlapped).  With
+        chained=True, host_in continuing the previous call's host_out unchanged, the step reuses the time
+        step that call reduced, and the upload overlaps the step."""
+        fn = H.hydro_step_host_chained if chained else H.hydro_step_host
+        fn(self.ctx, host_in.data_ptr(), host_out.data_ptr(), tmax)
 
     def time(self):
         return H.hydro_get_time(self.ctx)
