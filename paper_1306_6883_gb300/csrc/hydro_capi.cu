@@ -62,6 +62,7 @@ struct hydro_ctx {
     int cur, parity, chained;
     double tmax;
     cudaGraphExec_t exec;
+    int used;  // slot holds this key; exec == nullptr: its capture failed (the step then runs uncaptured)
   } hgraph[HOST_GRAPHS];
   int hgraph_next;
   // chained host steps: the buffer the last host step wrote, and the step count and tmax it left behind
@@ -760,18 +761,19 @@ static cudaError_t enqueue_host_step(hydro_ctx* c, const void* host_in, void* ho
 
 static void drop_host_graphs(hydro_ctx* c) {
   for (int k = 0; k < hydro_ctx::HOST_GRAPHS; ++k)
-    if (c->hgraph[k].exec) {
-      cudaGraphExecDestroy(c->hgraph[k].exec);
-      c->hgraph[k].exec = nullptr;
+    if (c->hgraph[k].used) {
+      if (c->hgraph[k].exec) cudaGraphExecDestroy(c->hgraph[k].exec);
+      c->hgraph[k] = hydro_ctx::HostGraph{};
     }
 }
 
 // The graph of this host step: found among the kept ones, else captured from the upload stream and
-// instantiated.  nullptr when capture or instantiation fails (the step then runs uncaptured).
+// instantiated.  nullptr when capture or instantiation fails (pageable host memory, for one, cannot be
+// captured; the step then runs uncaptured, and the failure is kept so that the next call does not retry).
 static cudaGraphExec_t host_step_graph(hydro_ctx* c, const void* host_in, void* host_out, double tmax, int chained) {
   for (int k = 0; k < hydro_ctx::HOST_GRAPHS; ++k) {
     const hydro_ctx::HostGraph& g = c->hgraph[k];
-    if (g.exec && g.in == host_in && g.out == host_out && g.cur == c->cur && g.parity == c->fused_parity &&
+    if (g.used && g.in == host_in && g.out == host_out && g.cur == c->cur && g.parity == c->fused_parity &&
         g.chained == chained && g.tmax == tmax)
       return g.exec;
   }
@@ -787,11 +789,10 @@ static cudaGraphExec_t host_step_graph(hydro_ctx* c, const void* host_in, void* 
     exec = nullptr;
   if (graph) cudaGraphDestroy(graph);
   cudaGetLastError();  // a failed capture leaves no sticky error; the step then runs uncaptured
-  if (!exec) return nullptr;
   hydro_ctx::HostGraph& slot = c->hgraph[c->hgraph_next];
   c->hgraph_next = (c->hgraph_next + 1) % hydro_ctx::HOST_GRAPHS;
   if (slot.exec) cudaGraphExecDestroy(slot.exec);
-  slot = hydro_ctx::HostGraph{host_in, host_out, c->cur, c->fused_parity, chained, tmax, exec};
+  slot = hydro_ctx::HostGraph{host_in, host_out, c->cur, c->fused_parity, chained, tmax, exec, 1};
   return exec;
 }
 

@@ -116,3 +116,25 @@ def test_the_chain_breaks_when_the_state_changes_under_it(precision):
     assert st == 0
     c.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pageable_host_buffers_give_the_same_steps(precision):
+    # host memory that is not pinned takes the copies as they come (no captured graph); same results
+    import torch
+    from paper_1306_6883_gb300.solver import Solver, params_for
+    pr = hp.kh(128, 96, seed=8)
+    a = Solver(params_for(pr, precision), pr.U)
+    b = Solver(params_for(pr, precision), pr.U)
+    hp_ = _pinned_pair(pr, precision)
+    hq = [x.clone() for x in hp_]
+    assert not hq[0].is_pinned()
+    for k in range(4):
+        a.step_host(hp_[k % 2], hp_[(k + 1) % 2], chained=True)
+        b.step_host(hq[k % 2], hq[(k + 1) % 2], chained=True)
+        torch.testing.assert_close(_interior(hq[(k + 1) % 2]), _interior(hp_[(k + 1) % 2]), rtol=0, atol=0)
+    assert a.time() == b.time()
+    for s in (a, b):
+        st, _ = s.status()
+        assert st == 0
+        s.close()
