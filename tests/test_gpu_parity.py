@@ -198,18 +198,12 @@ def test_device_driver_loop_equals_the_host_loop():
                                       ((5, 70), ("periodic", "periodic", "outflow", "outflow"))])
 def test_fused_step_equals_the_three_passes(precision, shape, bc):
     # one launch per step (ghost cells through the boundary map, dt folded into the step) must give the
-    # same state and time as ghost fill + dt reduction + step.  FP64: bit for bit.  FP32: the two kernels
-    # are compiled separately and the compiler may fuse a different multiply-add pair of the same source
-    # expression in each (one rounding of 2^-24 relative at a face), so after 7 steps the states agree to a
-    # few hundred FP32 rounding units of each field's magnitude and the times to a few rounding units
+    # same state and time as ghost fill + dt reduction + step, bit for bit in both precisions (in FP32 the
+    # CFL value of a cell rounds every product and sum on its own, so the step's dt equals the reduction's)
     H, Solver, params_for = _mods()
 
     def same(A, B):
-        if precision == 0:
-            np.testing.assert_array_equal(A, B)
-        else:
-            scale = np.abs(A).max(axis=(1, 2), keepdims=True)
-            assert np.all(np.abs(A - B) <= 2.0 ** -24 * 256 * scale), np.abs(A - B).max()
+        np.testing.assert_array_equal(A, B)
 
     nx, ny = shape
     pr = hp.quad(nx, ny, seed=nx + ny)
@@ -224,7 +218,7 @@ def test_fused_step_equals_the_three_passes(precision, shape, bc):
     ta, na = a.time()
     tb, nb = b.time()
     assert na == nb
-    assert ta == tb if precision == 0 else ta == pytest.approx(tb, rel=2.0 ** -24 * 16)
+    assert ta == tb
     same(_interior(a.state_numpy()), _interior(b.state_numpy()))
     # an upload invalidates the kept dt: the next fused step recomputes it from the new state
     U2 = hp.quad(nx, ny, seed=99).U
