@@ -50,6 +50,7 @@ PROBLEMS = {
     "quad_1x1": lambda: hp.quad(1, 1, seed=4),
     "quad_17x33": lambda: hp.quad(17, 33, seed=6),
     "rt_32x96": lambda: hp.rt(32, 96),
+    "bubble_32x64": lambda: hp.bubble(32, 64),
 }
 
 

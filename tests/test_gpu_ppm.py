@@ -50,6 +50,7 @@ PROBLEMS = {
     "quad_1x1": lambda: hp.quad(1, 1, seed=4),
     "quad_17x33": lambda: hp.quad(17, 33, seed=6),
     "rt_32x96": lambda: hp.rt(32, 96),
+    "bubble_32x64": lambda: hp.bubble(32, 64),
 }
 
 
@@ -79,7 +80,8 @@ def test_fp64_ppm_step_matches_the_oracle(name, solver):
                                                       ("quad_70x50", 20, False, "hllc"),
                                                       ("rt_32x96", 20, False, "two-shock"),
                                                       ("kh_100x70", 20, True, "two-shock"),
-                                                      ("sedov_100", 15, True, "hllc")])
+                                                      ("sedov_100", 15, True, "hllc"),
+                                                      ("bubble_32x64", 20, True, "hllc")])
 def test_fp64_ppm_driver_loop_is_bit_identical_to_the_oracle_loop(name, nsteps, split, solver):
     H, Solver, params_for = _mods()
     pr = PROBLEMS[name]()

@@ -68,6 +68,7 @@ PROBLEMS = {
     "walls_45x33": lambda: _random_box(45, 33, ("reflect",) * 4, 1),
     "mixed_walls_70x66": lambda: _random_box(70, 66, ("reflect", "outflow", "hydrostatic", "reflect"), 2),
     "rt_32x96": lambda: hp.rt(32, 96),
+    "bubble_32x64": lambda: hp.bubble(32, 64),
     "rt_37x50": lambda: hp.rt(37, 50),
 }
 
