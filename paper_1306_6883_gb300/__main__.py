@@ -2,13 +2,15 @@
 
     python -m paper_1306_6883_gb300 PROBLEM [--nx N] [--ny N] [--precision fp32|fp64]
                                             [--steps K | --tmax T] [--seed S] [--split]
-                                            [--riemann two-shock|hllc] [--recon plm|ppm] [--dump FILE]
+                                            [--riemann two-shock|hllc] [--recon plm|ppm] [--host]
+                                            [--dump FILE]
 
 PROBLEM is one of sod, sod_y, kh, sedov, quad, pulse, rt, bubble (seeded set-ups of hydro_problems; rt is
 the Rayleigh-Taylor column with gravity, nx x 3nx by default; bubble a buoyant bubble in a stratified
 atmosphere, nx x 2nx by default).  Runs the device-resident loop (fill ghost
 cells, CFL dt, CTU step; --split: the dimensionally split step; --riemann and --recon choose the Riemann
-solver and the reconstruction) and prints one JSON line with the simulated
+solver and the reconstruction; --host keeps the state in pinned host memory and takes every step through
+hydro_step_host_chained, the whole state going up and down each step) and prints one JSON line with the simulated
 time, step count, wall time, conserved totals and the Riemann-solver counters.  --dump writes the final
 state (dense float64 array, shape (4, ny+8, nx+8)) with numpy.save.
 """
@@ -58,6 +60,7 @@ def main(argv=None):
     ap.add_argument("--split", action="store_true")
     ap.add_argument("--riemann", choices=["two-shock", "hllc"], default="two-shock")
     ap.add_argument("--recon", choices=["plm", "ppm"], default="plm")
+    ap.add_argument("--host", action="store_true")
     ap.add_argument("--dump", default=None)
     a = ap.parse_args(argv)
 
@@ -78,9 +81,16 @@ def main(argv=None):
     t0 = time.perf_counter()
     chunk = 64
     done = 0
+    if a.host:  # the run lives in two pinned host buffers, each step's output the next step's input
+        dt_ = torch.float32 if prec == H.HYDRO_FP32 else torch.float64
+        host = [torch.from_numpy(np.ascontiguousarray(pr.U)).to(dt_).pin_memory() for _ in range(2)]
     while done < steps:
         n = min(chunk, steps - done)
-        s.advance(n, tmax)
+        if a.host:
+            for k in range(done, done + n):
+                s.step_host(host[k % 2], host[(k + 1) % 2], tmax, chained=True)
+        else:
+            s.advance(n, tmax)
         done += n
         if tmax > 0.0:
             t, _ = s.time()
@@ -91,7 +101,7 @@ def main(argv=None):
     st, stats = s.status(raise_on_error=False)
     t, nsteps = s.time()
     out = {"problem": a.problem, "nx": pr.nx, "ny": pr.ny, "precision": a.precision, "split": a.split, "riemann": a.riemann,
-           "recon": a.recon, "t": t,
+           "recon": a.recon, "host": a.host, "t": t,
            "steps": nsteps,
            "wall_s": wall, "zone_updates_per_s": pr.nx * pr.ny * nsteps / wall if wall > 0 else None,
            "totals": s.totals(), "status": H.STATUS_NAMES[st], "riemann_solves": stats[0],

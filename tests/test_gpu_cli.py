@@ -22,7 +22,8 @@ def _cuda():
                                   ["kh", "--nx", "96", "--precision", "fp32", "--steps", "20"],
                                   ["rt", "--nx", "32", "--steps", "12", "--riemann", "hllc", "--recon", "ppm"],
                                   ["sedov", "--nx", "64", "--precision", "fp32", "--steps", "10", "--split"],
-                                  ["bubble", "--nx", "32", "--steps", "15", "--split"]])
+                                  ["bubble", "--nx", "32", "--steps", "15", "--split"],
+                                  ["kh", "--nx", "64", "--precision", "fp32", "--steps", "12", "--host"]])
 def test_cli_runs_and_reports(args):
     r = subprocess.run([sys.executable, "-m", "paper_1306_6883_gb300", *args], cwd=ROOT, capture_output=True,
                        text=True, timeout=600)
@@ -36,3 +37,22 @@ def test_cli_runs_and_reports(args):
     if "--riemann" in args:
         assert out["riemann"] == "hllc" and out["recon"] == "ppm" and out["riemann_iters"] == 0
     assert out["split"] == ("--split" in args)
+
+
+def _run(args, tmp_path, name):
+    dump = os.path.join(str(tmp_path), name + ".npy")
+    r = subprocess.run([sys.executable, "-m", "paper_1306_6883_gb300", *args, "--dump", dump], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1]), dump
+
+
+@pytest.mark.parametrize("args", [["sod", "--nx", "64", "--tmax", "0.05"], ["rt", "--nx", "32", "--steps", "30"]])
+def test_host_resident_run_equals_the_device_run(args, tmp_path):
+    # --host takes every step through hydro_step_host_chained: FP64, the same run bit for bit
+    import numpy as np
+    dev, fd = _run(args, tmp_path, "dev")
+    host, fh = _run(args + ["--host"], tmp_path, "host")
+    assert host["host"] and not dev["host"]
+    assert host["t"] == dev["t"] and host["steps"] == dev["steps"] and host["totals"] == dev["totals"]
+    np.testing.assert_array_equal(np.load(fh)[:, 4:-4, 4:-4], np.load(fd)[:, 4:-4, 4:-4])
