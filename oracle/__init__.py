@@ -55,6 +55,7 @@ def lib():
         L.oracle_slope.restype = ctypes.c_double
         L.oracle_flatten_chi.argtypes = [ctypes.c_double] * 7
         L.oracle_flatten_chi.restype = ctypes.c_double
+        L.oracle_flatten_xi.argtypes = [P, _D, _D]
         L.oracle_trace.argtypes = [P, ctypes.c_double, _D, _D, _D, _D]
         L.oracle_riemann.argtypes = [P, _D, _D, ctypes.c_double, _D, _D, _D, _D, ctypes.POINTER(ctypes.c_int)]
         L.oracle_euler_flux.argtypes = [P, _D, _D]
@@ -145,6 +146,16 @@ def slope(limiter, qm2, qm1, q0, qp1, qp2):
 
 def flatten_chi(pm2, pm1, pp1, pp2, um1, up1, small_pres=1e-20):
     return lib().oracle_flatten_chi(pm2, pm1, pp1, pp2, um1, up1, small_pres)
+
+
+def flatten_xi(p, q):
+    """Flattening coefficient xi[j, i] of every cell from the primitive planes q[k, j, i] (rho, u, v, p),
+    shape (4, ny + 2 ng, nx + 2 ng) (§3.2 flattening; 1 on the outer three rings of cells)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    assert q.shape == (4, p.ny + 2 * p.ng, p.nx + 2 * p.ng)
+    xi = np.zeros(q.shape[1:])
+    _check(lib().oracle_flatten_xi(ctypes.byref(p), _ptr(q), _ptr(xi)), "oracle_flatten_xi")
+    return xi
 
 
 def trace(p, sigma, q, dq):

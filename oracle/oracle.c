@@ -596,6 +596,58 @@ typedef struct {
 
 #define AT(arr, k, j, i) ((arr)[((size_t)(k) * NY + (j)) * NX + (i)])
 
+/* ------------------------------------------------------------------------------------------------ */
+/* Flattening coefficient of every cell (§3.2, flattening "from Colella 1990", whose detector is that of
+ * Colella & Woodward 1984).  q: primitives [4][NY][NX] (rho, u, v, p planes); xi: [NY][NX] output.
+ * Per direction, chi_i is the shock detector of oracle_flatten_chi on the line through cell i (normal
+ * velocity u along x, v along y).  Each cell then also takes the detector of its lower-pressure
+ * neighbour: xi_d(i) = min(chi_i, chi_{i-s}) with s = sign(p_{i+1} - p_{i-1}) (s = +1 where the two are
+ * equal), so the flattened band of a shock reaches one cell further into its high-pressure (post-shock)
+ * side and no further into the low-pressure side.  xi = min(xi_x, xi_y): a cell is flattened as much as
+ * its stronger direction asks.  Defined on cells [3, NX-3) x [3, NY-3); 1 elsewhere
+ * and everywhere when use_flattening = 0.  Returns 0, or 2 when out of memory. */
+int oracle_flatten_xi(const oracle_params* p, const double* q, double* xi) {
+  const int NX = p->nx + 2 * p->ng, NY = p->ny + 2 * p->ng;
+  const size_t plane = (size_t)NX * NY;
+#pragma omp parallel for
+  for (int j = 0; j < NY; ++j)
+    for (int i = 0; i < NX; ++i) AT(xi, 0, j, i) = 1.0;
+  if (!p->use_flattening) return 0;
+  double* chix = calloc(plane, sizeof(double));
+  double* chiy = calloc(plane, sizeof(double));
+  if (!chix || !chiy) {
+    free(chix);
+    free(chiy);
+    return 2;
+  }
+#pragma omp parallel for
+  for (int j = 0; j < NY; ++j)
+    for (int i = 0; i < NX; ++i) {
+      chix[(size_t)j * NX + i] = 1.0;
+      chiy[(size_t)j * NX + i] = 1.0;
+      if (i >= 2 && i < NX - 2)
+        chix[(size_t)j * NX + i] =
+            oracle_flatten_chi(AT(q, 3, j, i - 2), AT(q, 3, j, i - 1), AT(q, 3, j, i + 1), AT(q, 3, j, i + 2),
+                               AT(q, 1, j, i - 1), AT(q, 1, j, i + 1), p->small_pres);
+      if (j >= 2 && j < NY - 2)
+        chiy[(size_t)j * NX + i] =
+            oracle_flatten_chi(AT(q, 3, j - 2, i), AT(q, 3, j - 1, i), AT(q, 3, j + 1, i), AT(q, 3, j + 2, i),
+                               AT(q, 2, j - 1, i), AT(q, 2, j + 1, i), p->small_pres);
+    }
+#pragma omp parallel for
+  for (int j = 3; j < NY - 3; ++j)
+    for (int i = 3; i < NX - 3; ++i) {
+      int sx = (AT(q, 3, j, i + 1) - AT(q, 3, j, i - 1)) >= 0.0 ? 1 : -1;
+      int sy = (AT(q, 3, j + 1, i) - AT(q, 3, j - 1, i)) >= 0.0 ? 1 : -1;
+      double xix = fmin(chix[(size_t)j * NX + i], chix[(size_t)j * NX + i - sx]);
+      double xiy = fmin(chiy[(size_t)j * NX + i], chiy[(size_t)(j - sy) * NX + i]);
+      AT(xi, 0, j, i) = fmin(xix, xiy);
+    }
+  free(chix);
+  free(chiy);
+  return 0;
+}
+
 int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) {
   if (!params_ok(p) || !U || !(dt >= 0.0)) return 1;
   const int ng = p->ng, nx = p->nx, ny = p->ny, NX = nx + 2 * ng, NY = ny + 2 * ng;
@@ -634,45 +686,10 @@ int oracle_step(const oracle_params* p, double* U, double dt, oracle_stats* st) 
       for (int k = 0; k < 4; ++k) AT(q, k, j, i) = qc[k];
     }
 
-  /* 2. flattening: chi per direction, xi_d = min(chi_i, chi_{i-s}), s = sign(p_{i+1} - p_{i-1}) (+1 at 0),
-   *    then xi = min(xi_x, xi_y); defined on cells [3, NX-3) x [3, NY-3) */
-#pragma omp parallel for
-  for (int j = 0; j < NY; ++j)
-    for (int i = 0; i < NX; ++i) AT(xi, 0, j, i) = 1.0;
-  if (p->use_flattening) {
-    double* chix = calloc(plane, sizeof(double));
-    double* chiy = calloc(plane, sizeof(double));
-    if (!chix || !chiy) {
-      free(chix);
-      free(chiy);
-      err = 2;
-      goto done;
-    }
-#pragma omp parallel for
-    for (int j = 0; j < NY; ++j)
-      for (int i = 0; i < NX; ++i) {
-        chix[(size_t)j * NX + i] = 1.0;
-        chiy[(size_t)j * NX + i] = 1.0;
-        if (i >= 2 && i < NX - 2)
-          chix[(size_t)j * NX + i] =
-              oracle_flatten_chi(AT(q, 3, j, i - 2), AT(q, 3, j, i - 1), AT(q, 3, j, i + 1), AT(q, 3, j, i + 2),
-                                 AT(q, 1, j, i - 1), AT(q, 1, j, i + 1), p->small_pres);
-        if (j >= 2 && j < NY - 2)
-          chiy[(size_t)j * NX + i] =
-              oracle_flatten_chi(AT(q, 3, j - 2, i), AT(q, 3, j - 1, i), AT(q, 3, j + 1, i), AT(q, 3, j + 2, i),
-                                 AT(q, 2, j - 1, i), AT(q, 2, j + 1, i), p->small_pres);
-      }
-#pragma omp parallel for
-    for (int j = 3; j < NY - 3; ++j)
-      for (int i = 3; i < NX - 3; ++i) {
-        int sx = (AT(q, 3, j, i + 1) - AT(q, 3, j, i - 1)) >= 0.0 ? 1 : -1;
-        int sy = (AT(q, 3, j + 1, i) - AT(q, 3, j - 1, i)) >= 0.0 ? 1 : -1;
-        double xix = fmin(chix[(size_t)j * NX + i], chix[(size_t)j * NX + i - sx]);
-        double xiy = fmin(chiy[(size_t)j * NX + i], chiy[(size_t)(j - sy) * NX + i]);
-        AT(xi, 0, j, i) = fmin(xix, xiy);
-      }
-    free(chix);
-    free(chiy);
+  /* 2. flattening coefficient xi (oracle_flatten_xi) */
+  if (oracle_flatten_xi(p, q, xi)) {
+    err = 2;
+    goto done;
   }
 
   /* 3. limited slopes of the primitives in x and y, multiplied by xi */

@@ -58,6 +58,9 @@ void oracle_cons_to_prim(const oracle_params* p, const double U[4], double q[4])
 void oracle_prim_to_cons(const oracle_params* p, const double q[4], double U[4]);
 double oracle_slope(int limiter, double qm2, double qm1, double q0, double qp1, double qp2);
 double oracle_flatten_chi(double pm2, double pm1, double pp1, double pp2, double um1, double up1, double small_pres);
+/* flattening coefficient of every cell from the primitives q [4][NY][NX] (rho, u, v, p planes) into
+ * xi [NY][NX]: xi = min over x and y of min(chi_i, chi_{i-s}), s = sign(p_{i+1} - p_{i-1}); 0 ok, 2 no memory */
+int oracle_flatten_xi(const oracle_params* p, const double* q, double* xi);
 void oracle_trace(const oracle_params* p, double sigma, const double q[4], const double dq[4], double qL[4],
                   double qR[4]);
 /* PPM: edge values (aL, aR) of the middle cell of a[0..4] after the monotonicity constraints and the

@@ -24,6 +24,17 @@ MUTATIONS = {
         ("{{0.0, -0.5 * rho / c, 0.0, 0.5 / (c * c)},", "{{0.0, 0.5 * rho / c, 0.0, 0.5 / (c * c)},")],
     "fourth-order slope constant": [("double d4 = (4.0 / 3.0) * dc", "double d4 = (1.0) * dc")],
     "flattening compression test": [("int compress = (um1 - up1) > 0.0;", "int compress = (um1 - up1) < 0.0;")],
+    "flattening takes the higher-pressure neighbour in x": [
+        ("chix[(size_t)j * NX + i - sx]", "chix[(size_t)j * NX + i + sx]")],
+    "flattening takes the higher-pressure neighbour in y": [
+        ("chiy[(size_t)(j - sy) * NX + i]", "chiy[(size_t)(j + sy) * NX + i]")],
+    "flattening directions combined by max": [("AT(xi, 0, j, i) = fmin(xix, xiy);", "AT(xi, 0, j, i) = fmax(xix, xiy);")],
+    "flattening ramp start": [("const double z0 = 0.75, z1 = 0.85, delta = 0.33;",
+                               "const double z0 = 0.7, z1 = 0.85, delta = 0.33;")],
+    "flattening ramp end": [("const double z0 = 0.75, z1 = 0.85, delta = 0.33;",
+                             "const double z0 = 0.75, z1 = 0.9, delta = 0.33;")],
+    "flattening jump threshold": [("const double z0 = 0.75, z1 = 0.85, delta = 0.33;",
+                                   "const double z0 = 0.75, z1 = 0.85, delta = 0.4;")],
     "shock mass flux": [("const double g1 = (g + 1.0) / (2.0 * g);", "const double g1 = (g + 1.0) / (2.0);")],
     "star density sign": [("double rst = 1.0 / (1.0 / ro - (pst - po) / (wo * wo));",
                            "double rst = 1.0 / (1.0 / ro + (pst - po) / (wo * wo));")],
@@ -92,7 +103,8 @@ def test_pins_catch_the_planted_mistake(name):
             src = src.replace(a, b)
         open(path, "w").write(src)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-                            "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_step.py",
+                            "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_flattening.py",
+                            "tests/test_oracle_step.py",
                             "tests/test_oracle_gravity.py", "tests/test_oracle_split.py",
                             "tests/test_oracle_hllc.py", "tests/test_oracle_ppm.py"],
                            cwd=d, capture_output=True, text=True, timeout=600)
