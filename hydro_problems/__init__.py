@@ -178,6 +178,29 @@ def pulse(nx=64, ny=64, A=60.0, u0=1.0, v0=1.0, p0=1.0, gamma=1.4):
                    extra={"A": A, "u0": u0, "v0": v0})
 
 
+def stream(nx=256, ny=256, mach=100.0, angle=0.0, rho0=1.0, p0=1.0, density_noise=0.01, seed=0, gamma=1.4,
+           domain=(0.0, 1.0, 0.0, 1.0), collide=False):
+    """Hypersonic stream, the regime where E - rho |u|^2 / 2 cancels (not one of the paper's problems, which
+    run at low Mach): speed mach * c0 (c0 = sqrt(gamma p0 / rho0)) at `angle` radians to x, uniform
+    pressure p0, density rho0 (1 + density_noise U[-1, 1]) per cell (seeded, row-major); periodic.  Kinetic
+    over total energy 1 - 1 / (1 + gamma (gamma - 1) mach^2 / 2) (0.99964 at Mach 100, gamma 1.4).
+    collide: the stream runs along +x in the left half and along -x in the right half (two strong shocks
+    form at x = 1/2), outflow in x."""
+    X, Y = _centres(nx, ny, domain)
+    c0 = np.sqrt(gamma * p0 / rho0)
+    rho = np.full((ny, nx), rho0)
+    if density_noise > 0.0:
+        rho = rho0 * (1.0 + density_noise * np.random.default_rng(seed).uniform(-1.0, 1.0, size=(ny, nx)))
+    sgn = np.where(X < 0.5 * (domain[0] + domain[1]), 1.0, -1.0) if collide else np.ones((ny, nx))
+    u = sgn * mach * c0 * np.cos(angle)
+    v = sgn * mach * c0 * np.sin(angle)
+    p = np.full((ny, nx), p0)
+    bc = ("outflow", "outflow", "periodic", "periodic") if collide else ("periodic",) * 4
+    return Problem("stream", nx, ny, _pack(rho, u, v, p, gamma), bc, gamma=gamma, tmax=np.inf, domain=domain,
+                   extra={"mach": mach, "angle": angle, "seed": seed, "density_noise": density_noise,
+                          "collide": collide})
+
+
 def ensemble_sizes(n=256, seed=0, choices=(64, 128, 256, 512)):
     """Grid sizes of an ensemble of independent problems: n square sizes drawn uniformly from choices."""
     g = np.random.default_rng(seed)

@@ -70,8 +70,8 @@ typedef enum { HYDRO_RECON_PLM = 0, HYDRO_RECON_PPM = 1 } hydro_recon;
 typedef enum {
   HYDRO_FP64 = 0, /* state and arithmetic in double */
   HYDRO_FP32 = 1  /* state and stencil arithmetic in float; the pressure of a cell whose kinetic energy
-                     is within 0.1% of its total energy is recomputed in double; dt and conserved totals
-                     are reduced in double */
+                     is within 0.1% of its total energy (recover_ke_frac) is recomputed in double; dt and
+                     conserved totals are reduced in double */
 } hydro_precision;
 
 /* Parameters of one problem (the paper's RuntimeParameters for the compressible solver, §2). */
@@ -105,6 +105,12 @@ typedef struct {
   int reconstruction;               /* hydro_recon: piecewise linear (default; `limiter` applies) or
                                        piecewise parabolic (the PPM upgrade §3.2 points to; `limiter` is
                                        unused; same restrictions as HLLC) */
+  double recover_ke_frac;           /* FP32 only (EOS of Eqs. 11-12): where the kinetic energy of a cell or
+                                       face state exceeds this fraction of its total energy, the pressure
+                                       (gamma - 1)(E - rho |u|^2 / 2) is recomputed in double from the float
+                                       conserved values, so the cancellation of E - rho |u|^2 / 2 is not left
+                                       to float arithmetic.  Default 0.999; 0 recomputes every one; a value
+                                       above 1 never does.  Must be finite and >= 0.  FP64 ignores it. */
 } hydro_params;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -112,6 +118,9 @@ typedef struct hydro_ctx hydro_ctx;
 /* Fill *p with the defaults above for an nx x ny grid on [0,1]^2, outflow on all sides, FP64.
  * Returns HYDRO_EINVAL if p is NULL. */
 hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision);
+
+/* sizeof(hydro_params) as compiled into the library, for bindings that mirror the struct. */
+size_t hydro_params_size(void);
 
 /* Row pitch (elements) and total byte size of one state array for these parameters; 0 if invalid. */
 size_t hydro_state_pitch(const hydro_params* p);
@@ -226,9 +235,11 @@ hydro_status hydro_conserved_totals(hydro_ctx* ctx, double out[4]);
  * Needs no context and calls no cudaMalloc, cudaFree or other allocating routine.  Its reduction scratch
  * is one file-scope device array of (4 HYDRO_NOALLOC_MAX_ROWS + 8) doubles (512 KB), which every GPU
  * that loads the library holds until the process exits.  The first call on a device looks up that
- * array's device address (with that device current) and caches it, so make the first call on each device
- * before any stream capture.  Every call shares the one array: calls whose kernels overlap on the GPU
- * (two streams, two threads) race and return wrong totals; serialise them.  Synchronises the stream.
+ * array's device address (with that device current) and caches it for the rest of the process, so make
+ * the first call on each device before any stream capture; a cudaDeviceReset of the device invalidates the
+ * cached address, and calls after one are not supported.  Every call shares the one array: calls whose
+ * kernels overlap on the GPU (two streams, two threads) race and return wrong totals; serialise them.
+ * The call synchronises the stream and copies the totals into `out` before it returns.
  * Errors: HYDRO_EINVAL (bad params or NULL pointers), HYDRO_ERANGE (ny > HYDRO_NOALLOC_MAX_ROWS),
  * HYDRO_ECUDA. */
 #define HYDRO_NOALLOC_MAX_ROWS 16384
@@ -237,7 +248,9 @@ hydro_status hydro_conserved_totals_noalloc(const hydro_params* p, const void* d
 
 /* Read and clear the device status word: HYDRO_OK, or the first of HYDRO_ENONFINITE, HYDRO_ENEGATIVE,
  * HYDRO_ENONCONV, HYDRO_ETIMEOUT (a tile's TMA copy did not land within the bounded wait) recorded since
- * the last call.  Synchronises.  If stats is not NULL it receives
+ * the last call.  After HYDRO_ETIMEOUT the state the steps wrote is not to be trusted: discard it and
+ * upload a known state again (hydro_last_error says whether a copy was still outstanding when its tile
+ * gave up, in which case later tiles on the same SM may have been overwritten as well).  Synchronises.  If stats is not NULL it receives
  * {riemann solves, riemann iterations, unconverged solves} accumulated since hydro_init. */
 hydro_status hydro_sync_status(hydro_ctx* ctx, unsigned long long stats[3]);
 
@@ -319,12 +332,19 @@ hydro_status hydro_set_harvest_gate(hydro_ctx* ctx, double gate_dp, double gate_
 typedef struct hydro_batch hydro_batch;
 
 /* Create an ensemble of n members.  params, d_states, d_states_alt: arrays of n entries.  Members take the
- * unsplit piecewise-linear step with the two-shock solver.
- * Errors: HYDRO_EINVAL (bad member, mixed precisions, split = 1, the HLLC solver or PPM), HYDRO_ENOMEM,
- * HYDRO_ECUDA. */
+ * unsplit piecewise-linear step with the two-shock solver; all share one precision and one use_learned_guess
+ * (1: FP32 members whose iterations start from the network set by hydro_batch_set_riemann_model).
+ * Errors: HYDRO_EINVAL (bad member, mixed precisions or use_learned_guess, split = 1, the HLLC solver or PPM),
+ * HYDRO_ENOMEM, HYDRO_ECUDA. */
 hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* d_states, void* const* d_states_alt,
                                 void* cuda_stream, hydro_batch** out);
 void hydro_batch_destroy(hydro_batch* b);
+
+/* Start every member's Riemann iterations from the learned proposal of network m (see hydro_set_riemann_model;
+ * the members must have been created with use_learned_guess = 1; m = NULL clears it, and such an ensemble
+ * then refuses to run).  One copy of the weights serves all members; warps read it from global memory only
+ * where their gate opens.  m must outlive its use.  Captured graphs are dropped when m changes. */
+hydro_status hydro_batch_set_riemann_model(hydro_batch* b, const hydro_mlp* m);
 
 /* Tile-shape autotuner: for every size class time `reps` launches of each candidate tile shape on the
  * current states (without advancing them) and keep the fastest.  chosen_shapes (optional) receives one

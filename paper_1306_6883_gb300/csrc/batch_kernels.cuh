@@ -109,12 +109,16 @@ static __device__ __noinline__ void member_tile_done(const BatchMember& m, doubl
 // members first: each CTA takes the next tile from an atomic queue until the list is exhausted.  A tile
 // reads the member's factors scf[parity], folds its cells' CFL minimum into the member's accumulator, and
 // the member's last tile sets its next factors scf[1 - parity] (and, if advance, its time and step count).
-template <typename R, int TX, int TY, int NT>
+// MODE FACE_LEARNED: every member's Riemann iterations start from the learned proposal of the weights mlp,
+// which the warps whose gate opens read from global memory (L1-resident; a shared-memory copy per CTA would
+// cost the third CTA per SM).
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(const BatchMember* __restrict__ mem,
                                                        const int4* __restrict__ tiles, int ntiles,
                                                        unsigned int* __restrict__ queue, int parity,
                                                        DevScratch* __restrict__ agg,
-                                                       const CUtensorMap* __restrict__ tmaps, int advance) {
+                                                       const CUtensorMap* __restrict__ tmaps, int advance,
+                                                       const MlpBlob* __restrict__ mlp) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int cur;
   __shared__ R wmin[NT / 32];
@@ -132,8 +136,9 @@ __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(con
     f.load(m.scr->scf[parity]);
     const CUtensorMap* tm = (tmaps != nullptr && m.tma) ? tmaps + 2 * t.x + parity : nullptr;
     R cmin = is_f32<R>() ? (R)FLT_MAX : (R)DBL_MAX;
-    ctu_tile<R, TX, TY, NT, FACE_PLAIN, true, true>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z,
-                                                    smem_raw, cnt, FaceHook{}, nullptr, &cmin, tm);
+    ctu_tile<R, TX, TY, NT, MODE, true, true>(m.P, s, f, (const R*)m.U[parity], (R*)m.U[1 - parity], t.y, t.z,
+                                              smem_raw, cnt, FaceHook{}, face_kind(MODE) == FACE_LEARNED ? mlp : nullptr,
+                                              &cmin, tm);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       const R o = __shfl_xor_sync(0xffffffffu, cmin, off);
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(NT, is_f32<R>() ? 3 : 2) batch_step_kernel(con
   }
 }
 
-template <typename R, int TX, int TY, int NT>
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 struct BatchStep {
   // per device (function attributes and occupancy belong to the device's context): set by prepare()
   static std::atomic<int> blocks_per_sm[64];
@@ -175,18 +180,18 @@ struct BatchStep {
     if (dev >= 64) return cudaErrorInvalidDevice;
     if (blocks_per_sm[dev].load(std::memory_order_relaxed) > 0) return cudaSuccess;
     const size_t smem = TileLayout<R, TX, TY>::bytes;
-    e = cudaFuncSetAttribute(batch_step_kernel<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(batch_step_kernel<R, TX, TY, NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<R, TX, TY, NT>, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<R, TX, TY, NT, MODE>, NT, smem);
     if (e != cudaSuccess) return e;
     blocks_per_sm[dev].store(b > 0 ? b : 1, std::memory_order_relaxed);
     return cudaSuccess;
   }
   static cudaError_t launch(const BatchMember* mem, const int4* tiles, int ntiles, unsigned int* queue, int parity,
                             DevScratch* agg, cudaStream_t stream, int* grid_out, const CUtensorMap* tmaps,
-                            int advance) {
+                            int advance, const MlpBlob* mlp = nullptr) {
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
@@ -199,12 +204,12 @@ struct BatchStep {
     if (grid <= 0) return cudaSuccess;
     e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), stream);
     if (e != cudaSuccess) return e;
-    batch_step_kernel<R, TX, TY, NT><<<grid, NT, TileLayout<R, TX, TY>::bytes, stream>>>(mem, tiles, ntiles, queue,
-                                                                                         parity, agg, tmaps, advance);
+    batch_step_kernel<R, TX, TY, NT, MODE><<<grid, NT, TileLayout<R, TX, TY>::bytes, stream>>>(
+        mem, tiles, ntiles, queue, parity, agg, tmaps, advance, mlp);
     return cudaGetLastError();
   }
 };
-template <typename R, int TX, int TY, int NT>
-std::atomic<int> BatchStep<R, TX, TY, NT>::blocks_per_sm[64] = {};
+template <typename R, int TX, int TY, int NT, int MODE>
+std::atomic<int> BatchStep<R, TX, TY, NT, MODE>::blocks_per_sm[64] = {};
 
 }  // namespace hydro

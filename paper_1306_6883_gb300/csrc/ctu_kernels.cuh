@@ -134,8 +134,11 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
                                                             StepScalars* __restrict__ sc_next,
                                                             DevScratch* __restrict__ scr, double tmax,
                                                             const __grid_constant__ CUtensorMap tmap, int use_tma,
-                                                            int by0, unsigned int nblocks) {
+                                                            int by0, unsigned int nblocks,
+                                                            const MlpBlob* __restrict__ mlp) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  // FACE_LEARNED: the network's weights (read from global memory by the warps whose gate opens)
+  const MlpBlob* wsm = face_kind(MODE) == FACE_LEARNED ? mlp : nullptr;
   SP<R> s;
   s.load(P);
   StepFactors<R> f;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
       cfl_value(s, u[0], u[1], u[2], u[3], cmin, cnt.flags);
     }
   } else {
-    ctu_tile<R, TX, TY, NT, MODE, true>(P, s, f, Uin, Uout, blockIdx.x, by, smem_raw, cnt, FaceHook{}, nullptr,
+    ctu_tile<R, TX, TY, NT, MODE, true>(P, s, f, Uin, Uout, blockIdx.x, by, smem_raw, cnt, FaceHook{}, wsm,
                                         &cmin, use_tma ? &tmap : nullptr);
   }
   flush_counters<NT>(cnt, scr);
@@ -197,11 +200,12 @@ __global__ void __launch_bounds__(NT, min_blocks<R>()) ctu_step_fused_kernel(KPa
   }
 }
 
-// band: tile rows [band.x, band.x + band.y) of the step (band.y <= 0: all of them)
+// band: tile rows [band.x, band.x + band.y) of the step (band.y <= 0: all of them).  mlp: the network of
+// MODE FACE_LEARNED (device).
 template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN>
 cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const StepScalars* sc_cur,
                                   StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
-                                  cudaStream_t stream, int2 band = make_int2(0, 0)) {
+                                  cudaStream_t stream, int2 band = make_int2(0, 0), const MlpBlob* mlp = nullptr) {
   const size_t smem = TileLayout<R, TX, TY>::bytes;
   static std::atomic<unsigned long long> attr_done{0};
   cudaError_t e = smem_attr_once(ctu_step_fused_kernel<R, TX, TY, NT, MODE>, smem, attr_done);
@@ -212,7 +216,7 @@ cudaError_t launch_ctu_step_fused(const KParams& P, const R* Uin, R* Uout, const
   dim3 grid(tx, ny);
   ctu_step_fused_kernel<R, TX, TY, NT, MODE><<<grid, NT, smem, stream>>>(
       P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap ? *tmap : CUtensorMap{}, tmap ? 1 : 0, y0,
-      (unsigned int)tx * (unsigned int)ty);
+      (unsigned int)tx * (unsigned int)ty, mlp);
   return cudaGetLastError();
 }
 

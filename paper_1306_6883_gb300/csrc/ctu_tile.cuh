@@ -199,10 +199,12 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     const bool landed = mbar_wait(bar, 0, polls);
     if (__syncthreads_or(!landed)) {
       // the copy did not complete within the poll budget: report it, give it one more budget to land
-      // (the shared memory must not be released under it) and leave this tile
+      // (the shared memory should not be released under it) and leave this tile.  If it has not landed after
+      // that either, say so apart: the step's output is then to be discarded, and so is anything a later
+      // block on this SM computed while the copy could still arrive
       cnt.flags |= STATUS_TIMEOUT;
-      mbar_wait(bar, 0, polls);
-      __syncthreads();
+      const bool late = !mbar_wait(bar, 0, polls);
+      if (__syncthreads_or(late)) cnt.flags |= STATUS_TIMEOUT_INFLIGHT;
       if (tid == 0) mbar_inval(bar);
       return;
     }
@@ -415,40 +417,38 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       const int e = e0 + (tid & 31);
       const bool isx = e < nXIa;
       const bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF && (e - nXIa) % RW < TX);
-      R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4], UL[4], UR[4];
+      R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4];
       if (active) {
         if (isx) {
           const int fx = e % SX, ty = e / SX;  // face lx = fx + 4, row ly = ty + 4
           const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
           // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
           const int fL = ty * SX + fx, fR = fL + 1;
-          prim_to_cons(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
-          prim_to_cons(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+          R dL[4], dR[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const R* fy = sfyh + k * (TY + 1) * SX;
-            UL[k] = UL[k] - hy * (fy[fL + SX] - fy[fL]);
-            UR[k] = UR[k] - hy * (fy[fR + SX] - fy[fR]);
+            dL[k] = fy[fL + SX] - fy[fL];
+            dR[k] = fy[fR + SX] - fy[fR];
           }
-          cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], a[0], a[1], a[2], a[3]);
-          cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], bq[0], bq[1], bq[2], bq[3]);
+          correct_state(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], dL, hy, a);
+          correct_state(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], dR, hy, bq);
         } else {
           const int f = e - nXIa;
           const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
           const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
           // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
           const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
-          prim_to_cons(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], UL[0], UL[1], UL[2], UL[3]);
-          prim_to_cons(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], UR[0], UR[1], UR[2], UR[3]);
+          R dL[4], dR[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const R* fxh = sfxh + k * SY * (TX + 1);
-            UL[k] = UL[k] - hx * (fxh[fL + 1] - fxh[fL]);
-            UR[k] = UR[k] - hx * (fxh[fR + 1] - fxh[fR]);
+            dL[k] = fxh[fL + 1] - fxh[fL];
+            dR[k] = fxh[fR + 1] - fxh[fR];
           }
           R ql[4], qrr[4];
-          cons_to_prim(s, UL[0], UL[1], UL[2], UL[3], ql[0], ql[1], ql[2], ql[3]);
-          cons_to_prim(s, UR[0], UR[1], UR[2], UR[3], qrr[0], qrr[1], qrr[2], qrr[3]);
+          correct_state(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], dL, hx, ql);
+          correct_state(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], dR, hx, qrr);
           a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
           bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
         }

@@ -62,6 +62,8 @@ struct hydro_batch {
   std::vector<ShapeGroup> groups;
   CUtensorMap* d_tmaps = nullptr; // FP32: two TMA descriptors per member (its buffers, its class's tile box)
   int parity = 0;                 // members' current state is U[parity]
+  int learned = 0;                // the members were created with use_learned_guess = 1
+  const hydro_mlp* mlp = nullptr; // their network (hydro_batch_set_riemann_model)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> executable graph
   char err[512] = {0};
 };
@@ -145,6 +147,11 @@ static void drop_graphs(hydro_batch* b) {
   b->graphs.clear();
 }
 
+// The network the members start their Riemann iterations from (NULL: the acoustic start).
+static const hydro::MlpBlob* batch_model(const hydro_batch* b) {
+  return b->learned && b->mlp ? (const hydro::MlpBlob*)hydro_mlp_device_blob(b->mlp) : nullptr;
+}
+
 // nsteps steps of every member from parity p0 on stream s (used directly and under stream capture): the dt
 // of the current states, then the fused steps, each handing its members' next factors to the following one
 static cudaError_t enqueue_run(hydro_batch* b, int nsteps, int p0, cudaStream_t s) {
@@ -153,7 +160,7 @@ static cudaError_t enqueue_run(hydro_batch* b, int nsteps, int p0, cudaStream_t 
     for (auto& g : b->groups) {
       if (e != cudaSuccess) break;
       e = hydro::batch_step(b->precision, g.shape, b->d_mem, g.d_tiles, g.ntiles, g.d_queue, (p0 + k) & 1, b->d_agg,
-                            s, nullptr, b->d_tmaps, 1);
+                            s, nullptr, b->d_tmaps, 1, batch_model(b));
     }
   return e;
 }
@@ -168,7 +175,8 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
   const int prec = params[0].precision;
   for (int i = 0; i < n; ++i) {
     if (hydro_state_pitch(&params[i]) == 0 || params[i].precision != prec || params[i].split ||
-        params[i].riemann_solver != HYDRO_RIEMANN_TWO_SHOCK || params[i].reconstruction != HYDRO_RECON_PLM)
+        params[i].riemann_solver != HYDRO_RIEMANN_TWO_SHOCK || params[i].reconstruction != HYDRO_RECON_PLM ||
+        params[i].use_learned_guess != params[0].use_learned_guess)
       return HYDRO_EINVAL;
     if (!d_states[i] || !d_states_alt[i] || ((uintptr_t)d_states[i] & 255) || ((uintptr_t)d_states_alt[i] & 255))
       return HYDRO_EINVAL;
@@ -179,6 +187,7 @@ hydro_status hydro_batch_create(int n, const hydro_params* params, void* const* 
   b->precision = prec;
   b->stream = (cudaStream_t)cuda_stream;
   b->params.assign(params, params + n);
+  b->learned = params[0].use_learned_guess;
   cudaError_t e = cudaMalloc((void**)&b->d_scr, sizeof(DevScratch) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_agg, sizeof(DevScratch));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_mem, sizeof(BatchMember) * n);
@@ -258,8 +267,28 @@ void hydro_batch_destroy(hydro_batch* b) {
   delete b;
 }
 
+hydro_status hydro_batch_set_riemann_model(hydro_batch* b, const hydro_mlp* m) {
+  if (!b) return HYDRO_EINVAL;
+  if (m && !b->learned) {
+    snprintf(b->err, sizeof b->err, "the members were created with use_learned_guess = 0");
+    return HYDRO_EINVAL;
+  }
+  if (m != b->mlp) drop_graphs(b);  // captured runs hold the old weights' address
+  b->mlp = m;
+  return HYDRO_OK;
+}
+
+static hydro_status check_batch_model(hydro_batch* b) {
+  if (b->learned && !b->mlp) {
+    snprintf(b->err, sizeof b->err, "use_learned_guess = 1 needs a model (hydro_batch_set_riemann_model)");
+    return HYDRO_EINVAL;
+  }
+  return HYDRO_OK;
+}
+
 hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes) {
   if (!b || reps < 1) return HYDRO_EINVAL;
+  if (check_batch_model(b) != HYDRO_OK) return HYDRO_EINVAL;
   // valid step factors for the current state, without advancing time
   cudaError_t e = hydro::batch_dt(b->precision, b->d_mem, b->d_dt, b->ndt, b->parity, 0, b->stream);
   if (e != cudaSuccess) return fail(b, e, "autotune set-up");
@@ -277,7 +306,7 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int reps, int* chosen_shapes) 
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
         if (r == 1) cudaEventRecord(e0, b->stream);
         e = hydro::batch_step(b->precision, sh, b->d_mem, c.d_tiles, c.ntiles, c.d_queue, b->parity, b->d_agg,
-                              b->stream, nullptr, b->d_tmaps, 0);
+                              b->stream, nullptr, b->d_tmaps, 0, batch_model(b));
       }
       cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -320,6 +349,7 @@ hydro_status hydro_batch_class_info(const hydro_batch* b, int k, int* nx, int* n
 
 hydro_status hydro_batch_run(hydro_batch* b, int nsteps, int use_graph) {
   if (!b || nsteps < 0) return HYDRO_EINVAL;
+  if (check_batch_model(b) != HYDRO_OK) return HYDRO_EINVAL;
   if (nsteps == 0) return HYDRO_OK;
   cudaError_t e = cudaSuccess;
   if (!use_graph) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "hydro_device.cuh"
+#include "mlp.cuh"
 
 namespace hydro {
 
@@ -32,9 +33,11 @@ cudaError_t batch_dt(int precision, const BatchMember* mem, const int4* tab, int
 // step), and the member's last tile writes scf[1 - parity] and, if advance, adds the step to its time.
 // tmaps (FP32, may be NULL): device array of two TMA descriptors per member (one per state buffer) with the
 // box of `shape`, used for members whose tma flag is set
+// mlp (FP32 only, may be NULL): every member's Riemann iterations start from the learned proposal of
+// these weights
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
                        unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out,
-                       const CUtensorMap* tmaps, int advance);
+                       const CUtensorMap* tmaps, int advance, const MlpBlob* mlp = nullptr);
 // set the kernel attributes of every shape (call once before any stream capture)
 cudaError_t batch_prepare(int precision);
 

@@ -174,6 +174,7 @@ static int params_valid(const hydro_params* p, char* why, size_t n) {
     BAD("reconstruction must be HYDRO_RECON_PLM or HYDRO_RECON_PPM");
   if (p->reconstruction == HYDRO_RECON_PPM && p->use_learned_guess != 0)
     BAD("the learned proposal runs with the piecewise-linear step only");
+  if (!(p->recover_ke_frac >= 0.0 && p->recover_ke_frac < 1e30)) BAD("recover_ke_frac must be finite and >= 0");
   return 1;
 #undef BAD
 }
@@ -239,6 +240,7 @@ void fill_kparams(const hydro_params* p, KParams* kp) {
   k.cvisc_f = (float)k.cvisc;
   k.dx_f = (float)k.dx;
   k.dy_f = (float)k.dy;
+  k.rec_f = (float)p->recover_ke_frac;
 }
 
 }  // namespace hydro
@@ -271,8 +273,11 @@ hydro_status hydro_default_params(hydro_params* p, int nx, int ny, int precision
   p->split = 0;
   p->riemann_solver = HYDRO_RIEMANN_TWO_SHOCK;
   p->reconstruction = HYDRO_RECON_PLM;
+  p->recover_ke_frac = 0.999;
   return HYDRO_OK;
 }
+
+size_t hydro_params_size(void) { return sizeof(hydro_params); }
 
 size_t hydro_state_pitch(const hydro_params* p) {
   if (!params_valid(p, nullptr, 0)) return 0;
@@ -415,12 +420,19 @@ static cudaError_t launch_split_step(hydro_ctx* c, const hydro::StepScalars& sc_
   return e;
 }
 
+static void drop_host_graphs(hydro_ctx* c);
+
 static hydro_status check_model(hydro_ctx* c) {
   if (c->p.use_learned_guess == 1 && !c->mlp) {
     set_err(c, "use_learned_guess = 1 needs a model (hydro_set_riemann_model)");
     return HYDRO_EINVAL;
   }
   return HYDRO_OK;
+}
+
+// The network the fused step starts its Riemann iterations from (NULL: the acoustic start).
+static const hydro::MlpBlob* ctx_model(const hydro_ctx* c) {
+  return c->p.use_learned_guess == 1 && c->mlp ? (const hydro::MlpBlob*)hydro_mlp_device_blob(c->mlp) : nullptr;
 }
 
 hydro_status hydro_step(hydro_ctx* c, double dt) {
@@ -455,8 +467,8 @@ hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
     c->fused_valid = 1;
     return HYDRO_OK;
   }
-  if (c->p.use_learned_guess == 1 || c->harvest) {  // the optional face variants use the separate passes
-    if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  if (c->harvest) {  // the harvest's face variant uses the separate passes
     cudaError_t e = hydro::fill_ghost(c->p.precision, c->kp, c->state[c->cur], c->stream);
     if (e == cudaSuccess) e = hydro::cfl_dt(c->p.precision, c->kp, c->state[c->cur], c->scr, tmax, 1, nullptr, c->stream);
     c->fused_valid = 0;
@@ -472,7 +484,7 @@ hydro_status hydro_step_fused(hydro_ctx* c, double tmax) {
   if (e == cudaSuccess)
     e = hydro::ctu_step_fused(c->p.precision, c->kp, c->state[c->cur], c->state[1 - c->cur],
                               &c->scr->scf[c->fused_parity], &c->scr->scf[1 - c->fused_parity], c->scr, tmax,
-                              c->tma_ok ? &c->tmap[c->cur] : nullptr, c->stream);
+                              c->tma_ok ? &c->tmap[c->cur] : nullptr, c->stream, make_int2(0, 0), ctx_model(c));
   if (e != cudaSuccess) return cuda_fail(c, e, "step_fused");
   ++c->step_calls;
   c->cur = 1 - c->cur;
@@ -515,6 +527,7 @@ hydro_status hydro_set_harvest_gate(hydro_ctx* c, double gate_dp, double gate_du
 hydro_status hydro_set_riemann_model(hydro_ctx* c, const hydro_mlp* m) {
   if (!c) return HYDRO_EINVAL;
   if (m && c->p.precision != HYDRO_FP32) return HYDRO_EINVAL;
+  if (m != c->mlp) drop_host_graphs(c);  // captured host steps hold the old weights' address
   c->mlp = m;
   return HYDRO_OK;
 }
@@ -579,7 +592,13 @@ hydro_status hydro_sync_status(hydro_ctx* c, unsigned long long stats[3]) {
     cudaError_t e = cudaMemsetAsync(&c->scr->status, 0, sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "clear status");
-    set_err(c, "device status flags 0x%x", f);
+    if (f & hydro::STATUS_TIMEOUT_INFLIGHT)
+      set_err(c, "device status flags 0x%x: a tile copy had not landed after two bounded waits; discard the "
+                 "state and upload it again", f);
+    else if (f & hydro::STATUS_TIMEOUT)
+      set_err(c, "device status flags 0x%x: a tile copy timed out; discard the state and upload it again", f);
+    else
+      set_err(c, "device status flags 0x%x", f);
   }
   return status_from_flags(f);
 }
@@ -738,7 +757,8 @@ static cudaError_t enqueue_host_step(hydro_ctx* c, const void* host_in, void* ho
     e = cudaStreamWaitEvent(bs, chained ? c->ev_up[b] : c->ev_ready, 0);
     if (e == cudaSuccess)
       e = hydro::ctu_step_fused(prec, ks, s_in, s_out, sc_cur, sc_next, c->scr, tmax,
-                                c->stage_tma ? &c->stage_map : nullptr, bs, make_int2(yb[b], yb[b + 1] - yb[b]));
+                                c->stage_tma ? &c->stage_map : nullptr, bs, make_int2(yb[b], yb[b + 1] - yb[b]),
+                                ctx_model(c));
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_band[b], bs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->d2h_stream, c->ev_band[b], 0);
     // the band's padded rows in the four planes (the first and last bands also carry the ghost rows below
@@ -826,7 +846,8 @@ static hydro_status step_host(hydro_ctx* c, const void* host_in, void* host_out,
 
 static hydro_status host_step_entry(hydro_ctx* c, const void* host_in, void* host_out, double tmax, int chain) {
   if (!c || !host_in || !host_out || host_in == host_out) return HYDRO_EINVAL;
-  if (c->p.use_learned_guess == 1 || c->harvest || c->p.split) {  // no banded fused launch for these
+  if (check_model(c) != HYDRO_OK) return HYDRO_EINVAL;
+  if (c->harvest || c->p.split) {  // no banded fused launch for these
     c->chain_out = nullptr;
     hydro_status st = hydro_upload(c, host_in);
     if (st == HYDRO_OK) st = hydro_step_fused(c, tmax);

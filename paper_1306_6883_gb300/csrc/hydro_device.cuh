@@ -40,6 +40,7 @@ struct KParams {
   int riemann_solver;  // 0 two-shock iteration, 1 HLLC
   int reconstruction;  // 0 piecewise linear, 1 piecewise parabolic
   int bc_general;      // some side is reflecting or hydrostatic (ghost values are not plain copies)
+  float rec_f;         // FP32: kinetic-energy fraction above which the pressure is recomputed in double
 };
 
 // Time-step dependent factors of one CTU step, computed once in double (host, or the last block of
@@ -92,6 +93,9 @@ enum : unsigned int {
   STATUS_NEGATIVE = 2u,
   STATUS_NONCONV = 4u,
   STATUS_TIMEOUT = 8u,  // a bounded device-side wait ran out (a tile's TMA copy did not land)
+  // the second, equally bounded wait of such a tile ran out too: the copy may still have been in flight when
+  // the block left, and could then have landed in shared memory a later block uses
+  STATUS_TIMEOUT_INFLIGHT = 16u,
 };
 
 template <typename R>
@@ -144,15 +148,16 @@ __device__ __forceinline__ float M<float>::sq(float x) { return x * rsqa(x); }
 template <typename R>
 struct SP {
   R gamma, gm1, igm1, g1, small_dens, small_pres, tol, cvisc, dx, dy, idx, idy;
+  R rec;  // FP32: energy-recovery threshold (kinetic over total energy)
   int maxiter, limiter, flatten;
   __device__ __forceinline__ void load(const KParams& P) {
     if constexpr (is_f32<R>()) {
       gamma = P.gamma_f; gm1 = P.gm1_f; igm1 = P.igm1_f; g1 = P.g1_f; small_dens = P.small_dens_f;
       small_pres = P.small_pres_f; tol = P.tol_f; cvisc = P.cvisc_f; dx = P.dx_f; dy = P.dy_f;
-      idx = P.idx_f; idy = P.idy_f;
+      idx = P.idx_f; idy = P.idy_f; rec = P.rec_f;
     } else {
       gamma = P.gamma; gm1 = P.gm1; igm1 = 0.0; g1 = P.g1; small_dens = P.small_dens; small_pres = P.small_pres;
-      tol = P.riemann_tol; cvisc = P.cvisc; dx = P.dx; dy = P.dy; idx = 0.0; idy = 0.0;
+      tol = P.riemann_tol; cvisc = P.cvisc; dx = P.dx; dy = P.dy; idx = 0.0; idy = 0.0; rec = 0.0;
     }
     maxiter = P.riemann_maxiter;
     limiter = P.limiter;
@@ -236,8 +241,8 @@ __device__ __forceinline__ void cons_to_prim(const SP<R>& s, R U0, R U1, R U2, R
     u = U1 * ir;
     v = U2 * ir;
     const float ke = 0.5f * rho * (u * u + v * v);
-    if (ke > 0.999f * U3) {
-      // kinetic energy within 0.1% of the total: recover e = E - rho |u|^2 / 2 in double
+    if (ke > s.rec * U3) {
+      // kinetic energy within 0.1% (by default) of the total: recover e = E - rho |u|^2 / 2 in double
       const double rd = (double)rho, ud = (double)U1 / rd, vd = (double)U2 / rd;
       const double ked = 0.5 * rd * (ud * ud + vd * vd);
       p = (float)(((double)s.gm1) * ((double)U3 - ked));
@@ -263,6 +268,52 @@ __device__ __forceinline__ void prim_to_cons(const SP<R>& s, R rho, R u, R v, R 
     U3 = p * s.igm1 + 0.5f * rho * (u * u + v * v);
   else
     U3 = p / s.gm1 + 0.5 * rho * (u * u + v * v);
+}
+
+// Pressure of a transversely corrected FP32 face state formed in double (see correct_state): the state's
+// conserved values from its traced primitives (rho, u, v, p), less h times the flux differences dF, all in
+// double, and p = (gamma - 1)(E - |m|^2 / (2 rho)) from them (rho floored as in cons_to_prim).  Not inlined:
+// only high-Mach states call it, and the face loops keep the registers of the plain path.
+static __device__ __noinline__ float corrected_pressure_f64(float gm1, float igm1, float small_dens, float small_pres,
+                                                           float rho, float u, float v, float p, float h, float dF0,
+                                                           float dF1, float dF2, float dF3) {
+  const double rd = (double)rho, ud = (double)u, vd = (double)v, hd = (double)h;
+  const double r2 = rd - hd * (double)dF0;
+  const double mx = rd * ud - hd * (double)dF1, my = rd * vd - hd * (double)dF2;
+  const double E = ((double)p * (double)igm1 + 0.5 * rd * (ud * ud + vd * vd)) - hd * (double)dF3;
+  const double rf = r2 < (double)small_dens ? (double)small_dens : r2;
+  const float pf = (float)((double)gm1 * (E - 0.5 * (mx * mx + my * my) / rf));
+  return pf < small_pres ? small_pres : pf;
+}
+
+// Transverse correction of one traced face state (§3.1 CTU, Eqs. 3-4; §3.2): its primitives (rho, u, v, p)
+// go to conserved variables, lose h times the transverse flux difference dF, and come back to primitives.
+// FP32: where the state's kinetic energy exceeds rec of its total energy, the corrected total energy and
+// the pressure are formed in double from the float primitives and flux difference, so that the float
+// round trip through E does not cancel the pressure away (high Mach).
+template <typename R>
+__device__ __forceinline__ void correct_state(const SP<R>& s, R rho, R u, R v, R p, const R dF[4], R h, R q[4]) {
+  R U[4];
+  if constexpr (is_f32<R>()) {
+    // prim_to_cons, keeping the kinetic energy for the high-Mach test
+    const float ke = 0.5f * rho * (u * u + v * v);
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = rho * v;
+    U[3] = p * s.igm1 + ke;
+    const bool high_mach = ke > s.rec * U[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[k] = U[k] - h * dF[k];
+    cons_to_prim(s, U[0], U[1], U[2], U[3], q[0], q[1], q[2], q[3]);
+    if (high_mach)
+      q[3] = corrected_pressure_f64(s.gm1, s.igm1, s.small_dens, s.small_pres, rho, u, v, p, h, dF[0], dF[1], dF[2],
+                                    dF[3]);
+  } else {
+    prim_to_cons(s, rho, u, v, p, U[0], U[1], U[2], U[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[k] = U[k] - h * dF[k];
+    cons_to_prim(s, U[0], U[1], U[2], U[3], q[0], q[1], q[2], q[3]);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -348,32 +399,52 @@ __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], con
   const R b3 = dq[2];
   const R b4 = roc * dq[1] + ic2h * dq[3];
   const R hs = (R)0.5 * sigma;
+  // eigenvalue gaps lam4 - lam1 = 2c and lam4 - lam2 = c: FP64 forms them as the differences the formula
+  // writes (the rounding the plain C implementation does); FP32 takes c and 2c themselves, since at high
+  // Mach the difference of two nearly equal speeds u + c and u - c loses ~Mach ulps
+  R g41, g42;
+  if constexpr (is_f32<R>()) {
+    g41 = 2.0f * c;
+    g42 = c;
+  } else {
+    g41 = lam4 - lam1;
+    g42 = lam4 - lam2;
+  }
   // left state: reference with lam4, waves moving right add (sigma/2)(lam4 - lam) beta r
   R aL = (R)0.5 * ((R)1 - sigma * lam4);
   R l0 = q[0] + aL * dq[0], l1 = q[1] + aL * dq[1], l2 = q[2] + aL * dq[2], l3 = q[3] + aL * dq[3];
   if (lam1 >= (R)0) {
-    R w = hs * (lam4 - lam1) * b1;
+    R w = hs * g41 * b1;
     l0 += w;
     l1 += w * (-cor);
     l3 += w * c2;
   }
   if (lam2 >= (R)0) {
-    R w2 = hs * (lam4 - lam2) * b2;
+    R w2 = hs * g42 * b2;
     l0 += w2;
-    R w3 = hs * (lam4 - lam2) * b3;
+    R w3 = hs * g42 * b3;
     l2 += w3;
   }
-  // right state: reference with lam1, waves moving left add (sigma/2)(lam1 - lam) beta r
+  // right state: reference with lam1, waves moving left add (sigma/2)(lam1 - lam) beta r, with
+  // lam1 - lam2 = -c and lam1 - lam4 = -2c
+  R g12, g14;
+  if constexpr (is_f32<R>()) {
+    g12 = -c;
+    g14 = -2.0f * c;
+  } else {
+    g12 = lam1 - lam2;
+    g14 = lam1 - lam4;
+  }
   R aR = (R)0.5 * ((R)1 + sigma * lam1);
   R r0 = q[0] - aR * dq[0], r1 = q[1] - aR * dq[1], r2 = q[2] - aR * dq[2], r3 = q[3] - aR * dq[3];
   if (lam2 <= (R)0) {
-    R w2 = hs * (lam1 - lam2) * b2;
+    R w2 = hs * g12 * b2;
     r0 += w2;
-    R w3 = hs * (lam1 - lam2) * b3;
+    R w3 = hs * g12 * b3;
     r2 += w3;
   }
   if (lam4 <= (R)0) {
-    R w = hs * (lam1 - lam4) * b4;
+    R w = hs * g14 * b4;
     r0 += w;
     r1 += w * cor;
     r3 += w * c2;
@@ -466,30 +537,33 @@ __device__ __forceinline__ void trace_ppm(const SP<R>& s, R sigma, const R q[4],
       ref[m] = eR[m] - (R)0.5 * s4 * (da[m] - ((R)1 - two3 * s4) * a6[m]);
       o[m] = ref[m];
     }
-    // ref - Ip(sn); FP32 in the factored form 0.5 (sn - s4)(da - a6 (1 - 2 (sn + s4) / 3))
-    auto dif = [&](int m, R sn) {
+    // ref - Ip(sn); FP32 in the factored form 0.5 (sn - s4)(da - a6 (1 - 2 (sn + s4) / 3)), with
+    // sn - s4 = sigma (lam_nu - lam4) = gap taken as -2 sigma c, -sigma c or 0 (at high Mach the difference of
+    // the two nearly equal products would lose ~Mach ulps)
+    auto dif = [&](int m, R sn, R gap) {
       if constexpr (is_f32<R>())
-        return 0.5f * (sn - s4) * (da[m] - a6[m] * (1.0f - two3 * (sn + s4)));
+        return 0.5f * gap * (da[m] - a6[m] * (1.0f - two3 * (sn + s4)));
       else
         return ref[m] - (eR[m] - (R)0.5 * sn * (da[m] - ((R)1 - two3 * sn) * a6[m]));
     };
+    const R sc = sigma * c;
     if (lam1 >= (R)0) {
       const R sn = sigma * lam1;
-      const R b = -roc * dif(1, sn) + ic2h * dif(3, sn);
+      const R b = -roc * dif(1, sn, -2 * sc) + ic2h * dif(3, sn, -2 * sc);
       o[0] -= b;
       o[1] -= b * (-cor);
       o[3] -= b * c2;
     }
     if (lam2 >= (R)0) {
       const R sn = sigma * lam2;
-      const R b2 = dif(0, sn) + (-ic2) * dif(3, sn);
+      const R b2 = dif(0, sn, -sc) + (-ic2) * dif(3, sn, -sc);
       o[0] -= b2;
-      const R b3 = dif(2, sn);
+      const R b3 = dif(2, sn, -sc);
       o[2] -= b3;
     }
     if (lam4 >= (R)0) {
       const R sn = sigma * lam4;
-      const R b = roc * dif(1, sn) + ic2h * dif(3, sn);
+      const R b = roc * dif(1, sn, (R)0) + ic2h * dif(3, sn, (R)0);
       o[0] -= b;
       o[1] -= b * cor;
       o[3] -= b * c2;
@@ -506,30 +580,32 @@ __device__ __forceinline__ void trace_ppm(const SP<R>& s, R sigma, const R q[4],
       ref[m] = eL[m] + (R)0.5 * s1 * (da[m] + ((R)1 - two3 * s1) * a6[m]);
       o[m] = ref[m];
     }
-    // ref - Im(sn); FP32 in the factored form 0.5 (s1 - sn)(da + a6 (1 - 2 (sn + s1) / 3))
-    auto dif = [&](int m, R sn) {
+    // ref - Im(sn); FP32 in the factored form 0.5 (s1 - sn)(da + a6 (1 - 2 (sn + s1) / 3)), with
+    // s1 - sn = sigma (lam_nu - lam1) = gap taken as 0, sigma c or 2 sigma c
+    auto dif = [&](int m, R sn, R gap) {
       if constexpr (is_f32<R>())
-        return 0.5f * (s1 - sn) * (da[m] + a6[m] * (1.0f - two3 * (sn + s1)));
+        return 0.5f * gap * (da[m] + a6[m] * (1.0f - two3 * (sn + s1)));
       else
         return ref[m] - (eL[m] + (R)0.5 * sn * (da[m] + ((R)1 - two3 * sn) * a6[m]));
     };
+    const R sc = sigma * c;
     if (lam1 <= (R)0) {
       const R sn = -sigma * lam1;
-      const R b = -roc * dif(1, sn) + ic2h * dif(3, sn);
+      const R b = -roc * dif(1, sn, (R)0) + ic2h * dif(3, sn, (R)0);
       o[0] -= b;
       o[1] -= b * (-cor);
       o[3] -= b * c2;
     }
     if (lam2 <= (R)0) {
       const R sn = -sigma * lam2;
-      const R b2 = dif(0, sn) + (-ic2) * dif(3, sn);
+      const R b2 = dif(0, sn, sc) + (-ic2) * dif(3, sn, sc);
       o[0] -= b2;
-      const R b3 = dif(2, sn);
+      const R b3 = dif(2, sn, sc);
       o[2] -= b3;
     }
     if (lam4 <= (R)0) {
       const R sn = -sigma * lam4;
-      const R b = roc * dif(1, sn) + ic2h * dif(3, sn);
+      const R b = roc * dif(1, sn, 2 * sc) + ic2h * dif(3, sn, 2 * sc);
       o[0] -= b;
       o[1] -= b * cor;
       o[3] -= b * c2;
@@ -813,7 +889,7 @@ __device__ __forceinline__ void cfl_value(const SP<R>& s, R U0, R U1, R U2, R U3
     const float e = __fsub_rn(U3, ke);
     if (!(U0 > 0.0f) || !(e > 0.0f)) flags |= STATUS_NEGATIVE;
     float p;
-    if (ke > __fmul_rn(0.999f, U3)) {  // as cons_to_prim: recover e = E - rho |u|^2 / 2 in double
+    if (ke > __fmul_rn(s.rec, U3)) {  // as cons_to_prim: recover e = E - rho |u|^2 / 2 in double
       const double rd = (double)rho, ud = __ddiv_rn((double)U1, rd), vd = __ddiv_rn((double)U2, rd);
       p = (float)__dmul_rn((double)s.gm1,
                            __dsub_rn((double)U3, __dmul_rn(__dmul_rn(0.5, rd), __dadd_rn(__dmul_rn(ud, ud),

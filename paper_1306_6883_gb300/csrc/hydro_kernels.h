@@ -27,10 +27,11 @@ cudaError_t cfl_dt(int precision, const KParams& P, const void* U, DevScratch* s
 // then loaded by one bulk tensor copy.
 // band (optional): tile rows [band.x, band.x + band.y) only (band.y <= 0: the whole step); bands of one
 // step may run concurrently, the last tile of all of them finishes the step.  fused_tile_rows: the step's
-// number of tile rows for the precision.
+// number of tile rows for the precision.  mlp (FP32 piecewise-linear two-shock steps only, may be NULL):
+// start the Riemann iterations from the learned proposal of these weights (FACE_LEARNED).
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
-                           cudaStream_t stream, int2 band = make_int2(0, 0));
+                           cudaStream_t stream, int2 band = make_int2(0, 0), const MlpBlob* mlp = nullptr);
 int fused_tile_rows(int precision, const KParams& P);
 int fused_tile_height(int precision);
 

@@ -22,9 +22,22 @@ const int kNumTileShapes = sizeof(kTileShapes) / sizeof(kTileShapes[0]);
 
 cudaError_t batch_step(int precision, int shape, const BatchMember* mem, const int4* tiles, int ntiles,
                        unsigned int* queue, int parity, DevScratch* agg, cudaStream_t stream, int* grid_out,
-                       const CUtensorMap* tmaps, int advance) {
+                       const CUtensorMap* tmaps, int advance, const MlpBlob* mlp) {
   if (precision == 0)  // the FP64 path keeps one shape (its cost is the FP64 pipe, not the tile)
-    return batch_step_f64(mem, tiles, ntiles, queue, parity, agg, stream, grid_out, advance);
+    return mlp ? cudaErrorInvalidValue : batch_step_f64(mem, tiles, ntiles, queue, parity, agg, stream, grid_out, advance);
+  if (mlp) {
+    switch (shape) {
+      case 0: return BatchStep<float, 32, 16, 384, FACE_LEARNED>::launch(mem, tiles, ntiles, queue, parity, agg,
+                                                                         stream, grid_out, tmaps, advance, mlp);
+      case 1: return BatchStep<float, 16, 16, 256, FACE_LEARNED>::launch(mem, tiles, ntiles, queue, parity, agg,
+                                                                         stream, grid_out, tmaps, advance, mlp);
+      case 2: return BatchStep<float, 32, 8, 256, FACE_LEARNED>::launch(mem, tiles, ntiles, queue, parity, agg,
+                                                                        stream, grid_out, tmaps, advance, mlp);
+      case 3: return BatchStep<float, 32, 16, 256, FACE_LEARNED>::launch(mem, tiles, ntiles, queue, parity, agg,
+                                                                         stream, grid_out, tmaps, advance, mlp);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (shape) {
     case 0: return BatchStep<float, 32, 16, 384>::launch(mem, tiles, ntiles, queue, parity, agg, stream, grid_out,
                                                               tmaps, advance);
@@ -44,6 +57,10 @@ cudaError_t batch_prepare(int precision) {
   if (e == cudaSuccess) e = BatchStep<float, 16, 16, 256>::prepare();
   if (e == cudaSuccess) e = BatchStep<float, 32, 8, 256>::prepare();
   if (e == cudaSuccess) e = BatchStep<float, 32, 16, 256>::prepare();
+  if (e == cudaSuccess) e = BatchStep<float, 32, 16, 384, FACE_LEARNED>::prepare();
+  if (e == cudaSuccess) e = BatchStep<float, 16, 16, 256, FACE_LEARNED>::prepare();
+  if (e == cudaSuccess) e = BatchStep<float, 32, 8, 256, FACE_LEARNED>::prepare();
+  if (e == cudaSuccess) e = BatchStep<float, 32, 16, 256, FACE_LEARNED>::prepare();
   return e;
 }
 

@@ -8,7 +8,15 @@ int f32_tile_y() { return F32_TY; }
 
 cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, void* Uout, const StepScalars* sc_cur,
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
-                           cudaStream_t stream, int2 band) {
+                           cudaStream_t stream, int2 band, const MlpBlob* mlp) {
+  if (mlp != nullptr) {
+    // 256 threads: the warp-collective forward pass and its call site need more than the 56 registers three
+    // CTAs of 384 threads leave (at 384 threads the face loops spill, and a Sedov 8192^2 step takes 6.0 ms
+    // instead of 4.5 ms)
+    if (precision == 0 || P.reconstruction == 1 || P.riemann_solver == 1) return cudaErrorInvalidValue;
+    return launch_ctu_step_fused<float, F32_TX, F32_TY, 256, FACE_LEARNED>(
+        P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax, tmap, stream, band, mlp);
+  }
   if (P.reconstruction == 1)
     return ctu_step_fused_ppm(precision, P, Uin, Uout, sc_cur, sc_next, scr, tmax, tmap, stream, band);
   if (P.riemann_solver == 1)

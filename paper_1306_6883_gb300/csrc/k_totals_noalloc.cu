@@ -24,8 +24,9 @@ constexpr int kScratchDoubles = 4 * kMaxRows + 4 + 4;
 static __device__ __align__(256) double g_totals_scratch[kScratchDoubles];
 
 // One partial per grid row (fixed-shape tree over the row), then the last block to finish adds the row
-// partials in row order: the same per-cell double accumulation as the allocating totals kernel, with
-// deterministic results for a given grid.
+// partials: thread t sums rows t, t + 256, t + 512, ... in order, and a fixed-shape tree over the 256
+// threads combines those sums.  The same per-cell double accumulation as the allocating totals kernel,
+// with results that depend only on the grid (not on which block finishes last).
 template <typename R>
 __global__ void __launch_bounds__(kThreads) totals_rows_kernel(hydro::KParams P, const R* __restrict__ U,
                                                               double* __restrict__ scratch) {
@@ -63,19 +64,34 @@ __global__ void __launch_bounds__(kThreads) totals_rows_kernel(hydro::KParams P,
     last = (atomicAdd(done, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const double area = P.dx * P.dy;
-    for (int k = 0; k < 4; ++k) {
-      double s = 0.0;
-      for (int j = 0; j < P.ny; ++j) s += ((volatile double*)partials)[4 * j + k];
-      totals[k] = s * area;
+  if (!last) return;
+  __threadfence();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < P.ny; j += kThreads) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += ((volatile double*)partials)[4 * j + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
     }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double area = P.dx * P.dy;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) totals[k] = red[k][0] * area;
     *done = 0u;
   }
 }
 
-// Device address of g_totals_scratch per device ordinal, looked up once with that device current.
+// Device address of g_totals_scratch per device ordinal, looked up once with that device current and kept
+// for the life of the process.  A cudaDeviceReset of that device ends the context the address belongs to,
+// so the entry point does not support being called after one.
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {};

@@ -31,7 +31,7 @@ class HydroParams(ctypes.Structure):
         ("small_dens", ctypes.c_double), ("small_pres", ctypes.c_double),
         ("precision", ctypes.c_int), ("use_learned_guess", ctypes.c_int),
         ("grav", ctypes.c_double), ("split", ctypes.c_int), ("riemann_solver", ctypes.c_int),
-        ("reconstruction", ctypes.c_int),
+        ("reconstruction", ctypes.c_int), ("recover_ke_frac", ctypes.c_double),
     ]
 
 
@@ -49,6 +49,7 @@ _PP = ctypes.POINTER(HydroParams)
 # name -> (restype, argtypes); the same names as the C ABI
 SIGNATURES = {
     "hydro_default_params": (ctypes.c_int, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "hydro_params_size": (ctypes.c_size_t, []),
     "hydro_state_pitch": (ctypes.c_size_t, [_PP]),
     "hydro_state_bytes": (ctypes.c_size_t, [_PP]),
     "hydro_init": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
@@ -90,6 +91,7 @@ SIGNATURES = {
     "hydro_batch_create": (ctypes.c_int, [ctypes.c_int, _PP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP,
                                           ctypes.POINTER(_VP)]),
     "hydro_batch_destroy": (None, [_VP]),
+    "hydro_batch_set_riemann_model": (ctypes.c_int, [_VP, _VP]),
     "hydro_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "hydro_batch_num_classes": (ctypes.c_int, [_VP]),
     "hydro_batch_class_info": (ctypes.c_int, [_VP, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 6),
@@ -118,6 +120,9 @@ def load(path=LIB_PATH):
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        if L.hydro_params_size() != ctypes.sizeof(HydroParams):
+            raise ImportError(f"{path}: hydro_params is {L.hydro_params_size()} bytes in the library and "
+                              f"{ctypes.sizeof(HydroParams)} in this binding (stale build)")
         _LIB = L
     return _LIB
 
@@ -272,6 +277,10 @@ def hydro_batch_create(params_list, states, states_alt, stream_ptr):
 
 def hydro_batch_destroy(b):
     load().hydro_batch_destroy(b)
+
+
+def hydro_batch_set_riemann_model(b, m):
+    _bcheck(load().hydro_batch_set_riemann_model(b, m), b, "hydro_batch_set_riemann_model")
 
 
 def hydro_batch_autotune(b, reps=3):

@@ -156,6 +156,11 @@ class Ensemble:
     def autotune(self, reps=3):
         return H.hydro_batch_autotune(self.b, reps)
 
+    def set_model(self, model):
+        """Start every member's Riemann iterations from `model` (a Model; the members need
+        use_learned_guess = 1), or from the acoustic estimate again with None."""
+        H.hydro_batch_set_riemann_model(self.b, model.m if model is not None else None)
+
     def classes(self):
         return H.hydro_batch_classes(self.b)
 

@@ -41,6 +41,9 @@ def test_defaults_and_layout(lib):
     assert H.state_bytes(p) == 4 * pitch * 68 * 8
     p32 = H.default_params(100, 60, H.HYDRO_FP32)
     assert H.state_pitch(p32) * 4 % 128 == 0 and p32.riemann_tol == 1e-6
+    assert p.recover_ke_frac == 0.999 and p32.recover_ke_frac == 0.999
+    # the binding mirrors the library's struct byte for byte
+    assert lib.hydro_params_size() == ctypes.sizeof(H.HydroParams)
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("ng", 3), ("gamma", 1.0), ("cfl", 0.0),
@@ -48,7 +51,8 @@ def test_defaults_and_layout(lib):
                                          ("precision", 2), ("bc_xlo", 1), ("use_learned_guess", 1),
                                          ("bc_xlo", 3), ("bc_xhi", 3), ("bc_yhi", 4), ("bc_ylo", -1),
                                          ("grav", float("nan")), ("grav", float("inf")), ("split", 2),
-                                         ("split", -1)])
+                                         ("split", -1), ("recover_ke_frac", -0.5),
+                                         ("recover_ke_frac", float("nan")), ("recover_ke_frac", float("inf"))])
 def test_invalid_parameters_are_rejected_before_any_allocation(lib, field, value):
     from paper_1306_6883_gb300 import hydro as H
     p = H.default_params(16, 16)

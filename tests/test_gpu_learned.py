@@ -227,3 +227,128 @@ def test_learned_mode_requires_a_model(torch):
         s.step(s.cfl_dt())
     assert e.value.status == H.HYDRO_EINVAL
     s.close()
+
+
+def test_fused_learned_step_equals_the_separate_passes(torch):
+    # hydro_step_fused on a learned context is one launch (boundary map, CTU step started from the network,
+    # CFL dt of the new state); it must give the state of ghost fill + dt + hydro_step to float rounding (two
+    # compilations of the same tile code) and stay within the FP32 bound of the oracle's step
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Model, Solver, params_for
+    m = Model(seed=21)
+    m.train(torch.from_numpy(_random_faces(20000, seed=22)).cuda(), steps=600, batch=1024, lr=2e-3, seed=4)
+    m.set_gate(0.0, 0.0)  # every warp evaluates the network
+    for pr in (hp.quad(96, 80, seed=23), hp.sod(64, 48)):
+        a = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1), pr.U)
+        b = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1), pr.U)
+        H.hydro_set_riemann_model(a.ctx, m.m)
+        H.hydro_set_riemann_model(b.ctx, m.m)
+        for _ in range(4):
+            a.fill_ghost()
+            a.step(a.cfl_dt())
+            b.step_fused()
+        sa, _ = a.status()
+        sb, stats = b.status()
+        assert sa == 0 and sb == 0 and stats[2] == 0
+        A = a.interior().astype(np.float64)
+        B = b.interior().astype(np.float64)
+        scale = np.abs(A).reshape(4, -1).max(axis=1)
+        assert np.all(np.abs(A - B).reshape(4, -1).max(axis=1) <= 1e-4 * scale)
+        a.close()
+        b.close()
+        # one fused learned step against the oracle's step from the same state
+        c = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1), pr.U)
+        H.hydro_set_riemann_model(c.ctx, m.m)
+        Uin = c.state_numpy().astype(np.float64)
+        c.step_fused()
+        t, _ = c.time()
+        got = c.interior().astype(np.float64)
+        c.close()
+        po = oracle.params(pr.nx, pr.ny, bc=pr.bc)
+        oracle.fill_ghost(po, Uin)
+        oracle.step(po, Uin, t)
+        ref = Uin[:, NG:-NG, NG:-NG]
+        scale = np.abs(ref).reshape(4, -1).max(axis=1)
+        assert np.all(np.abs(got - ref).reshape(4, -1).max(axis=1) <= 2e-5 * scale)
+    m.close()
+
+
+def _quads(seed):
+    g = np.random.default_rng(seed)
+    return [hp.quad(nx, ny, rng=g) for nx, ny in ((64, 64), (37, 21), (128, 96), (16, 16), (64, 64))]
+
+
+def test_learned_ensemble_members_evolve_as_alone(torch):
+    # every member of an ensemble started from the network evolves as the same problem run alone with the
+    # same network (the batched persistent kernel and the single-problem fused kernel are two compilations of
+    # the same tile code: equal to float rounding), and stays within the FP32 bound of the oracle after a step
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Ensemble, Model, Solver, params_for
+    m = Model(seed=31)
+    m.train(torch.from_numpy(_random_faces(20000, seed=32)).cuda(), steps=600, batch=1024, lr=2e-3, seed=5)
+    m.set_gate(0.0, 0.0)
+    probs = _quads(33)
+    for tune in (False, True):
+        e = Ensemble([params_for(p, H.HYDRO_FP32, use_learned_guess=1) for p in probs], [p.U for p in probs])
+        e.set_model(m)
+        if tune:
+            e.autotune(reps=1)
+        e.run(5)
+        st, stats = e.status()
+        assert st == 0 and stats[0] > 0 and stats[2] == 0
+        for i, pr in enumerate(probs):
+            s = Solver(params_for(pr, H.HYDRO_FP32, use_learned_guess=1), pr.U)
+            H.hydro_set_riemann_model(s.ctx, m.m)
+            s.advance(5)
+            ref = s.interior().astype(np.float64)
+            t_ref, _ = s.time()
+            s.close()
+            got = e.state_numpy(i)[:, NG:-NG, NG:-NG].astype(np.float64)
+            scale = np.abs(ref).max(axis=(1, 2), keepdims=True)
+            assert np.all(np.abs(got - ref) <= 2.0 ** -24 * 256 * scale), np.abs(got - ref).max()
+            t, n = e.time(i)
+            assert n == 5 and t == pytest.approx(t_ref, rel=2.0 ** -24 * 16)
+        e.close()
+    # one step of each member against the oracle
+    e = Ensemble([params_for(p, H.HYDRO_FP32, use_learned_guess=1) for p in probs], [p.U for p in probs])
+    e.set_model(m)
+    e.run(1)
+    for i, pr in enumerate(probs):
+        t, _ = e.time(i)
+        U = pr.U.astype(np.float32).astype(np.float64)
+        po = oracle.params(pr.nx, pr.ny, bc=pr.bc)
+        oracle.fill_ghost(po, U)
+        oracle.step(po, U, t)
+        got = e.state_numpy(i)[:, NG:-NG, NG:-NG].astype(np.float64)
+        ref = U[:, NG:-NG, NG:-NG]
+        scale = np.abs(ref).reshape(4, -1).max(axis=1)
+        assert np.all(np.abs(got - ref).reshape(4, -1).max(axis=1) <= 2e-5 * scale)
+    e.close()
+    m.close()
+
+
+def test_learned_ensemble_needs_its_model(torch):
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Ensemble, Model, params_for
+    probs = _quads(41)[:2]
+    m = Model(seed=1)
+    # members created without the learned start refuse a model
+    plain = Ensemble([params_for(p, H.HYDRO_FP32) for p in probs], [p.U for p in probs])
+    with pytest.raises(H.HydroError) as ex:
+        plain.set_model(m)
+    assert ex.value.status == H.HYDRO_EINVAL
+    plain.close()
+    # learned members refuse to run without one, and mixed members are rejected at creation
+    e = Ensemble([params_for(p, H.HYDRO_FP32, use_learned_guess=1) for p in probs], [p.U for p in probs])
+    with pytest.raises(H.HydroError):
+        e.run(1)
+    e.set_model(m)
+    e.run(1)
+    e.set_model(None)
+    with pytest.raises(H.HydroError):
+        e.run(1)
+    e.close()
+    with pytest.raises(H.HydroError):
+        Ensemble([params_for(probs[0], H.HYDRO_FP32, use_learned_guess=1), params_for(probs[1], H.HYDRO_FP32)],
+                 [p.U for p in probs])
+    m.close()

@@ -38,7 +38,10 @@ def test_noalloc_totals_match_the_allocating_entry_point_twice(cuda, precision):
     from paper_1306_6883_gb300 import hydro as H
     from paper_1306_6883_gb300.solver import Solver, params_for
 
-    for pr in (hp.kh(300, 200, seed=4), hp.quad(77, 131, seed=2)):
+    # grids with fewer rows than the kernel's 304 blocks (one row per block), more rows (blocks take several
+    # rows in turn), and the row limit itself on a narrow grid
+    for pr in (hp.kh(300, 200, seed=4), hp.quad(77, 131, seed=2), hp.kh(64, 1000, seed=5),
+               hp.quad(8, H.NOALLOC_MAX_ROWS, seed=6)):
         p = params_for(pr, precision)
         s = Solver(p, pr.U)
         s.advance(3)  # a state that is not the initial one
