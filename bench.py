@@ -394,15 +394,42 @@ def time_e2e(pr, precision, steps, warmup, model=None):
         one(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    step_s = []
     for k in range(warmup, warmup + steps):  # the run goes on: each input is the previous step's output
         one(k)
+        step_s.append(time.perf_counter())
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    step_s = [b - a for a, b in zip([t0] + step_s[:-1], step_s)]
+    # what the link alone gives for the same bytes: one whole-state copy up, one down, and both at once
+    nbytes = host[0].numel() * host[0].element_size()
+    dev = torch.empty(host[0].numel(), dtype=dt_, device="cuda")
+    dev2 = torch.empty_like(dev)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - a) / reps * 1e3
+
+    def both():
+        with torch.cuda.stream(s1):
+            dev.copy_(host[0].view(-1), non_blocking=True)
+        with torch.cuda.stream(s2):
+            host[1].view(-1).copy_(dev2, non_blocking=True)
+
+    link = {"h2d_ms": timed(lambda: dev.copy_(host[0].view(-1), non_blocking=True)),
+            "d2h_ms": timed(lambda: host[1].view(-1).copy_(dev2, non_blocking=True)),
+            "both_ms": timed(both), "bytes_each_way": nbytes}
     s.status()
     s.close()
-    nbytes = host[0].numel() * host[0].element_size()
-    del host
-    return {"seconds": el, "steps": steps, "h2d": nbytes, "d2h": nbytes}
+    del host, dev, dev2
+    return {"seconds": el, "steps": steps, "h2d": nbytes, "d2h": nbytes,
+            "ms_per_step_each": [1e3 * x for x in step_s], "link_alone": link}
 
 
 def roofline(precision, zones, kernel_ms, iters_per_solve, kernel, traffic_key=None, peak_kind="burst"):
@@ -739,7 +766,8 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": None,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"], "call": "hydro_step_host_chained (learned context)",
-                "steps": e2e_steps},
+                "steps": e2e_steps, "ms_per_step_each": e2e["ms_per_step_each"],
+                "link_alone": e2e["link_alone"]},
         "gpu_launches": main["launches_per_step"] * args.steps,
         "clocks": clk.summary(),
         "riemann_iters_per_solve": main["iters_per_solve"],

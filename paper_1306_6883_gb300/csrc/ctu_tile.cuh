@@ -86,29 +86,27 @@ __device__ __forceinline__ unsigned int face_key(int bx, int by, int stage, int 
 
 // One Riemann solve of a face (every lane of the warp calls this; `active` lanes have a face).
 //  FACE_PLAIN:   acoustic start.
-//  FACE_LEARNED: start from the network's proposal where the warp's gate opens (warp-collective).
 //  FACE_HARVEST: acoustic start, and a hash-sampled subset of faces records inputs, p* and iterations.
 //  FACE_HLLC:    the HLLC solver instead of the two-shock iteration (no iterations to count).
+// (FACE_LEARNED tiles solve their ungated faces as FACE_PLAIN and their gated ones after the tile's network
+// pass, see ctu_tile.)
 template <typename R, int MODE>
 __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R b[4], bool active,
-                                           const FaceHook& hook, const MlpBlob* wsm, unsigned int key, R F[4],
-                                           TileCounters& cnt) {
+                                           const FaceHook& hook, unsigned int key, R F[4], TileCounters& cnt) {
   constexpr int K = face_kind(MODE);
-  static_assert(K == FACE_PLAIN || K == FACE_HLLC || is_f32<R>(),
-                "the harvest and the learned proposal are FP32 paths");
+  static_assert(K == FACE_PLAIN || K == FACE_HLLC || K == FACE_HARVEST, "face loops solve plain, harvest or HLLC");
+  static_assert(K != FACE_HARVEST || is_f32<R>(), "the harvest is an FP32 path");
   if constexpr (K == FACE_HLLC) {
     if (!active) return;
     hllc(s, a, b, F);
     cnt.solves++;
     return;
   }
-  R guess = (R)0;
-  if constexpr (K == FACE_LEARNED) guess = learned_guess(a, b, active, wsm);
   if (!active) return;
   int it;
   bool ok;
   R pst;
-  riemann(s, a, b, guess, F, it, ok, &pst);
+  riemann(s, a, b, (R)0, F, it, ok, &pst);
   cnt.solves++;
   cnt.iters += it;
   cnt.nonconv += ok ? 0 : 1;
@@ -123,6 +121,14 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
       }
     }
   }
+}
+
+// Gated faces a FACE_LEARNED tile holds per stage: 2 words each (face item, starting pressure).  A shared
+// array of its own (1 KB), present only in the learned kernels.
+constexpr int LEARNED_QUEUE = 128;
+__device__ __forceinline__ float* learned_queue() {
+  __shared__ float q[2 * LEARNED_QUEUE];
+  return q;
 }
 
 // One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
@@ -273,6 +279,8 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     __syncthreads();
   }
 
+  __shared__ int queue_n[2];  // gated faces queued by a FACE_LEARNED tile in stages 3 and 4
+  if (face_kind(MODE) == FACE_LEARNED && tid == 0) queue_n[0] = queue_n[1] = 0;
   const R* qu = sq + QP * QY;
   const R* qv = sq + 2 * QP * QY;
   const R* qp = sq + 3 * QP * QY;
@@ -360,51 +368,127 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   }
   __syncthreads();
 
+  // FACE_LEARNED: faces past the network's gate are not solved in the face loops.  Each is queued in a small
+  // shared array of its own (face item and, later, starting pressure; LEARNED_QUEUE entries), the other faces
+  // are solved at once from the acoustic start, and after a barrier the network proposes the starting
+  // pressures of the queued faces, 32 per warp, which are then solved from them.  The face loops thus carry
+  // no call and keep the registers of the plain kernel, and a warp evaluates the network on 32 gated faces
+  // rather than on the 31 others of a warp that holds one.  The queued faces' states are rebuilt from the
+  // traced states, which stay in place until each face's own flux replaces them.  A full queue leaves
+  // further gated faces to the acoustic start.
+  constexpr bool LEARNED = face_kind(MODE) == FACE_LEARNED;
+  float* queue = nullptr;
+  float gate_ratio = 0.f, gate_u4 = 0.f;
+  if constexpr (LEARNED) {
+    queue = learned_queue();
+    gate_ratio = wsm->gate_ratio;
+    gate_u4 = wsm->gate_u4;
+  }
+  // queue the face of item e of stage st (0: 3, 1: 4) if it is past the gate; false if it is solved in the loop
+  auto defer = [&](int st, int e, const R a[4], const R b[4]) -> bool {
+    if constexpr (LEARNED) {
+      if (!strong_face(a, b, gate_ratio, gate_u4)) return false;
+      const int k = atomicAdd(&queue_n[st], 1);
+      if (k >= LEARNED_QUEUE) return false;
+      queue[2 * k] = __int_as_float(e);
+      return true;
+    } else {
+      return false;
+    }
+  };
+  // the network's starting pressures for the queued faces, then their solves (block-wide; the queue was
+  // filled before a barrier); states(e, isx, a, b) rebuilds an item's face states, finish(e, isx, F) stores
+  // its flux
+  auto learned_pass = [&](int st, int nXIa, auto&& states, auto&& finish) {
+    if constexpr (LEARNED) {
+      const int n = queue_n[st] < LEARNED_QUEUE ? queue_n[st] : LEARNED_QUEUE;
+      if (n == 0) return;  // block-uniform
+      for (int b0 = tid - (tid & 31); b0 < n; b0 += NT) {  // warp-uniform: the forward pass is warp-collective
+        const int k = b0 + (tid & 31);
+        float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float pref = 0.f;
+        if (k < n) {
+          const int e = __float_as_int(queue[2 * k]);
+          R a[4], b[4];
+          states(e, e < nXIa, a, b);
+          pref = mlp_features(a[0], a[1], a[3], b[0], b[1], b[3], x);
+        }
+        float y = mlp_warp_forward(x, wsm);
+        y = fminf(fmaxf(y, -40.f), 40.f);
+        if (k < n) queue[2 * k + 1] = pref * __expf(y);
+      }
+      __syncthreads();
+      for (int k = tid; k < n; k += NT) {
+        const int e = __float_as_int(queue[2 * k]);
+        const bool isx = e < nXIa;
+        R a[4], b[4], F[4];
+        states(e, isx, a, b);
+        int it;
+        bool ok;
+        riemann(s, a, b, queue[2 * k + 1], F, it, ok);
+        cnt.solves++;
+        cnt.iters += it;
+        cnt.nonconv += ok ? 0 : 1;
+        finish(e, isx, F);
+      }
+    }
+  };
+  constexpr int FACE_LOOP_MODE = LEARNED ? (MODE & ~3) | FACE_PLAIN : MODE;
+
   // ---- 3. hat Riemann solves.  x faces: lx in [4, TX+5) between cells lx-1 and lx, rows [3, TY+5).
   //         y faces: ly in [4, TY+5), columns [3, TX+5).  Results overwrite region A.
   {
     // x-face items run over rows of SX (the last item of each row idle) so a warp's shared-memory reads
     // stay on consecutive addresses of the SX-wide arrays; y-face items start at a warp boundary
     constexpr int nXI = SX * SY, nXIa = (nXI + 31) / 32 * 32, nYF = (TY + 1) * SX;
-    // warp-uniform trip count: every lane of a warp runs the same iterations (the learned proposal is a
-    // warp-collective tensor-core computation); lanes without a face only take part in it
+    auto states = [&](int e, bool isx, R a[4], R bq[4]) {
+      if (isx) {
+        // face fx = e % SX (0..TX) <-> lx = fx + 4 in row ly = e / SX + 3; cell lx-1 has s index e
+        const int cL = e;
+        const int cR = cL + 1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          a[m] = sxl[m * nC + cL];
+          bq[m] = sxr[m * nC + cR];
+        }
+      } else {
+        const int f = e - nXIa;                // = fy * SX + column s index; face 0..TY <-> ly = fy + 4
+        const int cL = f;                      // cell ly-1 = fy + 3
+        const int cR = cL + SX;
+        a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
+        bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
+      }
+    };
+    auto finish = [&](int e, bool isx, const R F[4]) {
+      if (isx) {
+        const int fx = e % SX, ry = e / SX;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
+      } else {
+        const int o = e - nXIa;
+        sfyh[0 * (TY + 1) * SX + o] = F[0];
+        sfyh[1 * (TY + 1) * SX + o] = F[2];
+        sfyh[2 * (TY + 1) * SX + o] = F[1];
+        sfyh[3 * (TY + 1) * SX + o] = F[3];
+      }
+    };
+    // warp-uniform trip count: every lane of a warp runs the same iterations (the harvest's gated faces and
+    // the solver's fan test are warp-collective); lanes without a face only take part in them
     for (int e0 = tid - (tid & 31); e0 < nXIa + nYF; e0 += NT) {
       const int e = e0 + (tid & 31);
       const bool isx = e < nXIa;
-      const bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF);
+      bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF);
       R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4];
       if (active) {
-        if (isx) {
-          // face fx = e % SX (0..TX) <-> lx = fx + 4 in row ly = e / SX + 3; cell lx-1 has s index e
-          const int cL = e;
-          const int cR = cL + 1;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            a[m] = sxl[m * nC + cL];
-            bq[m] = sxr[m * nC + cR];
-          }
-        } else {
-          const int f = e - nXIa;                // = fy * SX + column s index; face 0..TY <-> ly = fy + 4
-          const int cL = f;                      // cell ly-1 = fy + 3
-          const int cR = cL + SX;
-          a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
-          bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
-        }
+        states(e, isx, a, bq);
+        if (defer(0, e, a, bq)) active = false;
       }
-      face_solve<R, MODE>(s, a, bq, active, hook, wsm, face_key(bx, by, 0, e), F, cnt);
-      if (active) {
-        if (isx) {
-          const int fx = e % SX, ry = e / SX;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
-        } else {
-          const int o = e - nXIa;
-          sfyh[0 * (TY + 1) * SX + o] = F[0];
-          sfyh[1 * (TY + 1) * SX + o] = F[2];
-          sfyh[2 * (TY + 1) * SX + o] = F[1];
-          sfyh[3 * (TY + 1) * SX + o] = F[3];
-        }
-      }
+      face_solve<R, FACE_LOOP_MODE>(s, a, bq, active, hook, face_key(bx, by, 0, e), F, cnt);
+      if (active) finish(e, isx, F);
+    }
+    if constexpr (LEARNED) {
+      __syncthreads();
+      learned_pass(0, nXIa, states, finish);
     }
   }
   __syncthreads();
@@ -413,51 +497,46 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   {
     // as in stage 3: x-face items over rows of SX, y-face items from a warp boundary, over rows of RW
     constexpr int nXI = SX * TY, nXIa = (nXI + 31) / 32 * 32, nYF = (TY + 1) * RW;
-    for (int e0 = tid - (tid & 31); e0 < nXIa + nYF; e0 += NT) {
-      const int e = e0 + (tid & 31);
-      const bool isx = e < nXIa;
-      const bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF && (e - nXIa) % RW < TX);
-      R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4];
-      if (active) {
-        if (isx) {
-          const int fx = e % SX, ty = e / SX;  // face lx = fx + 4, row ly = ty + 4
-          const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
-          // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
-          const int fL = ty * SX + fx, fR = fL + 1;
-          R dL[4], dR[4];
+    auto states = [&](int e, bool isx, R a[4], R bq[4]) {
+      if (isx) {
+        const int fx = e % SX, ty = e / SX;  // face lx = fx + 4, row ly = ty + 4
+        const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
+        // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
+        const int fL = ty * SX + fx, fR = fL + 1;
+        R dL[4], dR[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const R* fy = sfyh + k * (TY + 1) * SX;
-            dL[k] = fy[fL + SX] - fy[fL];
-            dR[k] = fy[fR + SX] - fy[fR];
-          }
-          correct_state(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], dL, hy, a);
-          correct_state(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], dR, hy, bq);
-        } else {
-          const int f = e - nXIa;
-          const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
-          const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
-          // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
-          const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
-          R dL[4], dR[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const R* fxh = sfxh + k * SY * (TX + 1);
-            dL[k] = fxh[fL + 1] - fxh[fL];
-            dR[k] = fxh[fR + 1] - fxh[fR];
-          }
-          R ql[4], qrr[4];
-          correct_state(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], dL, hx, ql);
-          correct_state(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], dR, hx, qrr);
-          a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
-          bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
+        for (int k = 0; k < 4; ++k) {
+          const R* fy = sfyh + k * (TY + 1) * SX;
+          dL[k] = fy[fL + SX] - fy[fL];
+          dR[k] = fy[fR + SX] - fy[fR];
         }
+        correct_state(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], dL, hy, a);
+        correct_state(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], dR, hy, bq);
+      } else {
+        const int f = e - nXIa;
+        const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
+        const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
+        // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
+        const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
+        R dL[4], dR[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R* fxh = sfxh + k * SY * (TX + 1);
+          dL[k] = fxh[fL + 1] - fxh[fL];
+          dR[k] = fxh[fR + 1] - fxh[fR];
+        }
+        R ql[4], qrr[4];
+        correct_state(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], dL, hx, ql);
+        correct_state(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], dR, hx, qrr);
+        a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
+        bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
       }
-      face_solve<R, MODE>(s, a, bq, active, hook, wsm, face_key(bx, by, 1, e), F, cnt);
-      if (!active) continue;
+    };
+    auto finish = [&](int e, bool isx, const R F[4]) {
       if (isx) {
         const int fx = e % SX, ty = e / SX;
         const int cL = (ty + 1) * SX + fx, cR = cL + 1;
+        R G[4] = {F[0], F[1], F[2], F[3]};
         // artificial viscosity from the cell-centred velocities of the time-n state
         if (s.cvisc > (R)0) {
           R div;
@@ -469,18 +548,18 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
           const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
           if constexpr (L::SMEM_U) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
+            for (int k = 0; k < 4; ++k) G[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
           } else {
             const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
             R uL[4], uR[4];
             tile_cell<FUSED>(P, Uin, gi - 1, gj, plane, uL);
             tile_cell<FUSED>(P, Uin, gi, gj, plane, uR);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += av * (uL[k] - uR[k]);
+            for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
           }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = F[k];  // only this face read sxl[cL]
+        for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = G[k];  // only this face read sxl[cL]
       } else {
         const int f = e - nXIa;
         const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
@@ -509,6 +588,22 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
 #pragma unroll
         for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
       }
+    };
+    for (int e0 = tid - (tid & 31); e0 < nXIa + nYF; e0 += NT) {
+      const int e = e0 + (tid & 31);
+      const bool isx = e < nXIa;
+      bool active = isx ? (e < nXI && e % SX <= TX) : (e - nXIa < nYF && (e - nXIa) % RW < TX);
+      R a[4] = {(R)1, (R)0, (R)0, (R)1}, bq[4] = {(R)1, (R)0, (R)0, (R)1}, F[4];
+      if (active) {
+        states(e, isx, a, bq);
+        if (defer(1, e, a, bq)) active = false;
+      }
+      face_solve<R, FACE_LOOP_MODE>(s, a, bq, active, hook, face_key(bx, by, 1, e), F, cnt);
+      if (active) finish(e, isx, F);
+    }
+    if constexpr (LEARNED) {
+      __syncthreads();
+      learned_pass(1, nXIa, states, finish);
     }
   }
   __syncthreads();

@@ -10,11 +10,8 @@ cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, voi
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
                            cudaStream_t stream, int2 band, const MlpBlob* mlp) {
   if (mlp != nullptr) {
-    // 256 threads: the warp-collective forward pass and its call site need more than the 56 registers three
-    // CTAs of 384 threads leave (at 384 threads the face loops spill, and a Sedov 8192^2 step takes 6.0 ms
-    // instead of 4.5 ms)
     if (precision == 0 || P.reconstruction == 1 || P.riemann_solver == 1) return cudaErrorInvalidValue;
-    return launch_ctu_step_fused<float, F32_TX, F32_TY, 256, FACE_LEARNED>(
+    return launch_ctu_step_fused<float, F32_TX, F32_TY, F32_NT, FACE_LEARNED>(
         P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax, tmap, stream, band, mlp);
   }
   if (P.reconstruction == 1)
@@ -48,9 +45,8 @@ cudaError_t ctu_step(int precision, const KParams& P, const void* Uin, void* Uou
       return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_HARVEST>(P, in, out, sc_host, sc_dev, scr, h, tmap,
                                                                            stream);
     case FACE_LEARNED:
-      // 256 threads: the network's warp-collective forward pass needs more than 56 registers
-      return launch_ctu_step<float, F32_TX, F32_TY, 256, FACE_LEARNED>(P, in, out, sc_host, sc_dev, scr, h, tmap,
-                                                                        stream);
+      return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_LEARNED>(P, in, out, sc_host, sc_dev, scr, h, tmap,
+                                                                           stream);
     default:
       return launch_ctu_step<float, F32_TX, F32_TY, F32_NT, FACE_PLAIN>(P, in, out, sc_host, sc_dev, scr, h, tmap, stream);
   }

@@ -7,7 +7,7 @@
 //   y = ln(p*/p_ref), proposal p0 = p_ref exp(y).
 // Master weights are FP32 (layout W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3); inference uses BF16
 // weights and activations with FP32 accumulation on the tensor cores (mma.sync m16n8k16), 32 faces per
-// warp, inside the CTU face loops.
+// warp, in a pass of each CTU tile over its gated faces.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,9 +25,9 @@ struct MlpBlob {
   uint32_t w2f[4][8][32][2];  // layer 2 B fragments per (k tile, n tile, lane)
   float b1[64], b2[64], w3[64];
   float b3;
-  // gate: a warp runs the network if any face has max(pL,pR) >= gate_ratio min(pL,pR) or
+  // gate: a face starts from the network's proposal if max(pL,pR) >= gate_ratio min(pL,pR) or
   // (uL-uR)^4 rho_L rho_R >= gate_u4 p_L p_R, i.e. |ln(pL/pR)|/2 >= gate_dp or |uL-uR|/c_ref >= gate_du with
-  // gate_ratio = exp(2 gate_dp), gate_u4 = gate_du^4; otherwise its faces start from the acoustic guess
+  // gate_ratio = exp(2 gate_dp), gate_u4 = gate_du^4; otherwise from the acoustic guess
   float gate_ratio, gate_u4;
   float pad_[1];
 };
@@ -91,8 +91,8 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
 }
 
 // Network output y for the face of every lane of the warp (all 32 lanes must call it).  Not inlined: the
-// CTU face loops call it rarely (gated), and keeping its unrolled tensor-core code and registers out of
-// those loops leaves their register allocation and instruction footprint as in the plain kernel.
+// CTU tiles call it only in their pass over the gated faces, after the face loops, and keeping its unrolled
+// tensor-core code and registers apart leaves the loops' register allocation as in the plain kernel.
 static __device__ __noinline__ float mlp_warp_forward(const float x[6], const MlpBlob* __restrict__ w) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float yv[2][2];  // [m tile][row half] partial outputs of rows 16 mt + g + 8 half
@@ -161,19 +161,6 @@ static __device__ __noinline__ float mlp_warp_forward(const float x[6], const Ml
 __device__ __forceinline__ bool strong_face(const float a[4], const float b[4], float ratio, float u4) {
   const float du = a[1] - b[1], du2 = du * du;
   return fmaxf(a[3], b[3]) >= ratio * fminf(a[3], b[3]) || du2 * du2 * (a[0] * b[0]) >= u4 * (a[3] * b[3]);
-}
-
-// Starting pressure proposed for the face of every lane (0 = use the acoustic guess); warp-collective.
-__device__ __forceinline__ float learned_guess(const float a[4], const float b[4], bool active,
-                                               const MlpBlob* __restrict__ w) {
-  const bool strong = active && strong_face(a, b, w->gate_ratio, w->gate_u4);
-  if (!__any_sync(0xffffffffu, strong)) return 0.f;
-  float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float pref = 0.f;
-  if (active) pref = mlp_features(a[0], a[1], a[3], b[0], b[1], b[3], x);
-  float y = mlp_warp_forward(x, w);
-  y = fminf(fmaxf(y, -40.f), 40.f);
-  return (active && strong) ? pref * __expf(y) : 0.f;
 }
 
 }  // namespace hydro
