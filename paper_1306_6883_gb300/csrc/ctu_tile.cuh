@@ -24,6 +24,29 @@
 
 namespace hydro {
 
+// Storage of a family of 4-component values per cell or face (traced states, fluxes, U^n copies) in shared
+// memory.  FP32 keeps a cell's four components together, so that one 16-byte access moves them (the face
+// loops then issue one load or store per state instead of four); FP64 keeps four planes of n values.
+template <typename R, int n>
+struct Quad {
+  static __device__ __forceinline__ void ld(const R* base, int c, R v[4]) {
+    if constexpr (is_f32<R>()) {
+      const float4 t = reinterpret_cast<const float4*>(base)[c];
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = base[k * n + c];
+    }
+  }
+  static __device__ __forceinline__ void st(R* base, int c, R v0, R v1, R v2, R v3) {
+    if constexpr (is_f32<R>()) {
+      reinterpret_cast<float4*>(base)[c] = make_float4(v0, v1, v2, v3);
+    } else {
+      base[c] = v0; base[n + c] = v1; base[2 * n + c] = v2; base[3 * n + c] = v3;
+    }
+  }
+};
+
 template <typename R, int TX, int TY>
 struct TileLayout {
   static constexpr int QX = TX + 8, QY = TY + 8;  // primitive tile with a 4-cell halo
@@ -41,6 +64,8 @@ struct TileLayout {
   static constexpr int nU = SMEM_U ? 4 * nC : 0;
   static constexpr int elems = nA + 4 * nS + 2 * nC + nU;
   static constexpr size_t bytes = sizeof(R) * (size_t)elems;
+  // FP32 quads (Quad) are 16-byte accesses: every array of them starts on a 16-byte boundary
+  static_assert(sizeof(R) != 4 || (nA % 4 == 0 && nC % 4 == 0 && nFXH % 4 == 0), "quad arrays must stay aligned");
 };
 
 // The four conserved values of padded cell (gi, gj) as the step sees them: through the boundary map for the
@@ -222,10 +247,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       cons_to_prim(s, U0, U1, U2, U3, rho, u, v, p);
       if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
         const int c = (ly - 3) * SX + (lx - 3);
-        sU[c] = U0;
-        sU[nC + c] = U1;
-        sU[2 * nC + c] = U2;
-        sU[3 * nC + c] = U3;
+        Quad<R, nC>::st(sU, c, U0, U1, U2, U3);
       }
       sq[d] = rho;
       sq[QP * QY + d] = u;
@@ -265,8 +287,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         if constexpr (L::SMEM_U) {
           if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
             const int c = (ly - 3) * SX + (lx - 3);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) sU[k * nC + c] = Ul[it][k];
+            Quad<R, nC>::st(sU, c, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3]);
           }
         }
         const int d = ly * QP + lx;
@@ -348,13 +369,13 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         ql[mg] = ql[mg] + f.hdtg;
         qrr[mg] = qrr[mg] + f.hdtg;
       }
-      R* dl = YD ? syl : sxl;
-      R* dr = YD ? syr : sxr;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {  // stored in (rho, u, v, p) order
-        const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
-        dl[k * nC + c] = ql[m];
-        dr[k * nC + c] = qrr[m];
+      // stored in (rho, u, v, p) order
+      if constexpr (YD) {
+        Quad<R, nC>::st(syl, c, ql[0], ql[2], ql[1], ql[3]);
+        Quad<R, nC>::st(syr, c, qrr[0], qrr[2], qrr[1], qrr[3]);
+      } else {
+        Quad<R, nC>::st(sxl, c, ql[0], ql[1], ql[2], ql[3]);
+        Quad<R, nC>::st(sxr, c, qrr[0], qrr[1], qrr[2], qrr[3]);
       }
     };
     constexpr int nCa = (nC + 31) / 32 * 32;
@@ -446,30 +467,25 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         // face fx = e % SX (0..TX) <-> lx = fx + 4 in row ly = e / SX + 3; cell lx-1 has s index e
         const int cL = e;
         const int cR = cL + 1;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          a[m] = sxl[m * nC + cL];
-          bq[m] = sxr[m * nC + cR];
-        }
+        Quad<R, nC>::ld(sxl, cL, a);
+        Quad<R, nC>::ld(sxr, cR, bq);
       } else {
         const int f = e - nXIa;                // = fy * SX + column s index; face 0..TY <-> ly = fy + 4
         const int cL = f;                      // cell ly-1 = fy + 3
         const int cR = cL + SX;
-        a[0] = syl[cL]; a[1] = syl[2 * nC + cL]; a[2] = syl[nC + cL]; a[3] = syl[3 * nC + cL];
-        bq[0] = syr[cR]; bq[1] = syr[2 * nC + cR]; bq[2] = syr[nC + cR]; bq[3] = syr[3 * nC + cR];
+        R l[4], r[4];
+        Quad<R, nC>::ld(syl, cL, l);
+        Quad<R, nC>::ld(syr, cR, r);
+        a[0] = l[0]; a[1] = l[2]; a[2] = l[1]; a[3] = l[3];
+        bq[0] = r[0]; bq[1] = r[2]; bq[2] = r[1]; bq[3] = r[3];
       }
     };
     auto finish = [&](int e, bool isx, const R F[4]) {
       if (isx) {
         const int fx = e % SX, ry = e / SX;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) sfxh[(m * SY + ry) * (TX + 1) + fx] = F[m];
+        Quad<R, SY * (TX + 1)>::st(sfxh, ry * (TX + 1) + fx, F[0], F[1], F[2], F[3]);
       } else {
-        const int o = e - nXIa;
-        sfyh[0 * (TY + 1) * SX + o] = F[0];
-        sfyh[1 * (TY + 1) * SX + o] = F[2];
-        sfyh[2 * (TY + 1) * SX + o] = F[1];
-        sfyh[3 * (TY + 1) * SX + o] = F[3];
+        Quad<R, (TY + 1) * SX>::st(sfyh, e - nXIa, F[0], F[2], F[1], F[3]);
       }
     };
     // warp-uniform trip count: every lane of a warp runs the same iterations (the harvest's gated faces and
@@ -503,31 +519,41 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         const int cL = (ty + 1) * SX + fx, cR = cL + 1;  // s indices of cells lx-1 and lx
         // hat y fluxes of columns lx-1 and lx at faces ly (j-1/2) and ly+1 (j+1/2): index fy = ly - 4
         const int fL = ty * SX + fx, fR = fL + 1;
-        R dL[4], dR[4];
+        using FY = Quad<R, (TY + 1) * SX>;
+        R dL[4], dR[4], t0[4], t1[4], l[4], r[4];
+        FY::ld(sfyh, fL + SX, t1);
+        FY::ld(sfyh, fL, t0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const R* fy = sfyh + k * (TY + 1) * SX;
-          dL[k] = fy[fL + SX] - fy[fL];
-          dR[k] = fy[fR + SX] - fy[fR];
-        }
-        correct_state(s, sxl[cL], sxl[nC + cL], sxl[2 * nC + cL], sxl[3 * nC + cL], dL, hy, a);
-        correct_state(s, sxr[cR], sxr[nC + cR], sxr[2 * nC + cR], sxr[3 * nC + cR], dR, hy, bq);
+        for (int k = 0; k < 4; ++k) dL[k] = t1[k] - t0[k];
+        FY::ld(sfyh, fR + SX, t1);
+        FY::ld(sfyh, fR, t0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dR[k] = t1[k] - t0[k];
+        Quad<R, nC>::ld(sxl, cL, l);
+        Quad<R, nC>::ld(sxr, cR, r);
+        correct_state(s, l[0], l[1], l[2], l[3], dL, hy, a);
+        correct_state(s, r[0], r[1], r[2], r[3], dR, hy, bq);
       } else {
         const int f = e - nXIa;
         const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
         const int cL = fy * SX + tx + 1, cR = cL + SX;  // cells ly-1 and ly of column lx
         // hat x fluxes of rows ly-1 and ly at faces lx (i-1/2) and lx+1 (i+1/2): row index ry = ly - 3
         const int fL = fy * (TX + 1) + tx, fR = fL + (TX + 1);
-        R dL[4], dR[4];
+        using FX = Quad<R, SY * (TX + 1)>;
+        R dL[4], dR[4], t0[4], t1[4], l[4], r[4];
+        FX::ld(sfxh, fL + 1, t1);
+        FX::ld(sfxh, fL, t0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const R* fxh = sfxh + k * SY * (TX + 1);
-          dL[k] = fxh[fL + 1] - fxh[fL];
-          dR[k] = fxh[fR + 1] - fxh[fR];
-        }
+        for (int k = 0; k < 4; ++k) dL[k] = t1[k] - t0[k];
+        FX::ld(sfxh, fR + 1, t1);
+        FX::ld(sfxh, fR, t0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dR[k] = t1[k] - t0[k];
         R ql[4], qrr[4];
-        correct_state(s, syl[cL], syl[nC + cL], syl[2 * nC + cL], syl[3 * nC + cL], dL, hx, ql);
-        correct_state(s, syr[cR], syr[nC + cR], syr[2 * nC + cR], syr[3 * nC + cR], dR, hx, qrr);
+        Quad<R, nC>::ld(syl, cL, l);
+        Quad<R, nC>::ld(syr, cR, r);
+        correct_state(s, l[0], l[1], l[2], l[3], dL, hx, ql);
+        correct_state(s, r[0], r[1], r[2], r[3], dR, hx, qrr);
         a[0] = ql[0]; a[1] = ql[2]; a[2] = ql[1]; a[3] = ql[3];
         bq[0] = qrr[0]; bq[1] = qrr[2]; bq[2] = qrr[1]; bq[3] = qrr[3];
       }
@@ -547,8 +573,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             div = (su[cR] - su[cL]) / s.dx + dvy / (4.0 * s.dy);
           const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
           if constexpr (L::SMEM_U) {
+            R uL[4], uR[4];
+            Quad<R, nC>::ld(sU, cL, uL);
+            Quad<R, nC>::ld(sU, cR, uR);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) G[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
+            for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
           } else {
             const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
             R uL[4], uR[4];
@@ -558,8 +587,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
           }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sxl[k * nC + cL] = G[k];  // only this face read sxl[cL]
+        Quad<R, nC>::st(sxl, cL, G[0], G[1], G[2], G[3]);  // only this face read sxl[cL]
       } else {
         const int f = e - nXIa;
         const int tx = f % RW, fy = f / RW;  // column lx = tx + 4, face ly = fy + 4
@@ -574,8 +602,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             div = (sv[cR] - sv[cL]) / s.dy + dux / (4.0 * s.dx);
           const R av = s.cvisc * M<R>::mx(-div * s.dy, (R)0);
           if constexpr (L::SMEM_U) {
+            R uL[4], uR[4];
+            Quad<R, nC>::ld(sU, cL, uL);
+            Quad<R, nC>::ld(sU, cR, uR);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) G[k] += av * (sU[k * nC + cL] - sU[k * nC + cR]);
+            for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
           } else {
             const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
             R uL[4], uR[4];
@@ -585,8 +616,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
           }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) syl[k * nC + cL] = G[k];  // only this face read syl[cL]
+        Quad<R, nC>::st(syl, cL, G[0], G[1], G[2], G[3]);  // only this face read syl[cL]
       }
     };
     for (int e0 = tid - (tid & 31); e0 < nXIa + nYF; e0 += NT) {
@@ -617,17 +647,21 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
     const size_t o = (size_t)gj * P.pitch + gi;
     const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
     const int cy = ty * SX + tx + 1;    // final y flux of face ty (below the cell) lives in syl[cy]
-    R Un[4], rho_n, my_n;
+    R Un[4], rho_n, my_n, fx0[4], fx1[4], fy0[4], fy1[4], un[4];
+    Quad<R, nC>::ld(sxl, cx, fx0);
+    Quad<R, nC>::ld(sxl, cx + 1, fx1);
+    Quad<R, nC>::ld(syl, cy, fy0);
+    Quad<R, nC>::ld(syl, cy + SX, fy1);
+    if constexpr (L::SMEM_U) {
+      Quad<R, nC>::ld(sU, cy + SX, un);  // the cell's own U^n, s index (ty + 1) * SX + tx + 1
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) un[k] = __ldg(Uin + o + k * plane);
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const R* fx = sxl + k * nC;
-      const R* fy = syl + k * nC;
-      const R d = ux * (fx[cx] - fx[cx + 1]) + uy * (fy[cy] - fy[cy + SX]);
-      R u0;
-      if constexpr (L::SMEM_U)
-        u0 = sU[k * nC + cy + SX];  // the cell's own U^n, s index (ty + 1) * SX + tx + 1
-      else
-        u0 = __ldg(Uin + o + k * plane);
+      const R d = ux * (fx0[k] - fx1[k]) + uy * (fy0[k] - fy1[k]);
+      const R u0 = un[k];
       if (k == 0) rho_n = u0;
       if (k == 2) my_n = u0;
       Un[k] = u0 + d;
