@@ -719,7 +719,7 @@ def run_ours(args, world, rank, local):
 
     kern_ms = sum(main["step_ms"]) / len(main["step_ms"])
     rl = roofline("fp32", zones, kern_ms, main["iters_per_solve"],
-                  "ctu_step_fused_kernel<float, 32, 16, 384, FACE_LEARNED>",
+                  "ctu_step_fused_kernel<float, 32, 16, 320, FACE_LEARNED>",
                   "sedov8192_learned" if wname.startswith("sedov_8192") else None)
     rl_plain = roofline("fp32", zones, sum(plain["step_ms"]) / len(plain["step_ms"]), plain["iters_per_solve"],
                         "ctu_step_fused_kernel<float, 32, 16, 384, FACE_PLAIN>")
