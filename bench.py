@@ -633,11 +633,30 @@ def kh_fp32_error(steps=50):
     return out
 
 
+def _advance_to(s, tmax):
+    """Steps of a solver until its device time reaches tmax (the last step's dt is clamped to land on it);
+    returns the number of steps taken.  Chunks of 10 steps, then single steps near tmax, so that no step of
+    zero length is taken after it."""
+    t, n = s.time()
+    t_prev, n_prev = t, n
+    while t < tmax * (1 - 1e-12):
+        per = (t - t_prev) / max(n - n_prev, 1)
+        chunk = 1 if n == n_prev or tmax - t < 20 * per else 10
+        t_prev, n_prev = t, n
+        s.advance(chunk, tmax)
+        t, n = s.time()
+        if not t > t_prev:
+            raise RuntimeError(f"the device time does not advance (t = {t} after {n} steps)")
+    return n
+
+
 def sedov4096_error(steps=100, tmax=0.0):
     """Sedov 4096^2 (the blast without noise): FP32 against FP64 after `steps` fused steps from the initial
-    state (tmax > 0: steps until that time instead)."""
+    state (tmax > 0: steps until that time instead).  With tmax, also the grid's own error scale: the FP64
+    4096^2 state averaged over 2 x 2 blocks against the FP64 2048^2 run to the same time."""
     from paper_1306_6883_gb300 import hydro as H
     from paper_1306_6883_gb300.solver import Solver, params_for
+    import hydro_problems as hp
     pr, wname = workload("sedov4096")
     res = {}
     for prec in (H.HYDRO_FP32, H.HYDRO_FP64):
@@ -645,11 +664,7 @@ def sedov4096_error(steps=100, tmax=0.0):
         tot0 = np.array(s.totals())
         t0 = time.perf_counter()
         if tmax > 0:
-            while True:
-                s.advance(500, tmax)
-                t, n = s.time()
-                if t >= tmax * (1 - 1e-12):
-                    break
+            _advance_to(s, tmax)
         else:
             s.advance(steps)
         t, n = s.time()
@@ -662,6 +677,25 @@ def sedov4096_error(steps=100, tmax=0.0):
     out = state_error(a[0], b[0], a[1], a[2], b[1])
     out.update({"workload": wname, "t_fp32": a[3], "t_fp64": b[3], "steps_fp32": a[4], "steps_fp64": b[4],
                 "seconds_fp32": a[5], "seconds_fp64": b[5]})
+    if tmax > 0:
+        # where the largest density error sits, against the shock's radius (the density peak)
+        n = pr.nx
+        xc = (np.arange(n) + 0.5) / n - 0.5
+        j, i = np.unravel_index(np.argmax(np.abs(a[0][0] - b[0][0])), (n, n))
+        js, is_ = np.unravel_index(np.argmax(b[0][0]), (n, n))
+        out["rho_max_error_radius"] = float(np.hypot(xc[i], xc[j]))
+        out["shock_radius"] = float(np.hypot(xc[is_], xc[js]))
+        out["cell"] = 1.0 / n
+        half = hp.sedov(2048, 2048)
+        s = Solver(params_for(half, H.HYDRO_FP64), half.U)
+        n_half = _advance_to(s, tmax)
+        coarse = s.interior().astype(np.float64)
+        s.close()
+        fine = b[0].reshape(4, 2048, 2, 2048, 2).mean(axis=(2, 4))
+        d = np.abs(fine - coarse).reshape(4, -1).sum(1) / np.abs(fine).reshape(4, -1).sum(1)
+        out["grid_l1_rel_2048_vs_4096"] = dict(zip(("rho", "rho_u", "rho_v", "E"), d.tolist()))
+        out["grid_note"] = (f"FP64 4096^2 averaged over 2x2 blocks against FP64 2048^2 ({n_half} steps) at the "
+                            f"same time: the discretisation error scale the FP32 rounding is compared with")
     return out
 
 
@@ -729,6 +763,8 @@ def run_ours(args, world, rank, local):
     secondary = {}
     secondary["kh1024"] = kh_line(flush, 40, args.warmup)
     secondary["kh1024"]["fp32_error_50_steps"] = kh_fp32_error()
+    if world == 1:
+        secondary["kh1024"]["cpu_oracle"] = cpu_variant(workload("kh1024")[0])
     secondary["sedov4096_fp32_error_100_steps"] = sedov4096_error(steps=100)
     if args.sedov4096_to_t01:
         secondary["sedov4096_fp32_error_to_t01"] = sedov4096_error(tmax=0.1)

@@ -156,6 +156,35 @@ __device__ __forceinline__ float* learned_queue() {
   return q;
 }
 
+// Whether tile (bx, by) loads its padded box by one TMA copy: the box must lie where the array holds the
+// values the step needs (FUSED: the interior, so that no boundary map applies; otherwise the ghost-filled
+// array), and the copy's shared-memory destination must be 128-byte aligned.
+template <int TX, int TY, bool FUSED>
+__device__ __forceinline__ bool tile_box_ok(const KParams& P, int bx, int by, const void* dst) {
+  constexpr int QX = TX + 8, QY = TY + 8;
+  if ((smem_addr(dst) & 127u) != 0) return false;
+  const int x0 = P.ng + bx * TX - 4, y0 = P.ng + by * TY - 4;
+  return FUSED ? (x0 >= P.ng && x0 + QX <= P.ng + P.nx && y0 >= P.ng && y0 + QY <= P.ng + P.ny)
+               : (x0 + QX <= P.NX && y0 + QY <= P.NY);
+}
+
+// Tile loads of a block that runs several tiles in turn with the next tile's copy issued early (the
+// single-problem fused step): one mbarrier serves the block's whole run, and the copy of the next tile's box
+// starts when stage 5 of the current tile starts (the primitive area is dead by then), so that its latency
+// overlaps the update instead of stalling the block at the next tile's start.
+// The struct lives in shared memory; thread 0 writes it, between barriers, and every thread reads it where
+// it needs a field (which keeps the fields out of the stages' registers).
+struct TilePipe {
+  unsigned long long bar;  // the block's mbarrier (initialised for one arrival)
+  unsigned int phase;      // parity of the mbarrier phase the next copy completes
+  int issued;              // the current tile's copy was issued during the previous tile
+  int next_tma;            // the next tile loads by TMA: issue its copy at the start of stage 5
+  int nbx, nby;            // the next tile
+  int cbx, cby;            // the current tile (read again in stage 5 rather than kept in registers)
+  int t;                   // the current tile's index in the block's list
+  int stop;                // a copy did not land within the poll budget: the block leaves its remaining tiles
+};
+
 // One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
 // smem_raw must hold TileLayout<R, TX, TY>::bytes.  Starts and ends with a block-wide barrier-free
 // state, so consecutive calls by the same block need one __syncthreads() between them.  MODE selects
@@ -165,12 +194,14 @@ __device__ __forceinline__ float* learned_queue() {
 // every new cell is folded into *cfl_min (no separate dt pass needed).  PERSIST: the block runs several
 // tiles in turn (a TMA tile load then first orders the previous tile's shared-memory accesses before it).
 // tmap: TMA descriptor of Uin for FP32 tile loads (NULL: cell by cell).
-template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false, bool PERSIST = false>
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false, bool PERSIST = false,
+          bool PREFETCH = false>
 __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
                                          const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
                                          unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
                                          const MlpBlob* wsm = nullptr, R* cfl_min = nullptr,
-                                         const CUtensorMap* tmap = nullptr) {
+                                         const CUtensorMap* tmap = nullptr, TilePipe* pipe = nullptr) {
+  static_assert(!(PREFETCH && PERSIST), "a prefetching block orders its tiles itself");
   using L = TileLayout<R, TX, TY>;
   constexpr int QX = L::QX, QP = L::QP, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
   // row width of the y-face items of stage 4 and the cells of stage 5: SX when that makes every warp one
@@ -192,6 +223,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   const R ux = sigx, uy = sigy;  // update factors dt/dx, dt/dy (Eq. 5)
 
   const int tid = threadIdx.x;
+  if constexpr (PREFETCH) {  // the tile's indices come from the pipe (read again in stage 5)
+    bx = pipe->cbx;
+    by = pipe->cby;
+  }
   const int x0 = P.ng + bx * TX;  // padded column of the first interior cell of the tile
   const int y0 = P.ng + by * TY;
   const size_t plane = (size_t)P.NY * P.pitch;
@@ -206,14 +241,13 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   bool tma_tile = false;
   if constexpr (is_f32<R>()) {
     static_assert(QP == QX, "the TMA box is stored densely");
-    // the bulk tensor copy's shared-memory destination must be 128-byte aligned
-    if (tmap != nullptr && (smem_addr(sq) & 127u) == 0)
-      tma_tile = FUSED ? (x0 - 4 >= P.ng && x0 - 4 + QX <= P.ng + P.nx && y0 - 4 >= P.ng && y0 - 4 + QY <= P.ng + P.ny)
-                       : (x0 - 4 + QX <= P.NX && y0 - 4 + QY <= P.NY);
+    // (a prefetching block whose copy of this tile is on its way takes it whatever it computes here)
+    tma_tile = (PREFETCH && pipe->issued) || (tmap != nullptr && tile_box_ok<TX, TY, FUSED>(P, bx, by, sq));
   }
   if (tma_tile) {
     __shared__ unsigned long long tma_bar;
-    const unsigned int bar = smem_addr(&tma_bar);
+    const unsigned int bar = smem_addr(PREFETCH ? &pipe->bar : &tma_bar);
+    const unsigned int parity = PREFETCH ? pipe->phase : 0u;
     if constexpr (PERSIST) {
       // a block that runs several tiles has read and written this shared memory through the generic
       // proxy; order those accesses before the copy's async-proxy writes
@@ -221,22 +255,37 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       __syncthreads();
     }
     const unsigned int polls = P.tma_polls ? P.tma_polls : TMA_WAIT_POLLS;
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
-      if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
+    if constexpr (PREFETCH) {
+      // the block's mbarrier is initialised once; the copy may already be on its way (issued in stage 5 of
+      // the previous tile).  A thread that polls before thread 0 arms the phase sees it incomplete.
+      if (tid == 0 && !pipe->issued) {
+        mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
+        if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
+      }
+    } else {
+      if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
+        if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const bool landed = mbar_wait(bar, 0, polls);
+    const bool landed = mbar_wait(bar, parity, polls);
     if (__syncthreads_or(!landed)) {
       // the copy did not complete within the poll budget: report it, give it one more budget to land
       // (the shared memory should not be released under it) and leave this tile.  If it has not landed after
       // that either, say so apart: the step's output is then to be discarded, and so is anything a later
-      // block on this SM computed while the copy could still arrive
+      // block on this SM computed while the copy could still arrive.  A prefetching block leaves its
+      // remaining tiles too.
       cnt.flags |= STATUS_TIMEOUT;
-      const bool late = !mbar_wait(bar, 0, polls);
+      const bool late = !mbar_wait(bar, parity, polls);
       if (__syncthreads_or(late)) cnt.flags |= STATUS_TIMEOUT_INFLIGHT;
-      if (tid == 0) mbar_inval(bar);
+      if (tid == 0) {
+        if constexpr (PREFETCH)
+          pipe->stop = 1;
+        else
+          mbar_inval(bar);
+      }
       return;
     }
     for (int e = tid; e < QX * QY; e += NT) {
@@ -255,46 +304,58 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       sq[3 * QP * QY + d] = p;
     }
     __syncthreads();
-    if (tid == 0) mbar_inval(bar);  // every thread has passed the wait; the next tile initialises it again
-  } else {
-    // all of a thread's loads are issued before any conversion, so their latencies overlap
-    constexpr int NLD = (QX * QY + NT - 1) / NT;
-    R Ul[NLD][4];
-#pragma unroll
-    for (int it = 0; it < NLD; ++it) {
-      const int e = tid + it * NT;
-      if (e < QX * QY) {
-        const int gi = x0 - 4 + e % QX, gj = y0 - 4 + e / QX;
-        if (FUSED && P.bc_general) {  // reflecting or hydrostatic sides: the ghost fill's values
-          R v[4];
-          bc_cell_clamped(P, Uin, gi, gj, plane, v);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) Ul[it][k] = v[k];
-        } else {
-          const size_t o = cell_offset<FUSED>(P, gi, gj);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
-        }
-      }
+    // every thread has passed the wait: the next tile initialises the mbarrier again, or a prefetching
+    // block's next copy completes its next phase
+    if (tid == 0) {
+      if constexpr (PREFETCH)
+        pipe->phase ^= 1u;
+      else
+        mbar_inval(bar);
     }
+  } else {
+    // a thread's cells in groups of two: both cells' loads are issued before either is converted, so their
+    // latencies overlap, while the values in flight stay few enough to keep the stages' registers free of
+    // spills (all of a thread's cells at once held up to 16 loads)
+    constexpr int NLD = (QX * QY + NT - 1) / NT, CH = 2;
+#pragma unroll 1
+    for (int c0 = 0; c0 < NLD; c0 += CH) {
+      R Ul[CH][4];
 #pragma unroll
-    for (int it = 0; it < NLD; ++it) {
-      const int e = tid + it * NT;
-      if (e < QX * QY) {
-        const int lx = e % QX, ly = e / QX;
-        R rho, u, v, p;
-        cons_to_prim(s, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3], rho, u, v, p);
-        if constexpr (L::SMEM_U) {
-          if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
-            const int c = (ly - 3) * SX + (lx - 3);
-            Quad<R, nC>::st(sU, c, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3]);
+      for (int it = 0; it < CH; ++it) {
+        const int e = tid + (c0 + it) * NT;
+        if (e < QX * QY) {
+          const int gi = x0 - 4 + e % QX, gj = y0 - 4 + e / QX;
+          if (FUSED && P.bc_general) {  // reflecting or hydrostatic sides: the ghost fill's values
+            R v[4];
+            bc_cell_clamped(P, Uin, gi, gj, plane, v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Ul[it][k] = v[k];
+          } else {
+            const size_t o = cell_offset<FUSED>(P, gi, gj);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Ul[it][k] = __ldg(Uin + o + k * plane);
           }
         }
-        const int d = ly * QP + lx;
-        sq[d] = rho;
-        sq[QP * QY + d] = u;
-        sq[2 * QP * QY + d] = v;
-        sq[3 * QP * QY + d] = p;
+      }
+#pragma unroll
+      for (int it = 0; it < CH; ++it) {
+        const int e = tid + (c0 + it) * NT;
+        if (e < QX * QY) {
+          const int lx = e % QX, ly = e / QX;
+          R rho, u, v, p;
+          cons_to_prim(s, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3], rho, u, v, p);
+          if constexpr (L::SMEM_U) {
+            if (lx >= 3 && lx < SX + 3 && ly >= 3 && ly < SY + 3) {
+              const int c = (ly - 3) * SX + (lx - 3);
+              Quad<R, nC>::st(sU, c, Ul[it][0], Ul[it][1], Ul[it][2], Ul[it][3]);
+            }
+          }
+          const int d = ly * QP + lx;
+          sq[d] = rho;
+          sq[QP * QY + d] = u;
+          sq[2 * QP * QY + d] = v;
+          sq[3 * QP * QY + d] = p;
+        }
       }
     }
     __syncthreads();
@@ -355,12 +416,27 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         trace_ppm<R>(s, YD ? sigy : sigx, q, eL, eR, ql, qrr);
       } else {
         R dq[4];
+        if constexpr (is_f32<R>()) {
+          // components in pairs (rho, un) and (ut, p), each pair's limiter in packed arithmetic
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
-          const R* a = sq + k * QP * QY + b;
-          q[m] = a[0];
-          dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+          for (int h = 0; h < 2; ++h) {
+            const R* a = sq + (h == 0 ? 0 : k2) * QP * QY + b;
+            const R* c = sq + (h == 0 ? k1 : 3) * QP * QY + b;
+            q[2 * h] = a[0];
+            q[2 * h + 1] = c[0];
+            const float2 d = mul2(f2(xi), slope_pair(s.limiter, f2(a[-2 * st], c[-2 * st]), f2(a[-st], c[-st]),
+                                                      f2(a[0], c[0]), f2(a[st], c[st]), f2(a[2 * st], c[2 * st])));
+            dq[2 * h] = d.x;
+            dq[2 * h + 1] = d.y;
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int k = m == 0 ? 0 : m == 1 ? k1 : m == 2 ? k2 : 3;
+            const R* a = sq + k * QP * QY + b;
+            q[m] = a[0];
+            dq[m] = xi * slope<R>(s.limiter, a[-2 * st], a[-st], a[0], a[st], a[2 * st]);
+          }
         }
         trace<R>(s, YD ? sigy : sigx, q, dq, ql, qrr);
       }
@@ -391,9 +467,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
 
   // FACE_LEARNED: faces past the network's gate are not solved in the face loops.  Each is queued in a small
   // shared array of its own (face item and, later, starting pressure; LEARNED_QUEUE entries), the other faces
-  // are solved at once from the acoustic start, and after a barrier the network proposes the starting
-  // pressures of the queued faces, 32 per warp, which are then solved from them.  The face loops thus carry
-  // no call and keep the registers of the plain kernel, and a warp evaluates the network on 32 gated faces
+  // are solved at once from the acoustic start, and after the stage's barrier the network proposes the
+  // starting pressures of the queued faces, 32 per warp, which are then solved from them (a tile with no
+  // gated face skips this, and its barriers are those of the plain kernel).  The face loops thus carry no
+  // call and keep the registers of the plain kernel, and a warp evaluates the network on 32 gated faces
   // rather than on the 31 others of a warp that holds one.  The queued faces' states are rebuilt from the
   // traced states, which stay in place until each face's own flux replaces them.  A full queue leaves
   // further gated faces to the acoustic start.
@@ -417,13 +494,12 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       return false;
     }
   };
-  // the network's starting pressures for the queued faces, then their solves (block-wide; the queue was
-  // filled before a barrier); states(e, isx, a, b) rebuilds an item's face states, finish(e, isx, F) stores
-  // its flux
+  // the network's starting pressures for the queued faces, then their solves (block-wide, called only when
+  // the queue, filled before a barrier, holds a face); states(e, isx, a, b) rebuilds an item's face states,
+  // finish(e, isx, F) stores its flux
   auto learned_pass = [&](int st, int nXIa, auto&& states, auto&& finish) {
     if constexpr (LEARNED) {
       const int n = queue_n[st] < LEARNED_QUEUE ? queue_n[st] : LEARNED_QUEUE;
-      if (n == 0) return;  // block-uniform
       for (int b0 = tid - (tid & 31); b0 < n; b0 += NT) {  // warp-uniform: the forward pass is warp-collective
         const int k = b0 + (tid & 31);
         float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -502,12 +578,15 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       face_solve<R, FACE_LOOP_MODE>(s, a, bq, active, hook, face_key(bx, by, 0, e), F, cnt);
       if (active) finish(e, isx, F);
     }
+    __syncthreads();
+    // the queued faces, if the tile has any, after the stage's own barrier (one more barrier only then)
     if constexpr (LEARNED) {
-      __syncthreads();
-      learned_pass(0, nXIa, states, finish);
+      if (queue_n[0] > 0) {  // block-uniform: read after the barrier
+        learned_pass(0, nXIa, states, finish);
+        __syncthreads();
+      }
     }
   }
-  __syncthreads();
 
   // ---- 4. transverse correction + final solves + artificial viscosity at the tile's faces
   {
@@ -523,12 +602,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         R dL[4], dR[4], t0[4], t1[4], l[4], r[4];
         FY::ld(sfyh, fL + SX, t1);
         FY::ld(sfyh, fL, t0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) dL[k] = t1[k] - t0[k];
+        sub4(t1, t0, dL);
         FY::ld(sfyh, fR + SX, t1);
         FY::ld(sfyh, fR, t0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) dR[k] = t1[k] - t0[k];
+        sub4(t1, t0, dR);
         Quad<R, nC>::ld(sxl, cL, l);
         Quad<R, nC>::ld(sxr, cR, r);
         correct_state(s, l[0], l[1], l[2], l[3], dL, hy, a);
@@ -543,12 +620,10 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         R dL[4], dR[4], t0[4], t1[4], l[4], r[4];
         FX::ld(sfxh, fL + 1, t1);
         FX::ld(sfxh, fL, t0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) dL[k] = t1[k] - t0[k];
+        sub4(t1, t0, dL);
         FX::ld(sfxh, fR + 1, t1);
         FX::ld(sfxh, fR, t0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) dR[k] = t1[k] - t0[k];
+        sub4(t1, t0, dR);
         R ql[4], qrr[4];
         Quad<R, nC>::ld(syl, cL, l);
         Quad<R, nC>::ld(syr, cR, r);
@@ -573,11 +648,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             div = (su[cR] - su[cL]) / s.dx + dvy / (4.0 * s.dy);
           const R av = s.cvisc * M<R>::mx(-div * s.dx, (R)0);
           if constexpr (L::SMEM_U) {
-            R uL[4], uR[4];
+            R uL[4], uR[4], du[4];
             Quad<R, nC>::ld(sU, cL, uL);
             Quad<R, nC>::ld(sU, cR, uR);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
+            sub4(uL, uR, du);
+            axpy4(av, du, G);
           } else {
             const int gi = x0 + fx, gj = y0 + ty;  // padded index of cell lx
             R uL[4], uR[4];
@@ -602,11 +677,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
             div = (sv[cR] - sv[cL]) / s.dy + dux / (4.0 * s.dx);
           const R av = s.cvisc * M<R>::mx(-div * s.dy, (R)0);
           if constexpr (L::SMEM_U) {
-            R uL[4], uR[4];
+            R uL[4], uR[4], du[4];
             Quad<R, nC>::ld(sU, cL, uL);
             Quad<R, nC>::ld(sU, cR, uR);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) G[k] += av * (uL[k] - uR[k]);
+            sub4(uL, uR, du);
+            axpy4(av, du, G);
           } else {
             const int gi = x0 + tx, gj = y0 + fy;  // padded index of cell (lx, ly)
             R uL[4], uR[4];
@@ -631,18 +706,40 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       face_solve<R, FACE_LOOP_MODE>(s, a, bq, active, hook, face_key(bx, by, 1, e), F, cnt);
       if (active) finish(e, isx, F);
     }
+    // PREFETCH: the primitive area (region A) is next written by the next tile's copy, through the async
+    // proxy; each thread orders its reads of the hat fluxes there before it
+    if constexpr (PREFETCH) fence_proxy_async_smem();
+    __syncthreads();
+    // the queued faces, if the tile has any, after the stage's own barrier (one more barrier only then)
     if constexpr (LEARNED) {
-      __syncthreads();
-      learned_pass(1, nXIa, states, finish);
+      if (queue_n[1] > 0) {  // block-uniform: read after the barrier
+        learned_pass(1, nXIa, states, finish);
+        if constexpr (PREFETCH) fence_proxy_async_smem();
+        __syncthreads();
+      }
     }
   }
-  __syncthreads();
+
+  // PREFETCH: the next tile's box is copied into the primitive area while this tile's update runs (stage 5
+  // reads the final fluxes and U^n, outside that area)
+  if constexpr (PREFETCH) {
+    if (tid == 0) {
+      if (pipe->next_tma) {
+        const unsigned int bar = smem_addr(&pipe->bar);
+        mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
+        if (!P.tma_test_drop)
+          tma_load_3d(smem_addr(sq), tmap, P.ng + pipe->nbx * TX - 4, P.ng + pipe->nby * TY - 4, 0, bar);
+      }
+      pipe->issued = pipe->next_tma;  // read by the next tile after the barrier between tiles
+    }
+  }
 
   // ---- 5. conservative update of the tile's valid cells
   unsigned int& flags = cnt.flags;
+  const int x5 = PREFETCH ? P.ng + pipe->cbx * TX : x0, y5 = PREFETCH ? P.ng + pipe->cby * TY : y0;
   for (int e = tid; e < RW * TY; e += NT) {
     const int tx = e % RW, ty = e / RW;
-    const int gi = x0 + tx, gj = y0 + ty;
+    const int gi = x5 + tx, gj = y5 + ty;
     if (tx >= TX || gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
     const size_t o = (size_t)gj * P.pitch + gi;
     const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
@@ -658,13 +755,25 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
 #pragma unroll
       for (int k = 0; k < 4; ++k) un[k] = __ldg(Uin + o + k * plane);
     }
+    rho_n = un[0];
+    my_n = un[2];
+    if constexpr (is_f32<R>()) {
+      // (rho, rho u) and (rho v, E) in packed arithmetic
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const R d = ux * (fx0[k] - fx1[k]) + uy * (fy0[k] - fy1[k]);
-      const R u0 = un[k];
-      if (k == 0) rho_n = u0;
-      if (k == 2) my_n = u0;
-      Un[k] = u0 + d;
+      for (int h = 0; h < 2; ++h) {
+        const float2 dx = sub2(f2(fx0[2 * h], fx0[2 * h + 1]), f2(fx1[2 * h], fx1[2 * h + 1]));
+        const float2 dy = sub2(f2(fy0[2 * h], fy0[2 * h + 1]), f2(fy1[2 * h], fy1[2 * h + 1]));
+        const float2 d = fma2(f2(ux), dx, mul2(f2(uy), dy));
+        const float2 n = add2(f2(un[2 * h], un[2 * h + 1]), d);
+        Un[2 * h] = n.x;
+        Un[2 * h + 1] = n.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const R d = ux * (fx0[k] - fx1[k]) + uy * (fy0[k] - fy1[k]);
+        Un[k] = un[k] + d;
+      }
     }
     if (P.use_grav) {
       // time-centred gravity sources (§3.2): rho v gains dt g (rho^n + rho^{n+1}) / 2, then rho E gains

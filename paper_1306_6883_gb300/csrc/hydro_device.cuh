@@ -144,6 +144,46 @@ __device__ __forceinline__ float rsqa(float x) {
 
 __device__ __forceinline__ float M<float>::sq(float x) { return x * rsqa(x); }
 
+// Packed FP32x2 arithmetic (sm_100 and later): one instruction applies the same operation to two values,
+// each rounded as the scalar operation rounds it.  The FP32 path uses it wherever two components of a state,
+// or the two sides of a face, go through the same arithmetic; it halves the issue slots of that arithmetic.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tsub.rn.f32x2 z, x, y;\n\t"
+      "mov.b64 {%0, %1}, z;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// Four-component helpers: d = a - b and y = y + c x, in the FP32 path as two packed operations each; the FP64
+// path keeps one scalar operation per component in the same order.
+template <typename R>
+__device__ __forceinline__ void sub4(const R a[4], const R b[4], R d[4]) {
+  if constexpr (is_f32<R>()) {
+    const float2 lo = sub2(f2(a[0], a[1]), f2(b[0], b[1])), hi = sub2(f2(a[2], a[3]), f2(b[2], b[3]));
+    d[0] = lo.x; d[1] = lo.y; d[2] = hi.x; d[3] = hi.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = a[k] - b[k];
+  }
+}
+template <typename R>
+__device__ __forceinline__ void axpy4(R c, const R x[4], R y[4]) {
+  if constexpr (is_f32<R>()) {
+    const float2 lo = fma2(f2(c), f2(x[0], x[1]), f2(y[0], y[1])), hi = fma2(f2(c), f2(x[2], x[3]), f2(y[2], y[3]));
+    y[0] = lo.x; y[1] = lo.y; y[2] = hi.x; y[3] = hi.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y[k] = y[k] + c * x[k];
+  }
+}
+
 // Per-precision copies of the scalar parameters used in the stencil.
 template <typename R>
 struct SP {
@@ -238,8 +278,9 @@ __device__ __forceinline__ void cons_to_prim(const SP<R>& s, R U0, R U1, R U2, R
   rho = U0 < s.small_dens ? s.small_dens : U0;
   if constexpr (is_f32<R>()) {
     const float ir = rcpa(rho);
-    u = U1 * ir;
-    v = U2 * ir;
+    const float2 uv = mul2(f2(U1, U2), f2(ir));
+    u = uv.x;
+    v = uv.y;
     const float ke = 0.5f * rho * (u * u + v * v);
     if (ke > s.rec * U3) {
       // kinetic energy within 0.1% (by default) of the total: recover e = E - rho |u|^2 / 2 in double
@@ -341,6 +382,28 @@ __device__ __forceinline__ R slope(int limiter, R qm2, R qm1, R q0, R qp1, R qp2
   return dl * dr > (R)0 ? lim : (R)0;
 }
 
+// The same limiter for two components at once (FP32 path): the differences and products as packed
+// operations, the magnitudes, minima and sign cases per component.
+__device__ __forceinline__ float2 mc2_pair(float2 qm, float2 q0, float2 qp) {
+  const float2 dl = sub2(q0, qm), dr = sub2(qp, q0), dc = mul2(f2(0.5f), sub2(qp, qm));
+  const float2 dlim = mul2(f2(2.0f), f2(fminf(fabsf(dl.x), fabsf(dr.x)), fminf(fabsf(dl.y), fabsf(dr.y))));
+  const float2 pr = mul2(dl, dr);
+  const float mx = fminf(fabsf(dc.x), dlim.x), my = fminf(fabsf(dc.y), dlim.y);
+  return f2(pr.x > 0.f ? (dc.x >= 0.f ? mx : -mx) : 0.f, pr.y > 0.f ? (dc.y >= 0.f ? my : -my) : 0.f);
+}
+
+__device__ __forceinline__ float2 slope_pair(int limiter, float2 qm2, float2 qm1, float2 q0, float2 qp1, float2 qp2) {
+  if (limiter == 0) return f2(0.f);  // uniform over the launch
+  if (limiter == 1) return mc2_pair(qm1, q0, qp1);
+  const float2 dl = sub2(q0, qm1), dr = sub2(qp1, q0), dc = mul2(f2(0.5f), sub2(qp1, qm1));
+  const float2 dlim = mul2(f2(2.0f), f2(fminf(fabsf(dl.x), fabsf(dr.x)), fminf(fabsf(dl.y), fabsf(dr.y))));
+  const float2 m = add2(mc2_pair(q0, qp1, qp2), mc2_pair(qm2, qm1, q0));
+  const float2 d4 = fma2(f2(4.0f / 3.0f), dc, mul2(f2(-1.0f / 6.0f), m));
+  const float2 pr = mul2(dl, dr);
+  const float mx = fminf(fabsf(d4.x), dlim.x), my = fminf(fabsf(d4.y), dlim.y);
+  return f2(pr.x > 0.f ? (d4.x >= 0.f ? mx : -mx) : 0.f, pr.y > 0.f ? (d4.y >= 0.f ? my : -my) : 0.f);
+}
+
 // Flattening shock detector on one line (§3.2, Colella 1990): chi in [0, 1].
 template <typename R>
 __device__ __forceinline__ R flatten_chi(R pm2, R pm1, R pp1, R pp2, R um1, R up1, R small_pres) {
@@ -412,7 +475,13 @@ __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], con
   }
   // left state: reference with lam4, waves moving right add (sigma/2)(lam4 - lam) beta r
   R aL = (R)0.5 * ((R)1 - sigma * lam4);
-  R l0 = q[0] + aL * dq[0], l1 = q[1] + aL * dq[1], l2 = q[2] + aL * dq[2], l3 = q[3] + aL * dq[3];
+  R l0, l1, l2, l3;
+  if constexpr (is_f32<R>()) {
+    const float2 lo = fma2(f2(aL), f2(dq[0], dq[1]), f2(q[0], q[1])), hi = fma2(f2(aL), f2(dq[2], dq[3]), f2(q[2], q[3]));
+    l0 = lo.x; l1 = lo.y; l2 = hi.x; l3 = hi.y;
+  } else {
+    l0 = q[0] + aL * dq[0]; l1 = q[1] + aL * dq[1]; l2 = q[2] + aL * dq[2]; l3 = q[3] + aL * dq[3];
+  }
   if (lam1 >= (R)0) {
     R w = hs * g41 * b1;
     l0 += w;
@@ -436,7 +505,13 @@ __device__ __forceinline__ void trace(const SP<R>& s, R sigma, const R q[4], con
     g14 = lam1 - lam4;
   }
   R aR = (R)0.5 * ((R)1 + sigma * lam1);
-  R r0 = q[0] - aR * dq[0], r1 = q[1] - aR * dq[1], r2 = q[2] - aR * dq[2], r3 = q[3] - aR * dq[3];
+  R r0, r1, r2, r3;
+  if constexpr (is_f32<R>()) {
+    const float2 lo = fma2(f2(-aR), f2(dq[0], dq[1]), f2(q[0], q[1])), hi = fma2(f2(-aR), f2(dq[2], dq[3]), f2(q[2], q[3]));
+    r0 = lo.x; r1 = lo.y; r2 = hi.x; r3 = hi.y;
+  } else {
+    r0 = q[0] - aR * dq[0]; r1 = q[1] - aR * dq[1]; r2 = q[2] - aR * dq[2]; r3 = q[3] - aR * dq[3];
+  }
   if (lam2 <= (R)0) {
     R w2 = hs * g12 * b2;
     r0 += w2;
@@ -725,30 +800,34 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   const float g = s.gamma, g1 = s.g1;
   const float rl = qL[0], ul = qL[1], vl = qL[2], pl = qL[3];
   const float rr = qR[0], ur = qR[1], vr = qR[2], pr = qR[3];
-  const float xl = g * pl * rl, xr = g * pr * rr;
-  const float icl = rsqa(xl), icr = rsqa(xr);  // 1/C_K
-  const float cl = xl * icl, cr = xr * icr;
+  // the two sides go through the same arithmetic: (left, right) pairs in packed operations
+  const float2 P = f2(pl, pr), U = f2(ul, ur);
+  const float2 X = mul2(mul2(f2(g), P), f2(rl, rr));  // C_K^2 = gamma p_K rho_K
+  const float icl = rsqa(X.x), icr = rsqa(X.y);       // 1/C_K
+  const float2 C = mul2(X, f2(icl, icr));
+  const float cl = C.x, cr = C.y;
   // one MUFU reciprocal each costs fewer issue slots than forming 1/p_K from 1/C_K^2 = 1/(gamma p_K rho_K)
-  const float ipl = rcpa(pl), ipr = rcpa(pr);
+  const float2 IP = f2(rcpa(pl), rcpa(pr));
   // velocity scale of the problem: float rounding leaves u*_R - u*_L uncertain by ~2^-24 of it, which can
   // exceed tol * p* in pressure when p* << rho u^2, so the FP32 stopping rule also accepts a pressure
   // change smaller than the one a velocity mismatch of tol times this scale would produce
-  const float tolv = s.tol * (fabsf(ul) + fabsf(ur) + g * (pl * icl + pr * icr));
+  const float2 PIC = mul2(P, f2(icl, icr));
+  const float tolv = s.tol * (fabsf(ul) + fabsf(ur) + g * (PIC.x + PIC.y));
+  // 1/C_K with the side's sign: u*_L falls and u*_R rises with the star pressure
+  const float2 ICS = f2(-icl, icr);
   float pst = guess > 0.0f ? guess : (cr * pl + cl * pr + cl * cr * (ul - ur)) * rcpa(cl + cr);
   pst = pst < s.small_pres ? s.small_pres : pst;
   int it = 0;
   bool ok = false;
   while (it < s.maxiter) {
-    const float al = 1.0f + g1 * (pst * ipl - 1.0f), ar = 1.0f + g1 * (pst * ipr - 1.0f);
-    const float tl = rsqa(al), tr = rsqa(ar);
-    const float iwl = tl * icl, iwr = tr * icr;
-    const float usl = ul - (pst - pl) * iwl;
-    const float usr = ur + (pst - pr) * iwr;
+    const float2 A = fma2(f2(g1), fma2(f2(pst), IP, f2(-1.0f)), f2(1.0f));  // a_K
+    const float2 T = f2(rsqa(A.x), rsqa(A.y));                             // t_K
+    const float2 IWS = mul2(T, ICS);                                        // (-1/W_L, 1/W_R)
+    const float2 US = fma2(sub2(f2(pst), P), IWS, U);                       // (u*_L, u*_R)
     // (a_K + 1) t_K^2 / 2 = (1 + 1/a_K) / 2 = (1 + t_K^2) / 2
-    const float izl = fmaf(0.5f, tl * tl, 0.5f) * iwl;
-    const float izr = fmaf(0.5f, tr * tr, 0.5f) * iwr;
-    const float iz = izl + izr;  // 1 / (Z_L Z_R / (Z_L + Z_R))
-    float pnew = pst - (usr - usl) * rcpa(iz);
+    const float2 IZS = mul2(fma2(f2(0.5f), mul2(T, T), f2(0.5f)), IWS);    // (-1/Z_L, 1/Z_R)
+    const float iz = IZS.y - IZS.x;  // 1 / (Z_L Z_R / (Z_L + Z_R))
+    float pnew = pst - (US.y - US.x) * rcpa(iz);
     pnew = pnew < s.small_pres ? s.small_pres : pnew;
     const float dp = fabsf(pnew - pst);
     pst = pnew;
@@ -760,10 +839,12 @@ __device__ __forceinline__ void riemann(const SP<float>& s, const float qL[4], c
   }
   iters = it;
   conv = ok;
-  const float al = 1.0f + g1 * (pst * ipl - 1.0f), ar = 1.0f + g1 * (pst * ipr - 1.0f);
-  const float tl = rsqa(al), tr = rsqa(ar);
-  const float wl = cl * al * tl, wr = cr * ar * tr;
-  const float ust = ((wl * ul + wr * ur) + (pl - pr)) * rcpa(wl + wr);
+  const float2 A = fma2(f2(g1), fma2(f2(pst), IP, f2(-1.0f)), f2(1.0f));
+  const float tl = rsqa(A.x), tr = rsqa(A.y);
+  const float2 W = mul2(mul2(C, A), f2(tl, tr));
+  const float wl = W.x, wr = W.y;
+  const float2 WU = mul2(W, U);
+  const float ust = ((WU.x + WU.y) + (pl - pr)) * rcpa(wl + wr);
 
   // sampling at x/t = 0 (the same cases as the FP64 solver).  A face on the contact (u* = 0; whole warps of
   // it in a fluid at rest) takes the mean state; otherwise the case (shock, fan head, fan tail, inside the

@@ -353,3 +353,35 @@ def test_learned_ensemble_needs_its_model(torch):
         Ensemble([params_for(probs[0], H.HYDRO_FP32, use_learned_guess=1), params_for(probs[1], H.HYDRO_FP32)],
                  [p.U for p in probs])
     m.close()
+
+
+def test_sedov_8192_learned_fp32_error_against_fp64(torch):
+    # the largest workload: the Sedov blast on 8192^2 cells with 1 % density noise, FP32 with the learned
+    # start (default gate) against the FP64 run, which is the oracle's bit for bit, after 25 fused steps from
+    # the same state.  Observed on GB300 (25 steps): L1 relative 2.2e-8 (rho), 4.0e-7 (rho u, rho v), 5.8e-8
+    # (E); max relative 9.1e-7, 8.3e-7, 8.4e-7, 7.0e-7.  Bounds 6-8x those.
+    from paper_1306_6883_gb300 import hydro as H
+    from paper_1306_6883_gb300.solver import Model, Solver, params_for
+    m = Model(seed=21)
+    m.train(torch.from_numpy(_random_faces(20000, seed=22)).cuda(), steps=800, batch=1024, lr=2e-3, seed=23)
+    pr = hp.sedov(8192, 8192, density_noise=0.01)
+    out = {}
+    for prec in (H.HYDRO_FP64, H.HYDRO_FP32):
+        learned = prec == H.HYDRO_FP32
+        s = Solver(params_for(pr, prec, use_learned_guess=1 if learned else 0), pr.U)
+        if learned:
+            H.hydro_set_riemann_model(s.ctx, m.m)
+        s.advance(25)
+        st, stats = s.status()
+        assert st == 0 and stats[2] == 0
+        out[prec] = s.interior()
+        s.close()
+    m.close()
+    l1, mx = np.zeros(4), np.zeros(4)
+    for k in range(4):  # field by field: the 8192^2 arrays are 0.5 GB each in double
+        b = out[H.HYDRO_FP64][k]
+        d = np.abs(out[H.HYDRO_FP32][k].astype(np.float64) - b)
+        l1[k] = d.sum() / np.abs(b).sum()
+        mx[k] = d.max() / np.abs(b).max()
+    assert np.all(l1 <= np.array([1.6e-7, 2.8e-6, 2.8e-6, 4e-7])), l1
+    assert np.all(mx <= np.array([6e-6, 6e-6, 6e-6, 5e-6])), mx
