@@ -168,23 +168,6 @@ __device__ __forceinline__ bool tile_box_ok(const KParams& P, int bx, int by, co
                : (x0 + QX <= P.NX && y0 + QY <= P.NY);
 }
 
-// Tile loads of a block that runs several tiles in turn with the next tile's copy issued early (the
-// single-problem fused step): one mbarrier serves the block's whole run, and the copy of the next tile's box
-// starts when stage 5 of the current tile starts (the primitive area is dead by then), so that its latency
-// overlaps the update instead of stalling the block at the next tile's start.
-// The struct lives in shared memory; thread 0 writes it, between barriers, and every thread reads it where
-// it needs a field (which keeps the fields out of the stages' registers).
-struct TilePipe {
-  unsigned long long bar;  // the block's mbarrier (initialised for one arrival)
-  unsigned int phase;      // parity of the mbarrier phase the next copy completes
-  int issued;              // the current tile's copy was issued during the previous tile
-  int next_tma;            // the next tile loads by TMA: issue its copy at the start of stage 5
-  int nbx, nby;            // the next tile
-  int cbx, cby;            // the current tile (read again in stage 5 rather than kept in registers)
-  int t;                   // the current tile's index in the block's list
-  int stop;                // a copy did not land within the poll budget: the block leaves its remaining tiles
-};
-
 // One TX x TY tile (tile indices bx, by) of one CTU step, executed by all NT threads of the block.
 // smem_raw must hold TileLayout<R, TX, TY>::bytes.  Starts and ends with a block-wide barrier-free
 // state, so consecutive calls by the same block need one __syncthreads() between them.  MODE selects
@@ -194,14 +177,12 @@ struct TilePipe {
 // every new cell is folded into *cfl_min (no separate dt pass needed).  PERSIST: the block runs several
 // tiles in turn (a TMA tile load then first orders the previous tile's shared-memory accesses before it).
 // tmap: TMA descriptor of Uin for FP32 tile loads (NULL: cell by cell).
-template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false, bool PERSIST = false,
-          bool PREFETCH = false>
+template <typename R, int TX, int TY, int NT, int MODE = FACE_PLAIN, bool FUSED = false, bool PERSIST = false>
 __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const StepFactors<R>& f,
                                          const R* __restrict__ Uin, R* __restrict__ Uout, int bx, int by,
                                          unsigned char* smem_raw, TileCounters& cnt, const FaceHook& hook = FaceHook{},
                                          const MlpBlob* wsm = nullptr, R* cfl_min = nullptr,
-                                         const CUtensorMap* tmap = nullptr, TilePipe* pipe = nullptr) {
-  static_assert(!(PREFETCH && PERSIST), "a prefetching block orders its tiles itself");
+                                         const CUtensorMap* tmap = nullptr) {
   using L = TileLayout<R, TX, TY>;
   constexpr int QX = L::QX, QP = L::QP, QY = L::QY, SX = L::SX, SY = L::SY, nC = L::nC;
   // row width of the y-face items of stage 4 and the cells of stage 5: SX when that makes every warp one
@@ -223,10 +204,6 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   const R ux = sigx, uy = sigy;  // update factors dt/dx, dt/dy (Eq. 5)
 
   const int tid = threadIdx.x;
-  if constexpr (PREFETCH) {  // the tile's indices come from the pipe (read again in stage 5)
-    bx = pipe->cbx;
-    by = pipe->cby;
-  }
   const int x0 = P.ng + bx * TX;  // padded column of the first interior cell of the tile
   const int y0 = P.ng + by * TY;
   const size_t plane = (size_t)P.NY * P.pitch;
@@ -241,13 +218,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
   bool tma_tile = false;
   if constexpr (is_f32<R>()) {
     static_assert(QP == QX, "the TMA box is stored densely");
-    // (a prefetching block whose copy of this tile is on its way takes it whatever it computes here)
-    tma_tile = (PREFETCH && pipe->issued) || (tmap != nullptr && tile_box_ok<TX, TY, FUSED>(P, bx, by, sq));
+    tma_tile = tmap != nullptr && tile_box_ok<TX, TY, FUSED>(P, bx, by, sq);
   }
   if (tma_tile) {
     __shared__ unsigned long long tma_bar;
-    const unsigned int bar = smem_addr(PREFETCH ? &pipe->bar : &tma_bar);
-    const unsigned int parity = PREFETCH ? pipe->phase : 0u;
+    const unsigned int bar = smem_addr(&tma_bar);
     if constexpr (PERSIST) {
       // a block that runs several tiles has read and written this shared memory through the generic
       // proxy; order those accesses before the copy's async-proxy writes
@@ -255,37 +230,22 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       __syncthreads();
     }
     const unsigned int polls = P.tma_polls ? P.tma_polls : TMA_WAIT_POLLS;
-    if constexpr (PREFETCH) {
-      // the block's mbarrier is initialised once; the copy may already be on its way (issued in stage 5 of
-      // the previous tile).  A thread that polls before thread 0 arms the phase sees it incomplete.
-      if (tid == 0 && !pipe->issued) {
-        mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
-        if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
-      }
-    } else {
-      if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
-        if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
-      }
-      __syncthreads();
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
+      if (!P.tma_test_drop) tma_load_3d(smem_addr(sq), tmap, x0 - 4, y0 - 4, 0, bar);
     }
-    const bool landed = mbar_wait(bar, parity, polls);
+    __syncthreads();
+    const bool landed = mbar_wait(bar, 0, polls);
     if (__syncthreads_or(!landed)) {
       // the copy did not complete within the poll budget: report it, give it one more budget to land
       // (the shared memory should not be released under it) and leave this tile.  If it has not landed after
       // that either, say so apart: the step's output is then to be discarded, and so is anything a later
-      // block on this SM computed while the copy could still arrive.  A prefetching block leaves its
-      // remaining tiles too.
+      // block on this SM computed while the copy could still arrive
       cnt.flags |= STATUS_TIMEOUT;
-      const bool late = !mbar_wait(bar, parity, polls);
+      const bool late = !mbar_wait(bar, 0, polls);
       if (__syncthreads_or(late)) cnt.flags |= STATUS_TIMEOUT_INFLIGHT;
-      if (tid == 0) {
-        if constexpr (PREFETCH)
-          pipe->stop = 1;
-        else
-          mbar_inval(bar);
-      }
+      if (tid == 0) mbar_inval(bar);
       return;
     }
     for (int e = tid; e < QX * QY; e += NT) {
@@ -304,14 +264,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       sq[3 * QP * QY + d] = p;
     }
     __syncthreads();
-    // every thread has passed the wait: the next tile initialises the mbarrier again, or a prefetching
-    // block's next copy completes its next phase
-    if (tid == 0) {
-      if constexpr (PREFETCH)
-        pipe->phase ^= 1u;
-      else
-        mbar_inval(bar);
-    }
+    if (tid == 0) mbar_inval(bar);  // every thread has passed the wait; the next tile initialises it again
   } else {
     // a thread's cells in groups of two: both cells' loads are issued before either is converted, so their
     // latencies overlap, while the values in flight stay few enough to keep the stages' registers free of
@@ -706,40 +659,21 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
       face_solve<R, FACE_LOOP_MODE>(s, a, bq, active, hook, face_key(bx, by, 1, e), F, cnt);
       if (active) finish(e, isx, F);
     }
-    // PREFETCH: the primitive area (region A) is next written by the next tile's copy, through the async
-    // proxy; each thread orders its reads of the hat fluxes there before it
-    if constexpr (PREFETCH) fence_proxy_async_smem();
     __syncthreads();
     // the queued faces, if the tile has any, after the stage's own barrier (one more barrier only then)
     if constexpr (LEARNED) {
       if (queue_n[1] > 0) {  // block-uniform: read after the barrier
         learned_pass(1, nXIa, states, finish);
-        if constexpr (PREFETCH) fence_proxy_async_smem();
         __syncthreads();
       }
     }
   }
 
-  // PREFETCH: the next tile's box is copied into the primitive area while this tile's update runs (stage 5
-  // reads the final fluxes and U^n, outside that area)
-  if constexpr (PREFETCH) {
-    if (tid == 0) {
-      if (pipe->next_tma) {
-        const unsigned int bar = smem_addr(&pipe->bar);
-        mbar_arrive_expect_tx(bar, 4u * QX * QY * sizeof(R));
-        if (!P.tma_test_drop)
-          tma_load_3d(smem_addr(sq), tmap, P.ng + pipe->nbx * TX - 4, P.ng + pipe->nby * TY - 4, 0, bar);
-      }
-      pipe->issued = pipe->next_tma;  // read by the next tile after the barrier between tiles
-    }
-  }
-
   // ---- 5. conservative update of the tile's valid cells
   unsigned int& flags = cnt.flags;
-  const int x5 = PREFETCH ? P.ng + pipe->cbx * TX : x0, y5 = PREFETCH ? P.ng + pipe->cby * TY : y0;
   for (int e = tid; e < RW * TY; e += NT) {
     const int tx = e % RW, ty = e / RW;
-    const int gi = x5 + tx, gj = y5 + ty;
+    const int gi = x0 + tx, gj = y0 + ty;
     if (tx >= TX || gi >= P.ng + P.nx || gj >= P.ng + P.ny) continue;
     const size_t o = (size_t)gj * P.pitch + gi;
     const int cx = (ty + 1) * SX + tx;  // final x flux of face tx (left of cell) lives in sxl[cx]
