@@ -467,7 +467,7 @@ def _oracle_window_params(pr, w):
     return oracle.params(w, w, xmax=w * dx, ymax=w * dy, gamma=pr.gamma, cfl=pr.cfl, grav=pr.grav)
 
 
-def cpu_baseline(pr, window=4096, max_steps=5, budget_s=12.0):
+def cpu_baseline(pr, window=4096, max_steps=5, budget_s=12.0, single_core=True):
     """The oracle as it stands (OpenMP over rows on all host cores) on a bounded sample of the workload:
     whole oracle steps (dt + step) of its centred window, from the initial state.  Beside it, the oracle on
     one core (a child process with OMP_NUM_THREADS=1) on a smaller centred window."""
@@ -488,7 +488,8 @@ def cpu_baseline(pr, window=4096, max_steps=5, budget_s=12.0):
                      f"{pr.nx}x{pr.ny} workload from its initial state (its outer 4 cells as ghost cells), "
                      f"{el:.1f} s; per zone-update, it stands for the whole grid (extrapolated)",
            "host": host_info()}
-    out["single_core"] = cpu_single_core(pr)
+    if single_core:
+        out["single_core"] = cpu_single_core(pr)
     return out
 
 
@@ -621,6 +622,65 @@ def kh_line(flush, steps, warmup):
     return {"workload": wname, "fp32": a32, "fp64": a64, "fp32_speedup_over_fp64": a32["value"] / a64["value"],
             "roofline_fp32": roofline("fp32", zones, kern, r32["iters_per_solve"], "ctu_step_fused_kernel", "kh1024"),
             "l2": "flushed (256 MB write) before every timed step"}
+
+
+def sedov4096_line(model, steps, warmup, world):
+    """The Sedov 4096^2 blast (no noise; one FP32 state buffer 269 MB, above L2): FP32 with the learned start,
+    plain FP32 and plain FP64 from the same state, each with its roofline, and the oracle beside them."""
+    pr, wname = workload("sedov4096")
+    zones = pr.nx * pr.ny
+    arms = {}
+    for name, prec, m in (("fp32_learned", "fp32", model), ("fp32_plain", "fp32", None), ("fp64_plain", "fp64", None)):
+        r = run_arm(pr, prec, steps, warmup, model=m, keep_state=False)
+        a = arm_summary(pr, r)
+        kern = sum(r["step_ms"]) / len(r["step_ms"])
+        rl = roofline(prec, zones, kern, r["iters_per_solve"], "ctu_step_fused_kernel")
+        arms[name] = dict(a, roofline_frac=rl["frac"], hbm_frac=rl["hbm"]["frac"])
+    out = {"workload": wname, "steps": steps, "arms": arms,
+           "speedup_fp32_learned_over_fp64": arms["fp32_learned"]["value"] / arms["fp64_plain"]["value"],
+           "l2": "inputs larger than L2 (one FP32 state buffer 269 MB); steps timed back to back"}
+    if world == 1:
+        out["cpu_oracle"] = cpu_baseline(pr, window=4096, max_steps=3, budget_s=6.0, single_core=False)
+    return out
+
+
+def learned_cost(model, n=1 << 23, seed=0):
+    """What the network's start costs and saves per face, apart from the step: the library's iteration kernel
+    (hydro_mlp_iterations) solves the same n Riemann problems from the acoustic start and from the network's
+    (every face evaluated, no gate), timed with CUDA events.  Two seeded face classes: weak faces (jumps of
+    about 1 %) and strong ones (density ratio up to 20, pressure ratio up to 1000, |u| up to 1.5)."""
+    import torch
+
+    from paper_1306_6883_gb300 import hydro as H
+
+    rng = np.random.default_rng(seed)
+    classes = {
+        "weak": (rng.uniform(1.0, 1.01, (n, 2)), rng.uniform(-0.005, 0.005, (n, 2)), rng.uniform(1.0, 1.01, (n, 2))),
+        "strong": (np.exp(rng.uniform(np.log(0.1), np.log(2.0), (n, 2))), rng.uniform(-1.5, 1.5, (n, 2)),
+                   np.exp(rng.uniform(np.log(0.01), np.log(10.0), (n, 2)))),
+    }
+    out = {"faces": n}
+    for name, (rho, u, p) in classes.items():
+        d = np.zeros((n, 8), dtype=np.float32)
+        d[:, 0], d[:, 1], d[:, 2] = rho[:, 0], u[:, 0], p[:, 0]
+        d[:, 3], d[:, 4], d[:, 5] = rho[:, 1], u[:, 1], p[:, 1]
+        dev = torch.from_numpy(d).cuda()
+        res = {}
+        for learned in (0, 1):
+            H.hydro_mlp_iterations(model.m, dev.data_ptr(), n, learned)  # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            mean, nonconv = H.hydro_mlp_iterations(model.m, dev.data_ptr(), n, learned)
+            b.record()
+            torch.cuda.synchronize()
+            res["learned" if learned else "acoustic"] = {"iters_per_solve": mean, "nonconverged": nonconv,
+                                                        "ns_per_face": a.elapsed_time(b) * 1e6 / n}
+        res["iterations_saved"] = res["acoustic"]["iters_per_solve"] - res["learned"]["iters_per_solve"]
+        out[name] = res
+        del dev
+    out["note"] = ("the acoustic runs are bound by reading the samples (32 B per face), the learned ones by the "
+                   "network's arithmetic; the instruction counts per face are in the ncu summary of this kernel")
+    return out
 
 
 def kh_fp32_error(steps=50):
@@ -765,11 +825,13 @@ def run_ours(args, world, rank, local):
     secondary["kh1024"]["fp32_error_50_steps"] = kh_fp32_error()
     if world == 1:
         secondary["kh1024"]["cpu_oracle"] = cpu_variant(workload("kh1024")[0])
+    secondary["sedov4096"] = sedov4096_line(model, args.steps, args.warmup, world)
     secondary["sedov4096_fp32_error_100_steps"] = sedov4096_error(steps=100)
     if args.sedov4096_to_t01:
         secondary["sedov4096_fp32_error_to_t01"] = sedov4096_error(tmax=0.1)
     secondary["ensemble_plain"] = time_ensemble()
     secondary["ensemble_learned"] = time_ensemble(model=model)
+    secondary["learned_cost"] = learned_cost(model)
     secondary.update(variant_legs(flush, args.warmup, world))
     model.close()
 

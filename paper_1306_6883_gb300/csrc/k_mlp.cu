@@ -278,44 +278,50 @@ __global__ void mlp_predict_kernel(const float* __restrict__ theta, const MlpBlo
 
 // FP32 two-shock iterations each sample needs at tolerance tol from the acoustic start (learned = 0) or
 // from the network's start (learned = 1, tensor-core inference, no gate); sums[0] += iterations,
-// sums[1] += unconverged solves, sums[2] += solves.
-__global__ void riemann_iters_kernel(const MlpBlob* __restrict__ blob, const float* __restrict__ samples,
-                                     unsigned long long n, int learned, float gamma, float tol, int maxiter,
-                                     unsigned long long* __restrict__ sums) {
-  const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = i < n;
-  float a[4] = {1.f, 0.f, 0.f, 1.f}, b[4] = {1.f, 0.f, 0.f, 1.f};
-  if (act) {
-    const float* d = samples + 8 * i;
-    a[0] = d[0]; a[1] = d[1]; a[3] = d[2];
-    b[0] = d[3]; b[1] = d[4]; b[3] = d[5];
-  }
-  float guess = 0.f;
-  if (learned) {  // warp-collective
-    float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float pref = 0.f;
-    if (act) pref = mlp_features(a[0], a[1], a[3], b[0], b[1], b[3], x);
-    const float y = fminf(fmaxf(mlp_warp_forward(x, blob), -40.f), 40.f);
-    guess = act ? pref * __expf(y) : 0.f;
-  }
-  unsigned int it = 0, nc = 0, ns = 0;
-  if (act) {
-    SP<float> s{};
-    s.gamma = gamma;
-    s.gm1 = gamma - 1.f;
-    s.igm1 = 1.f / (gamma - 1.f);
-    s.g1 = (gamma + 1.f) / (2.f * gamma);
-    s.small_dens = 1e-10f;
-    s.small_pres = 1e-20f;
-    s.tol = tol;
-    s.maxiter = maxiter;
-    float F[4];
-    int k;
-    bool ok;
-    riemann(s, a, b, guess, F, k, ok);
-    it = (unsigned int)k;
-    nc = ok ? 0u : 1u;
-    ns = 1u;
+// sums[1] += unconverged solves, sums[2] += solves.  Grid-stride over warps of 32 samples (the network is
+// warp-collective), counts kept per thread and added once per block, so that the time is the solves' own.
+__global__ void __launch_bounds__(256) riemann_iters_kernel(const MlpBlob* __restrict__ blob,
+                                                            const float* __restrict__ samples, unsigned long long n,
+                                                            int learned, float gamma, float tol, int maxiter,
+                                                            unsigned long long* __restrict__ sums) {
+  SP<float> s{};
+  s.gamma = gamma;
+  s.gm1 = gamma - 1.f;
+  s.igm1 = 1.f / (gamma - 1.f);
+  s.g1 = (gamma + 1.f) / (2.f * gamma);
+  s.small_dens = 1e-10f;
+  s.small_pres = 1e-20f;
+  s.tol = tol;
+  s.maxiter = maxiter;
+  unsigned long long it = 0, nc = 0, ns = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += stride) {  // warp-uniform
+    const unsigned long long i = base + (threadIdx.x & 31u);
+    const bool act = i < n;
+    float a[4] = {1.f, 0.f, 0.f, 1.f}, b[4] = {1.f, 0.f, 0.f, 1.f};
+    if (act) {
+      const float* d = samples + 8 * i;
+      a[0] = d[0]; a[1] = d[1]; a[3] = d[2];
+      b[0] = d[3]; b[1] = d[4]; b[3] = d[5];
+    }
+    float guess = 0.f;
+    if (learned) {  // warp-collective
+      float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float pref = 0.f;
+      if (act) pref = mlp_features(a[0], a[1], a[3], b[0], b[1], b[3], x);
+      const float y = fminf(fmaxf(mlp_warp_forward(x, blob), -40.f), 40.f);
+      guess = act ? pref * __expf(y) : 0.f;
+    }
+    if (act) {
+      float F[4];
+      int k;
+      bool ok;
+      riemann(s, a, b, guess, F, k, ok);
+      it += (unsigned int)k;
+      nc += ok ? 0u : 1u;
+      ns += 1u;
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -323,10 +329,17 @@ __global__ void riemann_iters_kernel(const MlpBlob* __restrict__ blob, const flo
     nc += __shfl_xor_sync(0xffffffffu, nc, off);
     ns += __shfl_xor_sync(0xffffffffu, ns, off);
   }
+  __shared__ unsigned long long part[8][3];
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&sums[0], (unsigned long long)it);
-    atomicAdd(&sums[1], (unsigned long long)nc);
-    atomicAdd(&sums[2], (unsigned long long)ns);
+    part[threadIdx.x >> 5][0] = it;
+    part[threadIdx.x >> 5][1] = nc;
+    part[threadIdx.x >> 5][2] = ns;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
+    if (t) atomicAdd(&sums[threadIdx.x], t);
   }
 }
 
@@ -520,10 +533,17 @@ hydro_status hydro_mlp_iterations(hydro_mlp* m, const float* d_samples, long lon
   cudaError_t e = cudaMalloc((void**)&d_sums, sizeof h);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_sums, 0, sizeof h, m->stream);
   if (e == cudaSuccess) {
-    const unsigned long long blocks = ((unsigned long long)n + 255) / 256;
-    hydro::riemann_iters_kernel<<<(unsigned int)blocks, 256, 0, m->stream>>>(
-        m->blob, d_samples, (unsigned long long)n, learned ? 1 : 0, (float)gamma, (float)tol, maxiter, d_sums);
-    e = cudaGetLastError();
+    // enough blocks to fill the GPU several times over; each takes a share of the samples
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    unsigned long long blocks = ((unsigned long long)n + 255) / 256;
+    const unsigned long long cap = 8ull * (unsigned long long)(nsm > 0 ? nsm : 1);
+    if (blocks > cap) blocks = cap;
+    if (e == cudaSuccess)
+      hydro::riemann_iters_kernel<<<(unsigned int)blocks, 256, 0, m->stream>>>(
+          m->blob, d_samples, (unsigned long long)n, learned ? 1 : 0, (float)gamma, (float)tol, maxiter, d_sums);
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_sums, sizeof h, cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
