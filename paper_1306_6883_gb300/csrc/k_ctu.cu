@@ -10,8 +10,8 @@ cudaError_t ctu_step_fused(int precision, const KParams& P, const void* Uin, voi
                            StepScalars* sc_next, DevScratch* scr, double tmax, const CUtensorMap* tmap,
                            cudaStream_t stream, int2 band, const MlpBlob* mlp) {
   if (mlp != nullptr) {
-    // 320 threads (64 registers at 3 CTAs per SM): at 384 threads (56 registers) the call of the network's
-    // forward pass makes the allocator spill values the face loops use (22 local loads per warp and tile)
+    // 320 threads (64 registers at 3 CTAs per SM): at 384 threads (56 registers) the gate test in the face
+    // loops, together with the pass over the queued faces, makes the allocator spill inside the loops
     if (precision == 0 || P.reconstruction == 1 || P.riemann_solver == 1) return cudaErrorInvalidValue;
     return launch_ctu_step_fused<float, F32_TX, F32_TY, 320, FACE_LEARNED>(
         P, (const float*)Uin, (float*)Uout, sc_cur, sc_next, scr, tmax, tmap, stream, band, mlp);
