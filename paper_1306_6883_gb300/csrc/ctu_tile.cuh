@@ -463,7 +463,7 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
           states(e, e < nXIa, a, b);
           pref = mlp_features(a[0], a[1], a[3], b[0], b[1], b[3], x);
         }
-        float y = mlp_warp_forward(x, wsm);
+        float y = mlp_warp_forward(x, wsm, n - b0);
         y = fminf(fmaxf(y, -40.f), 40.f);
         if (k < n) queue[2 * k + 1] = pref * __expf(y);
       }

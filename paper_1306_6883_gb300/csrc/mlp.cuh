@@ -93,12 +93,16 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
 // Network output y for the face of every lane of the warp (all 32 lanes must call it).  Not inlined: the
 // CTU tiles call it only in their pass over the gated faces, after the face loops, and keeping its unrolled
 // tensor-core code and registers apart leaves the loops' register allocation as in the plain kernel.
-static __device__ __noinline__ float mlp_warp_forward(const float x[6], const MlpBlob* __restrict__ w) {
+// rows (warp-uniform): the lanes whose outputs are used are 0 .. rows-1; with rows <= 16 only the first 16-row
+// tile is evaluated (lanes 16-31 then return 0).  A tile's pass over one to sixteen gated faces, the common
+// case, then waits on half the network's latency.
+static __device__ __noinline__ float mlp_warp_forward(const float x[6], const MlpBlob* __restrict__ w, int rows = 32) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float yv[2][2];  // [m tile][row half] partial outputs of rows 16 mt + g + 8 half
+  float yv[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [m tile][row half] partial outputs of rows 16 mt + g + 8 half
+  const int nmt = rows > 16 ? 2 : 1;
   // one m tile at a time keeps the live fragments to ~40 registers (weights are re-read from shared memory)
 #pragma unroll 1
-  for (int mt = 0; mt < 2; ++mt) {
+  for (int mt = 0; mt < nmt; ++mt) {
     // A fragment of layer 1: rows 16 mt + g and + 8, columns 2t, 2t+1 (columns >= 6 are zero padding)
     float xa[6], xb[6];
 #pragma unroll
