@@ -545,11 +545,11 @@ def cpu_variant(pr, steps=5, **kw):
 
 
 # ---------------------------------------------------------------------------------------------------- secondary
-def time_ensemble(model=None, steps=100, warmup=3, n=256, seed=0):
-    """The 256-member ensemble of four-quadrant problems on {64,128,256,512}^2 grids (seeded), FP32, each
-    member with its own CFL dt; tile shapes autotuned per size class; `steps` steps captured in one CUDA
-    graph and launched once.  The states (~0.4 GB per buffer) exceed L2.  model: every member starts its
-    Riemann iterations from the network."""
+def time_ensemble(model=None, steps=100, warmup=3, n=256, seed=0, precision="fp32"):
+    """The 256-member ensemble of four-quadrant problems on {64,128,256,512}^2 grids (seeded), each member with
+    its own CFL dt; tile shapes autotuned per size class; `steps` steps captured in one CUDA graph and launched
+    once.  The states (~0.4 GB per FP32 buffer) exceed L2.  model: every member starts its Riemann iterations
+    from the network (FP32 only)."""
     import torch
 
     import hydro_problems as hp
@@ -558,7 +558,8 @@ def time_ensemble(model=None, steps=100, warmup=3, n=256, seed=0):
 
     probs = hp.ensemble(n, seed)
     learned = 1 if model is not None else 0
-    e = Ensemble([params_for(p, H.HYDRO_FP32, use_learned_guess=learned) for p in probs], [p.U for p in probs])
+    prec = H.HYDRO_FP32 if precision == "fp32" else H.HYDRO_FP64
+    e = Ensemble([params_for(p, prec, use_learned_guess=learned) for p in probs], [p.U for p in probs])
     if model is not None:
         e.set_model(model)
     shapes = e.autotune(reps=2)
@@ -583,7 +584,7 @@ def time_ensemble(model=None, steps=100, warmup=3, n=256, seed=0):
            # per run: one dt kernel; per step: one persistent fused step kernel per distinct tile shape
            "unit": "zone-updates/s", "graph_launches": 1, "kernel_launches": 1 + steps * len(set(shapes)),
            "classes": e.classes(), "riemann_iters_per_solve": stats[1] / max(stats[0], 1),
-           "learned": bool(learned)}
+           "learned": bool(learned), "precision": precision}
     e.close()
     return out
 
@@ -831,6 +832,9 @@ def run_ours(args, world, rank, local):
         secondary["sedov4096_fp32_error_to_t01"] = sedov4096_error(tmax=0.1)
     secondary["ensemble_plain"] = time_ensemble()
     secondary["ensemble_learned"] = time_ensemble(model=model)
+    secondary["ensemble_fp64"] = time_ensemble(steps=10, precision="fp64")
+    secondary["ensemble_speedup_fp32_learned_over_fp64"] = (secondary["ensemble_learned"]["value"]
+                                                           / secondary["ensemble_fp64"]["value"])
     secondary["learned_cost"] = learned_cost(model)
     secondary.update(variant_legs(flush, args.warmup, world))
     model.close()
