@@ -148,6 +148,25 @@ __device__ __forceinline__ void face_solve(const SP<R>& s, const R a[4], const R
   }
 }
 
+// The FP32 two-shock solve of a queued face, out of line for the single-problem step: there the pass over
+// queued faces is rare, and a second inlined copy of the solver in the kernel made the code generated for the
+// face loops slower (Sedov 4096^2 learned step 1.163 ms inline, 1.150 ms with this call).  Ensemble tiles,
+// whose passes are frequent, keep the solver inline (the call made them 2.6 % slower).
+static __device__ __noinline__ void riemann_out(float gamma, float g1, float igm1, float small_pres, float tol,
+                                                int maxiter, float rl, float ul, float vl, float pl, float rr,
+                                                float ur, float vr, float pr, float guess, float F[4], int& it,
+                                                bool& ok) {
+  SP<float> s{};
+  s.gamma = gamma;
+  s.g1 = g1;
+  s.igm1 = igm1;
+  s.small_pres = small_pres;
+  s.tol = tol;
+  s.maxiter = maxiter;
+  const float a[4] = {rl, ul, vl, pl}, b[4] = {rr, ur, vr, pr};
+  riemann(s, a, b, guess, F, it, ok);
+}
+
 // Gated faces a FACE_LEARNED tile holds per stage: 2 words each (face item, starting pressure).  A shared
 // array of its own (1 KB), present only in the learned kernels.
 constexpr int LEARNED_QUEUE = 128;
@@ -475,7 +494,11 @@ __device__ __forceinline__ void ctu_tile(const KParams& P, const SP<R>& s, const
         states(e, isx, a, b);
         int it;
         bool ok;
-        riemann(s, a, b, queue[2 * k + 1], F, it, ok);
+        if constexpr (PERSIST)  // ensembles: passes are frequent (quadrant interfaces), the call would cost more
+          riemann(s, a, b, queue[2 * k + 1], F, it, ok);
+        else
+          riemann_out(s.gamma, s.g1, s.igm1, s.small_pres, s.tol, s.maxiter, a[0], a[1], a[2], a[3], b[0], b[1], b[2],
+                      b[3], queue[2 * k + 1], F, it, ok);
         cnt.solves++;
         cnt.iters += it;
         cnt.nonconv += ok ? 0 : 1;
