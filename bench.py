@@ -1,7 +1,7 @@
 """Throughput of the unsplit CTU step on a GB300 (zone-updates per second, and the HBM roofline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sedov8192|sedov4096|kh1024|rt1024] [--sedov4096-to-t01]
+                    [--workload sedov8192|sedov4096|kh1024|kh2048|rt1024] [--sedov4096-to-t01]
 
 A step is one pass of the solver's driver loop (paper §2): ghost cells (read through the boundary map),
 the CTU step of §3.2 with every Riemann iteration started from the learned proposal, and the CFL time step
@@ -109,6 +109,8 @@ def workload(name):
         return hp.sedov(4096, 4096), "sedov_4096x4096_outflow"
     if name == "kh1024":
         return hp.kh(1024, 1024, seed=0), "kh_1024x1024_periodic"
+    if name == "kh2048":
+        return hp.kh(2048, 2048, seed=0), "kh_2048x2048_periodic"
     if name == "rt1024":
         return hp.rt(1024, 3072), "rayleigh_taylor_1024x3072_gravity_hydrostatic"
     raise SystemExit(f"unknown workload {name}")
