@@ -698,7 +698,8 @@ def learned_cost(model, n=1 << 23, seed=0):
         out[name] = res
         del dev
     out["note"] = ("the acoustic runs are bound by reading the samples (32 B per face), the learned ones by the "
-                   "network's arithmetic; the instruction counts per face are in the ncu summary of this kernel")
+                   "network's arithmetic; the instruction counts per face are in "
+                   "profiles/riemann_iters_kernel_learned_cost.md")
     return out
 
 
