@@ -237,7 +237,7 @@ def _canonical(d):
     return d[order].contiguous()
 
 
-def train_model(train_steps=6000, batch=4096, lr=1e-3, seed=0):
+def train_model(train_steps=50000, batch=4096, lr=3e-3, seed=0):
     """Training set for the learned starting pressure: Riemann problems sampled from FP32 runs of the Sod
     tube (128^2 to t = 0.2), the Kelvin-Helmholtz layer (1024^2, 40 steps) and the Sedov blast (4096^2, 300
     steps), the workloads of the paper's problem list this build runs at full size.  Faces are kept at random
