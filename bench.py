@@ -866,6 +866,10 @@ def run_ours(args, world, rank, local):
         secondary["sedov4096_fp32_error_to_t01"] = sedov4096_error(tmax=0.1)
     secondary["ensemble_plain"] = time_ensemble()
     secondary["ensemble_learned"] = time_ensemble(model=model)
+    # the learned kernels with the gate closed (no face queued): their cost apart from the network's passes
+    model.set_gate(40.0, 1e9)
+    secondary["ensemble_learned_gate_closed"] = time_ensemble(model=model)
+    model.set_gate(0.35, 1.0)
     secondary["ensemble_fp64"] = time_ensemble(steps=10, precision="fp64")
     secondary["ensemble_speedup_fp32_learned_over_fp64"] = (secondary["ensemble_learned"]["value"]
                                                            / secondary["ensemble_fp64"]["value"])
